@@ -1,0 +1,394 @@
+"""Scheme-level pins of the oracle: interface equilibrium (with the paper's
+printed errors and the paper's negative control), discrete conservation,
+the flux limiter re-verified face by face, the exact Riemann solution, design
+orders, phase-confined diffusion and the CDI equilibrium profile."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2504_14063_gb300 import workloads as W
+from tests.exact_riemann import sample
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _iec_errors(o, U, P0, T0, u0):
+    pr = o.primitives(U)
+    ns = o.problem.ns
+    rho = U[:ns].sum(0)
+    u = U[ns] / rho
+    return (np.abs(pr["P"] / P0 - 1).max(), np.abs(pr["T"] / T0 - 1).max(), np.abs(u / u0 - 1).max())
+
+
+@pytest.mark.parametrize("cdi", [0, 1])
+def test_iec_liquid_slab(cdi):
+    """Isothermal stiffened-liquid slab advected at uniform P, T, u (Sec. 3.1.2,
+    Appendix C): P, T and u stay uniform to ~1e-10 relative."""
+    p = W.interface_advection_1d(n=400, cdi=cdi)
+    o = Oracle(p, nthreads=2)
+    U, t, n, st = o.run(o.init_state(), 300)
+    assert st == 0
+    eP, eT, eu = _iec_errors(o, U, 1e5, 300.0, 100.0)
+    assert eP < 1e-10 and eT < 1e-12 and eu < 1e-12
+
+
+def test_golden_paper_droplet_advection_one_flow_through():
+    """Table DropAdvectionIECResults: after one flow-through of the 100-cell
+    water-in-air droplet with CDI, the maximum normalized errors are within a
+    small factor of the paper's WENO5Z figures."""
+    g = json.load(open(os.path.join(HERE, "golden", "drop_advection_iec.json")))
+    p = W.paper_droplet_advection(n=100, cdi=1)
+    o = Oracle(p, nthreads=1)
+    U, t, n, st = o.run(o.init_state(), 10 ** 7, t_end=p.t_end)
+    assert st == 0 and t == pytest.approx(p.t_end, rel=1e-12)
+    eP, eT, eu = _iec_errors(o, U, 101325.0, 297.0, 5.0)
+    ref = g["max_rel_err"]
+    assert eP <= 5 * ref["P"] and eT <= 5 * ref["T"] and eu <= 5 * ref["u"]
+
+
+def test_negative_control_five_equation_basis_breaks_iec():
+    """Table DropAdvectionNoIECResults: reconstructing [rhoY, u, P] instead of
+    the characteristic [T, Y, u, P] basis gives errors many orders larger.
+    Three species (water, air, helium) so that the partial densities are not
+    affine images of one field."""
+    p = W.paper_droplet_advection(n=100, cdi=1)
+    x = (np.arange(100) + 0.5) / 100
+    phi = p.prim[0]
+    he = 0.5 + 0.4 * np.sin(2 * np.pi * x)
+    pr = np.zeros((6, 1, 1, 100))
+    pr[0], pr[1], pr[2] = phi, (1 - phi) * (1 - he), (1 - phi) * he
+    pr[3], pr[4], pr[5] = 5.0, 101325.0, 297.0
+    p3 = W.Problem("neg", 1, (100, 1, 1), 0.01, [W.WATER_NASG, W.AIR_TABLE, W.HELIUM], W.Model(cdi=1), pr)
+    errs = {}
+    for basis in (0, 1):
+        o = Oracle(p3, nthreads=1, recon_basis=basis)
+        U, _, _, st = o.run(o.init_state(), 500)
+        errs[basis] = _iec_errors(o, U, 101325.0, 297.0, 5.0)
+    assert max(errs[0]) < 1e-10
+    assert errs[1][0] > 1e-7 and errs[1][1] > 1e-6
+
+
+def test_conservation_periodic():
+    """Shared face fluxes: every partial mass, momentum and energy is conserved
+    to round-off on a periodic domain (CDI and diffusion on)."""
+    p = W.random_smooth_2d(40, 32, seed=1, cdi=1, diffusion=1)
+    p.model.mu_liquid = 1e-1
+    for s in p.species:
+        s.mu *= 1e3
+    o = Oracle(p, nthreads=4)
+    U0 = o.init_state()
+    U, _, _, st = o.run(U0, 5)
+    assert st == 0
+    for v in range(o.nv):
+        scale = np.abs(U0[v]).sum()
+        assert abs(U[v].sum() - U0[v].sum()) <= 1e-13 * scale
+
+
+def _admissible(U, sp):
+    ns = len(sp)
+    rY = U[:ns]
+    rho = rY.sum(0)
+    D = U.shape[0] - ns - 1
+    b = np.array([s.b for s in sp])
+    q = np.array([s.q for s in sp])
+    mm = sum(U[ns + j] ** 2 for j in range(D))
+    ok = np.all(rY >= -1e-14 * rho, axis=0) & (rho > 0)
+    ok &= 1.0 - np.tensordot(b, rY, 1) > 0
+    ok &= U[ns + D] - 0.5 * mm / rho - np.tensordot(q, rY, 1) > 0
+    return ok
+
+
+def test_flux_limiter_decisions_brute_force():
+    """Tiny shock-interface grid with an oversized step: every face flux whose
+    pseudo-updates (factor 2 D RK2 dt/dx, Sec. 3.3.2) are admissible is kept,
+    every other face carries the first-order HLLC of the two cell states."""
+    p = W.shock_bubble_2d(nx=24, ny=12, seed=0, mach=3.0, cdi=0)
+    o = Oracle(p, nthreads=2)
+    U = o.init_state()
+    U, _, _, st = o.run(U, 3)
+    dt, G, _ = o.dt_gamma(U)
+    dt *= 3.0
+    rk = (0.75, 0.25, 0.25)
+    Uk = U.copy()
+    _, _, flags, _ = o.stage(U, Uk, rk, dt, G, flags=True)
+    F, _ = o.face_fluxes(U, Uk, rk, dt, G)
+    sp = p.species
+    ns, D = p.ns, p.dim
+    lam = 2 * D * rk[2] * dt / p.dx
+    pr = o.primitives(Uk)
+    n_fb = 0
+    off = 0
+    for d in range(D):
+        Fd = F[d]
+        nf = Fd[0].size
+        fl = flags[off:off + nf].reshape(Fd.shape[1:])
+        off += nf
+        # interior faces only (both neighbours are real cells)
+        sl = [slice(None)] * 3
+        axis = 2 - d
+        for f in range(1, Fd.shape[1 + axis] - 1):
+            sl_f = [slice(None)] * 3
+            sl_f[axis] = f
+            Ff = Fd[(slice(None),) + tuple(sl_f)]
+            sl_i = [slice(None)] * 3
+            sl_i[axis] = f - 1
+            sl_j = [slice(None)] * 3
+            sl_j[axis] = f
+            Ui = rk[0] * U[(slice(None),) + tuple(sl_i)] + rk[1] * Uk[(slice(None),) + tuple(sl_i)] - lam * Ff
+            Uj = rk[0] * U[(slice(None),) + tuple(sl_j)] + rk[1] * Uk[(slice(None),) + tuple(sl_j)] + lam * Ff
+            ok = _admissible(Ui, sp) & _admissible(Uj, sp)
+            fb = (fl[tuple(sl_f)] & 16) != 0
+            assert np.all(ok[~fb])
+            for idx in zip(*np.nonzero(fb)):
+                n_fb += 1
+                def cell(sl_c):
+                    Uc = Uk[(slice(None),) + tuple(sl_c)][(slice(None),) + idx]
+                    rho = Uc[:ns].sum()
+                    u = np.zeros(3)
+                    u[:D] = Uc[ns:ns + D] / rho
+                    P = pr["P"][tuple(sl_c)][idx]
+                    T = pr["T"][tuple(sl_c)][idx]
+                    return (Uc[:ns] / rho, u, P, T)
+                ref = o.hllc(d, cell(sl_i), cell(sl_j))
+                got = Ff[(slice(None),) + idx]
+                assert np.allclose(got, ref, rtol=1e-8, atol=1e-8 * np.abs(ref).max())
+    assert n_fb > 0
+
+
+def test_sod_against_exact_riemann():
+    """Single-phase Sod tube: density L1 error against the exact solution is
+    small and decreases with refinement."""
+    errs = []
+    for n in (100, 200, 400):
+        p = W.sod(n)
+        o = Oracle(p, nthreads=1)
+        U, t, _, st = o.run(o.init_state(), 10 ** 6, t_end=0.2)
+        assert st == 0
+        x = (np.arange(n) + 0.5) / n
+        ex = sample(x, 0.2, 0.5, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4)
+        rho = U[0, 0, 0]
+        errs.append(np.abs(rho - ex[0]).mean())
+    assert errs[1] < errs[0] and errs[2] < errs[1]
+    assert errs[1] < 6e-3
+
+
+def test_fifth_order_semidiscrete_advection():
+    """Two species with identical EOS at uniform P, T, u: the mixture is
+    linearly advected and the semi-discrete operator converges at order ~5."""
+    g1 = W.ideal_gas("a", 1.4, 0.029)
+    g2 = W.ideal_gas("b", 1.4, 0.029)
+    errs = []
+    for n in (16, 32, 64):
+        dx = 1.0 / n
+        xf = np.arange(n + 1) * dx
+        A = lambda x: 0.5 * x - 0.4 * np.cos(2 * np.pi * x) / (2 * np.pi)
+        abar = (A(xf[1:]) - A(xf[:-1])) / dx
+        pr = np.zeros((5, 1, 1, n))
+        pr[0, 0, 0], pr[1, 0, 0] = abar, 1 - abar
+        pr[2], pr[3], pr[4] = 50.0, 1e5, 300.0
+        p = W.Problem("adv", 1, (n, 1, 1), dx, [g1, g2], W.Model(), pr)
+        o = Oracle(p, nthreads=1)
+        U = o.init_state()
+        _, L, _, st = o.stage(U, U, (1, 0, 1), 0.0, 0.0)
+        rho = U[:2].sum(0)[0, 0, 0]
+        a = lambda x: 0.5 + 0.4 * np.sin(2 * np.pi * x)
+        exact = -50.0 * rho * (a(xf[1:]) - a(xf[:-1])) / dx
+        errs.append(np.abs(L[0, 0, 0] - exact).max())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders.min() > 4.5
+
+
+def test_second_order_multi_d_entropy_wave():
+    """Diagonal temperature wave advected in 2D at uniform P and u: with the
+    one-point face quadrature the scheme is second order (Appendix D.1)."""
+    errs = []
+    gas = W.ideal_gas("g", 1.4, 0.029)
+    for n in (16, 32, 64):
+        dx = 1.0 / n
+        c = (np.arange(n) + 0.5) * dx
+        X, Y = np.meshgrid(c, c)
+        T0 = lambda x, y: 300.0 * (1.0 + 0.2 * np.sin(2 * np.pi * (x + y)))
+        pr = np.zeros((5, 1, n, n))
+        pr[0] = 1.0
+        pr[1], pr[2] = 100.0, 50.0
+        pr[3] = 1e5
+        pr[4, 0] = T0(X, Y)
+        p = W.Problem("ent", 2, (n, n, 1), dx, [gas], W.Model(cfl=0.3), pr)
+        o = Oracle(p, nthreads=4)
+        tend = 2e-3
+        U, t, _, st = o.run(o.init_state(), 10 ** 6, t_end=tend)
+        T = o.primitives(U)["T"][0]
+        errs.append(np.abs(T - T0(X - 100.0 * t, Y - 50.0 * t)).mean())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders.min() > 1.8
+
+
+def _diffusion_problem(equal_W=False):
+    p = W.random_smooth_2d(24, 20, seed=3, cdi=0, diffusion=1, u0=0.0)
+    sp = [W.ideal_gas("air", 1.4, 0.029, mu=1.81e-1, Sc=1.0),
+          W.ideal_gas("he", 1.67, 0.029 if equal_W else 0.004, mu=1.96e-1, Sc=0.7),
+          W.LIQUID_SG]
+    p.species = sp
+    p.prim[3:5] = 0.0
+    p.prim[5] = 1e5
+    p.prim[6] = 300.0
+    p.model.mu_liquid = 0.5
+    return p
+
+
+def test_diffusion_confined_to_phase():
+    """Eq. SpeciesMassDiffusion: the intraphase fluxes of a phase sum to zero
+    on every face, so each cell keeps its phase masses while the composition
+    within the phase changes."""
+    p = _diffusion_problem()
+    o = Oracle(p, nthreads=4)
+    U0 = o.init_state()
+    F, _ = o.face_fluxes(U0, U0, (1, 0, 1), 0.0, 0.0)
+    for Fd in F:
+        gas = Fd[0] + Fd[1]
+        assert np.abs(gas).max() <= 1e-13 * np.abs(Fd[0]).max()
+    # with equal molar masses P stays uniform and the fluid at rest, so the
+    # per-face statement becomes a per-cell invariant over many steps
+    o = Oracle(_diffusion_problem(equal_W=True), nthreads=4)
+    U0 = o.init_state()
+    U, _, _, st = o.run(U0, 20)
+    assert st == 0
+    gas0, gas1 = U0[0] + U0[1], U[0] + U[1]
+    assert np.abs(gas1 - gas0).max() <= 1e-12 * gas0.max()
+    assert np.abs(U[2] - U0[2]).max() <= 1e-12 * U0[2].max()
+    assert np.abs(U[1] - U0[1]).max() > 1e-4 * U0[1].max()
+
+
+def test_diffusion_isothermal_equal_molar_mass():
+    """Equal molar masses, uniform P and T, no flow: species diffusion with
+    the energy flux sum_c J^c h^c leaves P and T uniform to round-off."""
+    p = _diffusion_problem(equal_W=True)
+    o = Oracle(p, nthreads=4)
+    U0 = o.init_state()
+    U, _, _, st = o.run(U0, 20)
+    pr = o.primitives(U)
+    assert np.abs(pr["T"] / 300.0 - 1).max() < 1e-12
+    assert np.abs(pr["P"] / 1e5 - 1).max() < 1e-9
+    assert np.abs(U[1] - U0[1]).max() > 1e-4 * U0[1].max()
+
+
+def test_cdi_keeps_equilibrium_profile_and_sharpens_others():
+    """Eq. MPMC_ACDI: the tanh profile of thickness epsilon is the regularized
+    equilibrium, so at rest it barely changes, while a three-times thicker
+    profile is sharpened."""
+    def run(width):
+        n = 64
+        dx = 1.0 / n
+        x = (np.arange(n) + 0.5) * dx
+        phi = 0.5 * (np.tanh((x - 0.25) / (2 * width * dx)) - np.tanh((x - 0.75) / (2 * width * dx)))
+        pr = np.zeros((5, 1, 1, n))
+        pr[0, 0, 0], pr[1, 0, 0] = phi, 1 - phi
+        pr[2], pr[3], pr[4] = 0.0, 1e5, 300.0
+        p = W.Problem("cdi", 1, (n, 1, 1), dx, [W.LIQUID_SG, W.GAS_C1], W.Model(cdi=1, cdi_gamma=50.0), pr)
+        o = Oracle(p, nthreads=1)
+        U0 = o.init_state()
+        U, _, _, st = o.run(U0, 200)
+        ph0 = o.primitives(U0)["phi0"][0, 0]
+        ph = o.primitives(U)["phi0"][0, 0]
+        slope = lambda f: np.abs(np.diff(f)).max()
+        return ph0, ph, slope(ph0), slope(ph)
+    e0, e1, s0, s1 = run(1.0)
+    assert np.abs(e1 - e0).max() < 0.02
+    w0, w1, t0, t1 = run(3.0)
+    assert t1 > 1.2 * t0
+
+
+def test_cfl_and_gamma_on_uniform_state():
+    p = W.interface_advection_1d(n=50)
+    p.prim[0] = 1.0
+    p.prim[1] = 0.0
+    o = Oracle(p)
+    U = o.init_state()
+    dt, G, st = o.dt_gamma(U)
+    a = o.eos_forward(np.array([1.0, 0.0]), 1e5, 300.0)["a"]
+    assert dt == pytest.approx(0.5 * p.dx / (100.0 + a), rel=1e-12)
+    assert G == pytest.approx(100.0, rel=1e-14)
+
+
+def test_shock_bubble_stays_admissible():
+    """A shrunken 2D shock-bubble-liquid layer case runs with every cell
+    admissible (positivity limiters on)."""
+    p = W.shock_bubble_2d(nx=96, ny=48, seed=0)
+    o = Oracle(p, nthreads=4)
+    U, _, n, st = o.run(o.init_state(), 30)
+    assert st == 0 and n == 30
+    assert np.all(_admissible(U, p.species))
+
+
+def _wilke_mole_fraction_form(x, mu, Wm):
+    """Wilke (1950) in its textbook mole-fraction form."""
+    n = len(x)
+    out = 0.0
+    for i in range(n):
+        den = 0.0
+        for j in range(n):
+            phi = (1 + (mu[i] / mu[j]) ** 0.5 * (Wm[j] / Wm[i]) ** 0.25) ** 2 / (8 * (1 + Wm[i] / Wm[j])) ** 0.5
+            den += x[j] * phi
+        out += x[i] * mu[i] / den
+    return out
+
+
+def _mixture_viscosity_from_cfl(species, alphas, mu_liquid=0.0):
+    """Reads the mixture viscosity back from the diffusive CFL limit
+    dt = CFL rho dx^2 / (4 mu) on a uniform state with a tiny cell."""
+    n = 4
+    pr = np.zeros((len(species) + 3, 1, 1, n))
+    for k, a in enumerate(alphas):
+        pr[k] = a
+    pr[-3], pr[-2], pr[-1] = 0.0, 1e5, 300.0
+    dx = 1e-9
+    p = W.Problem("mu", 1, (n, 1, 1), dx, list(species), W.Model(diffusion=1, mu_liquid=mu_liquid), pr)
+    o = Oracle(p)
+    U = o.init_state()
+    dt, _, _ = o.dt_gamma(U)
+    rho = U[:len(species)].sum(0).ravel()[0]
+    return 0.5 * rho * dx * dx / (4.0 * dt)
+
+
+def test_wilke_viscosity_and_phase_mixing():
+    """Sec. 2.2.2: gas viscosity by Wilke's rule (here against the textbook
+    mole-fraction form), mixture viscosity sum_p phi_p mu_p."""
+    sp = [W.AIR, W.HELIUM]
+    for xa in (1.0, 0.7, 0.3):
+        # volume fractions of ideal gases at common P, T are mole fractions
+        mu = _mixture_viscosity_from_cfl(sp, [xa, 1 - xa])
+        ref = _wilke_mole_fraction_form([xa, 1 - xa], [s.mu for s in sp], [s.W for s in sp])
+        assert mu == pytest.approx(ref, rel=1e-12)
+    mu = _mixture_viscosity_from_cfl([W.AIR, W.LIQUID_SG], [0.4, 0.6], mu_liquid=2e-3)
+    assert mu == pytest.approx(0.4 * W.AIR.mu + 0.6 * 2e-3, rel=1e-12)
+
+
+def test_binary_diffusion_reduces_to_fick():
+    """Eq. SpeciesMassDiffusion for a binary single-phase mixture with equal
+    Schmidt numbers reduces to J = -rho D grad Y with D = mu / (rho Sc): the
+    semi-discrete rate of a small sine in composition matches
+    (mu/Sc) d2Y/dx2 to second order."""
+    sp = [W.ideal_gas("air", 1.4, 0.029, mu=2e-5, Sc=0.8), W.ideal_gas("he", 1.67, 0.004, mu=2e-5, Sc=0.8)]
+    n = 64
+    dx = 1e-3
+    x = (np.arange(n) + 0.5) * dx
+    L = n * dx
+    xa = 0.5 + 1e-4 * np.sin(2 * np.pi * x / L)
+    pr = np.zeros((5, 1, 1, n))
+    pr[0, 0, 0], pr[1, 0, 0] = xa, 1 - xa
+    pr[2], pr[3], pr[4] = 0.0, 1e5, 300.0
+    p = W.Problem("fick", 1, (n, 1, 1), dx, sp, W.Model(diffusion=1), pr)
+    o = Oracle(p)
+    U = o.init_state()
+    _, Lr, _, _ = o.stage(U, U, (1, 0, 1), 0.0, 0.0)
+    rho = U[:2].sum(0)[0, 0]
+    Y = U[0, 0, 0] / rho
+    mu = _wilke_mole_fraction_form([0.5, 0.5], [2e-5, 2e-5], [0.029, 0.004])
+    k = 2 * np.pi / L
+    Ymean = Y.mean()
+    dY = Y - Ymean
+    expected = -(mu / 0.8) * k * k * dY
+    assert np.abs(Lr[0, 0, 0] - expected).max() <= 0.01 * np.abs(expected).max()
