@@ -43,6 +43,7 @@ constexpr int MAXS = ORC_MAXS;
 constexpr int MAXV = MAXS + 4;   // conserved variables
 constexpr int MAXC = MAXS + 4;   // characteristic variables
 constexpr double YTOL = 1e-14;   // round-off allowance on partial densities
+constexpr double GTOL = 1e-8;    // |grad psi| below which the interface normal is zero
 
 using std::vector;
 
@@ -907,7 +908,10 @@ struct Solver {
       R gn(0.0);
       for (int t = 0; t < 3; ++t) gn = gn + g[t] * g[t];
       gn = sqrt(gn);
-      R nd = val(gn) > 0.0 ? g[d] / gn : R(0.0);
+      /* reading: the normal is taken as zero where |grad psi| is below
+       * GTOL (psi near a signed distance has |grad psi| ~ 1; a flat far
+       * field gives round-off, whose normalized direction is noise) */
+      R nd = val(gn) >= GTOL ? g[d] / gn : R(0.0);
       R psib = 0.5 * (ci.psi + cj.psi);
       R th = tanh(psib / (2.0 * eps));
       /* Eq. SkewSymmetricSplitting_Regularization_Expanded */
