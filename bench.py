@@ -1,0 +1,274 @@
+#!/usr/bin/env python
+"""Benchmark of the MPMC hot path: SSP-RK3 steps (three right-hand-side
+stages with the update fused in) of the 2D shock-bubble workload, 1024 x 512
+cells, 3 species in 2 phases, CDI on, FP64, on one GB300 per rank.
+
+One JSON line on rank 0.  `value` is device-timed cell-updates/s (inputs
+resident in HBM, L2 flushed between steps outside the per-step events);
+`e2e` is the same metric through the host-buffer C-ABI entry, copies
+included; `roofline` is the face-flux kernel (the dominant one) against the
+FP64 ALU peak; `cpu_baseline` is the CPU oracle on the host cores.
+`--impl reference` times the CPU oracle itself (there is no other
+implementation of the paper's method to install).
+With N ranks (torchrun) every rank runs an independent replica (the path is
+built for one GPU; the whole-job value sums the replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s (FP64 vs mixed at stated L1 error); adjoint/forward time ratio"
+UNIT = "cell-updates/s"
+FP64_PEAK_NOMINAL = 1.25e12   # GB300 FP64, nominal (no FP64 figure is measured in MEASURED_PEAKS)
+L2_BYTES = 129 * 2 ** 20
+
+
+def flops_per_face(ns, D, cdi, diffusion, pos_limiter=True):
+    """Algorithmic FP64 operations of one face (every +, -, *, /, sqrt,
+    transcendental counted once; an FMA counts two), itemized in the order of
+    the Godunov approach:"""
+    nv = ns + D + 1
+    eos_inv = 4 + 6 * ns + 10 + 5 + 2 + 4 + 3 + 7 * ns       # mixture sums, quadratic root, NASG_T1
+    eos_fwd = 13 * ns + 10                                     # v, e, alpha, beta, a at (P, T, Y)
+    f = 0
+    f += 2 * nv + 3 * ns + 2 * D + 6                           # face average of U, decode
+    f += eos_inv + eos_fwd + 8                                 # its EOS, X, rho a
+    f += 6 * 8                                                 # projection of 6 cells (w1, w5, w6)
+    f += 63 * 2 * (3 + ns + (D - 1))                           # WENO5-Z, both sides
+    f += 2 * 8                                                 # back-projection
+    if pos_limiter:
+        f += 2 * (3 * ns + 6) + 2 * (ns + 1)                   # Y limiter, theta_T, theta_P
+    f += 2 * (eos_fwd + 3 * ns + 2 * D + 6)                    # face states from the EOS
+    f += 22 + 8 * ns + 14 * D + 20                             # HLLC
+    if pos_limiter:
+        f += 2 * (3 * nv) + 2 * (4 * ns + 2 * D + 6)           # pseudo-updates + admissibility
+    if cdi:
+        f += 2 + 1 + 6 * (D - 1) + 2 * D + 2 + 1 + 12 + 4 * ns + 8 + 3 * D + 3 + nv
+        if pos_limiter:
+            f += 2 * (3 * nv) + 2 * (4 * ns + 2 * D + 6)
+    if diffusion:
+        f += 3 + ns * 10 + 6 * ns + 2
+    return f
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload():
+    from paper_2504_14063_gb300 import workloads as W
+    return W.shock_bubble_2d(nx=1024, ny=512, seed=0)
+
+
+def config_of(p, extra=None):
+    c = {"workload": "shock_bubble_2d", "grid": list(p.n[:p.dim]), "cells": p.ncells, "species": p.ns,
+         "phases": 2, "cdi": bool(p.model.cdi), "diffusion": bool(p.model.diffusion),
+         "mach": 1.5, "integrator": "SSP-RK3", "cfl": p.model.cfl,
+         "l2": "flushed between steps (256 MiB write, outside the per-step events)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def cpu_baseline(p, seconds=12.0):
+    """The CPU oracle, as it stands, on the host cores: SSP-RK3 steps of the
+    full workload until about `seconds` have passed."""
+    from oracle import Oracle
+    cores = os.cpu_count() or 1
+    o = Oracle(p, nthreads=cores)
+    U = o.init_state()
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        U = o.rk_step(U)[0]
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": p.ncells * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} SSP-RK3 steps of the full {p.n[0]}x{p.n[1]} workload from its initial state "
+                      f"({el:.1f} s, OpenMP threads = {cores})"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    p = workload()
+    from oracle import Oracle
+    cores = os.cpu_count() or 1
+    o = Oracle(p, nthreads=cores)
+    U = o.init_state()
+    for _ in range(args.warmup):
+        U = o.rk_step(U)[0]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = o.rk_step(U)[0]
+    el = time.perf_counter() - t0
+    v = p.ncells * args.steps / el
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": config_of(p, {"l2": "n/a (CPU)"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} timed SSP-RK3 steps of the full workload after "
+                                       f"{args.warmup} warm-up steps"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2504_14063_gb300 import binding as mp
+    p = workload()
+    ctx = mp.Context(p)
+    U = ctx.init_state(torch.from_numpy(p.prim))
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        ctx.rk_step(U)
+    torch.cuda.synchronize()
+    ctx.stats(reset=True)
+    ctx.profile(reset=True)
+
+    # ---- device-timed region -----------------------------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.set_profiling(True)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record()
+        ctx.rk_step(U)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    ctx.set_profiling(False)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    status = ctx.status()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    prof = ctx.profile(reset=True)
+    stats = ctx.stats(reset=True)
+    value = world * p.ncells * args.steps / total_s
+
+    # roofline of the face-flux kernel (dominant): algorithmic FP64 flops
+    face_ms, face_n = prof["face"]
+    faces_per_launch = ctx.nfaces_total / p.dim
+    fpf = flops_per_face(p.ns, p.dim, p.model.cdi, p.model.diffusion, p.model.pos_limiter)
+    achieved = fpf * faces_per_launch / (face_ms / face_n / 1e3) / 1e12
+    launches = int(sum(n for _, n in prof.values()))
+
+    # ---- end to end through the host-buffer entry --------------------------
+    H = U.cpu().pin_memory()
+    ctx.step_n_host(H, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.step_n_host(H, 1)
+    e2e_s = time.perf_counter() - t0
+    nbytes = ctx.nv * ctx.ncells * 8
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(p, {"parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"}),
+            "clocks": clk,
+            "e2e": {"value": world * p.ncells * args.steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL / 1e12,
+                         "unit": "TFLOP/s", "frac": achieved * 1e12 / FP64_PEAK_NOMINAL, "traffic": None,
+                         "kernel": "k_face (FP64 face flux)", "flops_per_face": fpf,
+                         "faces_per_launch": faces_per_launch, "avg_launch_ms": face_ms / face_n,
+                         "peak_source": "nominal GB300 FP64 rate (recipe table); FP64 pipe, not HBM, binds"},
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "limiter_activity": {k: stats[k] / max(stats["faces"], 1) for k in
+                                 ("hllc_fallback", "cdi_dropped", "theta_p", "theta_t", "ylim")},
+            "status": status,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

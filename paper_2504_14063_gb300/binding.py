@@ -1,0 +1,275 @@
+"""Thin ctypes binding of libmpmc.so (include/mpmc.h).
+
+Argument marshalling only: torch CUDA tensors are passed by data pointer and
+every step of the path runs in the library's kernels.  If the library is
+missing the import of this module raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import workloads as _wl
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpmc.so")
+MAXS = 4
+
+OK, INVALID_ARG, CUDA_ERROR, INADMISSIBLE, EOS_NO_CONVERGE, OUT_OF_MEMORY = 0, 1, 2, 3, 4, 5
+FP64, MIXED = 0, 1
+F_THETA_T_L, F_THETA_T_R, F_THETA_P_L, F_THETA_P_R = 1, 2, 4, 8
+F_HLLC_FALLBACK, F_CDI_DROPPED, F_YLIM_L, F_YLIM_R = 16, 32, 64, 128
+
+
+class MpmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mpmc error {code}: {msg}")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("dx", ctypes.c_double),
+                ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3),
+                ("inflow", ctypes.c_double * (MAXS + 5))]
+
+
+class Eos(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int), ("phase", ctypes.c_int * MAXS)] + [
+        (f, ctypes.c_double * MAXS) for f in ("cv", "gamma", "q", "b", "pinf", "W", "mu", "Sc")]
+
+
+class ModelC(ctypes.Structure):
+    _fields_ = [("weno_eps", ctypes.c_double), ("cdi", ctypes.c_int), ("diffusion", ctypes.c_int),
+                ("pos_limiter", ctypes.c_int), ("cdi_eps", ctypes.c_double), ("cdi_gamma", ctypes.c_double),
+                ("phi_min", ctypes.c_double), ("psi_delta", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("mu_liquid", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class StageC(ctypes.Structure):
+    _fields_ = [("U_n", ctypes.c_void_p), ("rk0", ctypes.c_double), ("rk1", ctypes.c_double),
+                ("rk2", ctypes.c_double), ("dt", ctypes.c_double), ("Gamma", ctypes.c_double)]
+
+
+class StatsC(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("faces", "hllc_fallback", "cdi_dropped", "theta_p", "theta_t", "ylim")]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmpmc.so not found at {LIB_PATH}: build it with paper_2504_14063_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "mpmc_create": (i, [ctypes.POINTER(Grid), ctypes.POINTER(Eos), ctypes.POINTER(ModelC), vp,
+                            ctypes.POINTER(vp)]),
+        "mpmc_destroy": (None, [vp]),
+        "mpmc_set_stream": (i, [vp, vp]),
+        "mpmc_nvars": (i, [vp]),
+        "mpmc_ncells": (ctypes.c_size_t, [vp]),
+        "mpmc_init_state": (i, [vp, vp, vp]),
+        "mpmc_rhs": (i, [vp, vp, vp, ctypes.POINTER(StageC), vp]),
+        "mpmc_rk_step": (i, [vp, vp, d, vp]),
+        "mpmc_step_n": (i, [vp, vp, i, vp]),
+        "mpmc_step_n_host": (i, [vp, vp, i]),
+        "mpmc_dt_gamma": (i, [vp, vp, vp]),
+        "mpmc_rhs_adjoint": (i, [vp, vp, ctypes.POINTER(StageC), vp, vp, vp]),
+        "mpmc_get_stats": (i, [vp, ctypes.POINTER(StatsC), i]),
+        "mpmc_get_status": (i, [vp, i]),
+        "mpmc_last_error": (ctypes.c_char_p, [vp]),
+        "mpmc_set_profiling": (i, [vp, i]),
+        "mpmc_get_profile": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64), i]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    assert t.is_cuda and t.is_contiguous(), "expects a contiguous CUDA tensor"
+    return t.data_ptr()
+
+
+def _dev(t):
+    assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+    return t.data_ptr()
+
+
+def structs_from_problem(problem, precision=FP64):
+    """Library structs from a workloads.Problem (same fields as the paper's
+    species table and model coefficients)."""
+    g = Grid()
+    g.dim = problem.dim
+    for d in range(3):
+        g.n[d] = problem.n[d]
+        g.bc_lo[d] = problem.bc_lo[d]
+        g.bc_hi[d] = problem.bc_hi[d]
+    g.dx = problem.dx
+    if problem.inflow is not None:
+        for q, v in enumerate(problem.inflow):
+            g.inflow[q] = float(v)
+    e = Eos()
+    e.n_species = problem.ns
+    for k, s in enumerate(problem.species):
+        e.phase[k] = s.phase
+        for f in ("cv", "gamma", "q", "b", "pinf", "W", "mu", "Sc"):
+            getattr(e, f)[k] = getattr(s, f)
+    m = ModelC()
+    pm = problem.model
+    for f in ("weno_eps", "cdi", "diffusion", "pos_limiter", "cdi_eps", "cdi_gamma", "phi_min", "psi_delta",
+              "cfl", "mu_liquid"):
+        setattr(m, f, getattr(pm, f))
+    m.precision = precision
+    return g, e, m
+
+
+class Context:
+    """One grid / species table / model on the current CUDA device."""
+
+    def __init__(self, problem, precision=FP64, stream=None):
+        self.problem = problem
+        self.precision = precision
+        g, e, m = structs_from_problem(problem, precision)
+        self._structs = (g, e, m)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        h = ctypes.c_void_p()
+        rc = lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), ctypes.c_void_p(s.cuda_stream),
+                             ctypes.byref(h))
+        if rc != OK:
+            raise MpmcError(rc, "mpmc_create failed")
+        self.h = h
+        self.nv = lib.mpmc_nvars(h)
+        self.ncells = lib.mpmc_ncells(h)
+        self.shape = (self.nv, problem.n[2], problem.n[1], problem.n[0])
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and lib is not None:
+            lib.mpmc_destroy(h)
+            self.h = None
+
+    def _check(self, rc):
+        if rc != OK:
+            raise MpmcError(rc, lib.mpmc_last_error(self.h).decode())
+
+    def nfaces(self, d):
+        n = list(self.problem.n)
+        n[d] += 1
+        return n[0] * n[1] * n[2]
+
+    @property
+    def nfaces_total(self):
+        return sum(self.nfaces(d) for d in range(self.problem.dim))
+
+    def empty_state(self):
+        return torch.empty(self.shape, dtype=torch.float64, device=self.device)
+
+    # ---- the five entry points ---------------------------------------------
+    def init_state(self, prim, U=None):
+        prim = prim.to(self.device, torch.float64).contiguous() if torch.is_tensor(prim) else \
+            torch.as_tensor(prim, dtype=torch.float64, device=self.device).contiguous()
+        U = self.empty_state() if U is None else U
+        self._check(lib.mpmc_init_state(self.h, _dev(prim), _dev(U)))
+        return U
+
+    def rhs(self, U, dUdt=None, stage=None, flags=None):
+        """stage: None or dict(U_n=tensor, rk=(rk0, rk1, rk2), dt=float, Gamma=float)."""
+        dUdt = torch.empty_like(U) if dUdt is None else dUdt
+        sp = None
+        if stage is not None:
+            sc = StageC()
+            sc.U_n = _dev(stage["U_n"]) if stage.get("U_n") is not None else None
+            sc.rk0, sc.rk1, sc.rk2 = stage.get("rk", (1.0, 0.0, 1.0))
+            sc.dt = stage.get("dt", 0.0)
+            sc.Gamma = stage.get("Gamma", -1.0)
+            sp = ctypes.byref(sc)
+        self._check(lib.mpmc_rhs(self.h, _dev(U), _dev(dUdt), sp, _ptr(flags)))
+        return dUdt
+
+    def rk_step(self, U, dt=0.0, tape=None):
+        self._check(lib.mpmc_rk_step(self.h, _dev(U), float(dt), _ptr(tape)))
+        return U
+
+    def step_n(self, U, n, dt_out=None):
+        self._check(lib.mpmc_step_n(self.h, _dev(U), int(n), _ptr(dt_out)))
+        return U
+
+    def step_n_host(self, U_host, n):
+        """U_host: CPU float64 tensor (pinned for overlap), updated in place."""
+        assert U_host.dtype == torch.float64 and not U_host.is_cuda and U_host.is_contiguous()
+        self._check(lib.mpmc_step_n_host(self.h, U_host.data_ptr(), int(n)))
+        return U_host
+
+    def dt_gamma(self, U):
+        out = torch.empty(2, dtype=torch.float64, device=self.device)
+        self._check(lib.mpmc_dt_gamma(self.h, _dev(U), _dev(out)))
+        return out
+
+    def rhs_adjoint(self, U, stage, tape, lam_dUdt, lam_U=None):
+        lam_U = torch.zeros_like(U) if lam_U is None else lam_U
+        sc = StageC()
+        sc.U_n = _dev(stage["U_n"])
+        sc.rk0, sc.rk1, sc.rk2 = stage["rk"]
+        sc.dt = stage["dt"]
+        sc.Gamma = stage["Gamma"]
+        self._check(lib.mpmc_rhs_adjoint(self.h, _dev(U), ctypes.byref(sc), _ptr(tape), _dev(lam_dUdt),
+                                         _dev(lam_U)))
+        return lam_U
+
+    def set_profiling(self, enable=True):
+        self._check(lib.mpmc_set_profiling(self.h, 1 if enable else 0))
+
+    def profile(self, reset=False):
+        """{family: (ms, launches)} for prim, face, update, dt."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_uint64 * 4)()
+        self._check(lib.mpmc_get_profile(self.h, ms, n, 1 if reset else 0))
+        return {k: (ms[i], n[i]) for i, k in enumerate(("prim", "face", "update", "dt"))}
+
+    def status(self, reset=False):
+        return lib.mpmc_get_status(self.h, 1 if reset else 0)
+
+    def stats(self, reset=False):
+        s = StatsC()
+        self._check(lib.mpmc_get_stats(self.h, ctypes.byref(s), 1 if reset else 0))
+        return {f: getattr(s, f) for f, _ in StatsC._fields_}
+
+
+# module-level names mirroring the C ABI
+def create(problem, precision=FP64, stream=None):
+    return Context(problem, precision, stream)
+
+
+def init_state(ctx, prim, U=None):
+    return ctx.init_state(prim, U)
+
+
+def rhs(ctx, U, dUdt=None, stage=None, flags=None):
+    return ctx.rhs(U, dUdt, stage, flags)
+
+
+def rk_step(ctx, U, dt=0.0, tape=None):
+    return ctx.rk_step(U, dt, tape)
+
+
+def step_n(ctx, U, n, dt_out=None):
+    return ctx.step_n(U, n, dt_out)
+
+
+def rhs_adjoint(ctx, U, stage, tape, lam_dUdt, lam_U=None):
+    return ctx.rhs_adjoint(U, stage, tape, lam_dUdt, lam_U)
+
+
+workloads = _wl

@@ -1,0 +1,520 @@
+// C ABI of the MPMC hot path (declared in include/mpmc.h): context,
+// scratch, stage sequencing of Eq. SSPRK3, CUDA-graph replay of steps.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mpmc.h"
+#include "mpmc_device.cuh"
+#include "mpmc_ops.h"
+
+using namespace mpmc;
+
+struct mpmc_ctx {
+  KParams P;
+  Ops ops;
+  int precision;
+  cudaStream_t stream;
+  cudaStream_t cap;  // internal stream used only to capture graphs
+  int device;
+  double* Wc = nullptr;
+  double* F[3] = {nullptr, nullptr, nullptr};
+  long long nface[3] = {0, 0, 0};
+  long long nface_total = 0;
+  double* U1 = nullptr;
+  double* U2 = nullptr;
+  double* Ud = nullptr;   // device state of the host-buffer entry
+  double* Uin = nullptr;
+  double* scal = nullptr; // [dt, Gamma]
+  unsigned long long* red = nullptr;
+  int* status = nullptr;
+  unsigned long long* stats = nullptr;
+  int* counter = nullptr;
+  // graph of one SSP-RK3 step for step_n
+  cudaGraphExec_t gexec = nullptr;
+  const double* g_U = nullptr;
+  double* g_hist = nullptr;
+  unsigned long long faces_done = 0;
+  // optional kernel timing
+  bool profiling = false;
+  bool capturing = false;
+  struct Mark {
+    int fam;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[4] = {0, 0, 0, 0};
+  unsigned long long prof_n[4] = {0, 0, 0, 0};
+  char err[256];
+};
+
+enum { FAM_PRIM = 0, FAM_FACE = 1, FAM_UPDATE = 2, FAM_DT = 3 };
+
+static cudaEvent_t take_event(mpmc_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// brackets one launch of family `fam` with events on stream s
+struct ProfScope {
+  mpmc_ctx* c;
+  int fam;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(mpmc_ctx* c_, int fam_, cudaStream_t s_) : c(c_), fam(fam_), s(s_) {
+    if (c->profiling && !c->capturing) {
+      a = take_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, s);
+      c->marks.push_back({fam, a, b});
+    }
+  }
+};
+
+namespace mpmc {
+__global__ void k_dt(const KParams P, unsigned long long* red, double* scal, double dt_fixed, double gamma_fixed,
+                     double* dt_hist, int* counter) {
+  const double smax = __longlong_as_double((long long)red[0]);
+  const double gmax = __longlong_as_double((long long)red[1]);
+  const double dt = dt_fixed > 0.0 ? dt_fixed : P.cfl / smax;
+  const double G = gamma_fixed >= 0.0 ? gamma_fixed : (P.cdi_gamma > 0.0 ? P.cdi_gamma : gmax);
+  scal[0] = dt;
+  scal[1] = G;
+  red[0] = 0ull;
+  red[1] = 0ull;
+  if (dt_hist) {
+    dt_hist[*counter] = dt;
+    *counter += 1;
+  }
+}
+}  // namespace mpmc
+
+static int fail(mpmc_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+static int check_launch(mpmc_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, MPMC_CUDA_ERROR, "%s: %s", where, cudaGetErrorString(e));
+  return MPMC_OK;
+}
+
+static void free_all(mpmc_ctx* c) {
+  // g_U and g_hist are caller-owned and never freed here
+  void* ptrs[] = {c->Wc, c->F[0], c->F[1], c->F[2], c->U1, c->U2, c->Ud, c->Uin, c->scal, c->red, c->status, c->stats,
+                  c->counter};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  for (auto& m : c->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  c->marks.clear();
+  c->pool.clear();
+}
+
+static int alloc(mpmc_ctx* c, void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes < 16 ? 16 : bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, MPMC_OUT_OF_MEMORY, "cudaMalloc of %zu bytes failed", bytes);
+  }
+  return MPMC_OK;
+}
+
+extern "C" int mpmc_create(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_model* m, void* stream,
+                           mpmc_ctx** out) {
+  if (!out) return MPMC_INVALID_ARG;
+  *out = nullptr;
+  if (!g || !eos || !m) return MPMC_INVALID_ARG;
+  if (g->dim < 1 || g->dim > 3 || eos->n_species < 1 || eos->n_species > MPMC_MAXS || !(g->dx > 0.0))
+    return MPMC_INVALID_ARG;
+  if (m->precision != MPMC_FP64 && m->precision != MPMC_MIXED) return MPMC_INVALID_ARG;
+  for (int d = 0; d < 3; ++d) {
+    if (d < g->dim && g->n[d] < 3) return MPMC_INVALID_ARG;
+    if (d >= g->dim && g->n[d] != 1) return MPMC_INVALID_ARG;
+    if (d < g->dim && (g->bc_lo[d] < 0 || g->bc_lo[d] > 3 || g->bc_hi[d] < 0 || g->bc_hi[d] > 3))
+      return MPMC_INVALID_ARG;
+    if (d < g->dim && ((g->bc_lo[d] == MPMC_BC_PERIODIC) != (g->bc_hi[d] == MPMC_BC_PERIODIC)))
+      return MPMC_INVALID_ARG;
+  }
+  mpmc_ctx* c = new (std::nothrow) mpmc_ctx();
+  if (!c) return MPMC_OUT_OF_MEMORY;
+  c->err[0] = 0;
+  KParams& P = c->P;
+  memset(&P, 0, sizeof(P));
+  const int ns = eos->n_species, D = g->dim;
+  P.dim = D;
+  P.ns = ns;
+  P.nv = ns + D + 1;
+  for (int d = 0; d < 3; ++d) {
+    P.n[d] = g->n[d];
+    P.bc_lo[d] = d < D ? g->bc_lo[d] : 0;
+    P.bc_hi[d] = d < D ? g->bc_hi[d] : 0;
+    if (d < D && (P.bc_lo[d] == MPMC_BC_INFLOW || P.bc_hi[d] == MPMC_BC_INFLOW)) P.has_inflow = 1;
+  }
+  P.ncell = (long long)g->n[0] * g->n[1] * g->n[2];
+  P.dx = g->dx;
+  P.inv_dx = 1.0 / g->dx;
+  bool has0 = false, has1 = false;
+  for (int k = 0; k < ns; ++k) {
+    P.phase[k] = eos->phase[k] ? 1 : 0;
+    (P.phase[k] ? has1 : has0) = true;
+    P.cv[k] = eos->cv[k];
+    P.gam[k] = eos->gamma[k];
+    P.q[k] = eos->q[k];
+    P.b[k] = eos->b[k];
+    P.pinf[k] = eos->pinf[k];
+    P.W[k] = eos->W[k];
+    P.mu[k] = eos->mu[k];
+    P.Sc[k] = eos->Sc[k];
+    P.Rk[k] = (eos->gamma[k] - 1.0) * eos->cv[k];
+    P.cp[k] = eos->gamma[k] * eos->cv[k];
+  }
+  for (int i = 0; i < ns; ++i)
+    for (int j = 0; j < ns; ++j) {
+      const double Wij = P.W[i] / P.W[j];
+      const double t = 1.0 + std::sqrt(P.mu[i] / P.mu[j]) * std::pow(P.W[j] / P.W[i], 0.25);
+      const double Phi = t * t / (std::sqrt(8.0) * std::sqrt(1.0 + Wij));
+      P.wilke[i][j] = Wij * Phi;
+    }
+  P.two_phase = has0 && has1;
+  P.weno_eps = m->weno_eps;
+  P.cdi = m->cdi ? 1 : 0;
+  P.diffusion = m->diffusion ? 1 : 0;
+  P.pos_limiter = m->pos_limiter ? 1 : 0;
+  P.cdi_eps = m->cdi_eps > 0.0 ? m->cdi_eps : g->dx;
+  P.cdi_gamma = m->cdi_gamma;
+  P.phi_min = m->phi_min;
+  P.psi_delta = m->psi_delta;
+  P.cfl = m->cfl;
+  P.mu_liquid = m->mu_liquid;
+  P.sharp0 = 4.0 * m->phi_min * (1.0 - m->phi_min);
+  // primitive cache layout
+  int f = 0;
+  P.wT = f++;
+  P.wP = f++;
+  P.wRho = f++;
+  P.wA = f++;
+  P.wY = f;
+  f += ns;
+  P.wU = f;
+  f += D;
+  if (P.cdi) {
+    P.wPhi0 = f++;
+    P.wPsi = f++;
+    P.wYrho = f;
+    f += ns;
+    P.wHrho = f;
+    f += 2;
+  }
+  if (P.diffusion) {
+    P.wXr = f;
+    f += ns;
+    P.wB = f;
+    f += ns;
+  }
+  P.nW = f;
+  P.wstride = P.ncell + 1;
+  c->precision = m->precision;
+
+  switch (D) {
+    case 1: c->ops = ops_fp64_d1(ns); break;
+    case 2: c->ops = ops_fp64_d2(ns); break;
+    default: c->ops = ops_fp64_d3(ns); break;
+  }
+  if (!c->ops.face) {
+    delete c;
+    return MPMC_INVALID_ARG;
+  }
+  cudaGetDevice(&c->device);
+  c->stream = (cudaStream_t)stream;
+  int rc = MPMC_OK;
+  const size_t st_bytes = (size_t)P.nv * P.ncell * sizeof(double);
+  rc = rc ? rc : alloc(c, (void**)&c->Wc, (size_t)P.nW * P.wstride * sizeof(double));
+  for (int d = 0; d < D && !rc; ++d) {
+    long long nf = 1;
+    for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
+    c->nface[d] = nf;
+    c->nface_total += nf;
+    rc = alloc(c, (void**)&c->F[d], (size_t)P.nv * nf * sizeof(double));
+  }
+  rc = rc ? rc : alloc(c, (void**)&c->U1, st_bytes);
+  rc = rc ? rc : alloc(c, (void**)&c->U2, st_bytes);
+  rc = rc ? rc : alloc(c, (void**)&c->Uin, 32 * sizeof(double));
+  rc = rc ? rc : alloc(c, (void**)&c->scal, 8 * sizeof(double));
+  rc = rc ? rc : alloc(c, (void**)&c->red, 4 * sizeof(unsigned long long));
+  rc = rc ? rc : alloc(c, (void**)&c->status, 4 * sizeof(int));
+  rc = rc ? rc : alloc(c, (void**)&c->stats, 8 * sizeof(unsigned long long));
+  rc = rc ? rc : alloc(c, (void**)&c->counter, 4 * sizeof(int));
+  if (!rc && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+    rc = fail(c, MPMC_CUDA_ERROR, "stream creation failed");
+  if (rc) {
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  cudaMemsetAsync(c->red, 0, 4 * sizeof(unsigned long long), c->stream);
+  cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->stream);
+  cudaMemsetAsync(c->stats, 0, 8 * sizeof(unsigned long long), c->stream);
+  cudaMemsetAsync(c->scal, 0, 8 * sizeof(double), c->stream);
+  cudaMemsetAsync(c->Uin, 0, 32 * sizeof(double), c->stream);
+  if (P.has_inflow) {
+    // inflow state: primitive -> conserved on the device (1 cell)
+    double* tmp = nullptr;
+    rc = alloc(c, (void**)&tmp, 32 * sizeof(double));
+    if (!rc) {
+      double w[32] = {0};
+      for (int v = 0; v < ns + D + 2; ++v) w[v] = g->inflow[v];
+      cudaMemcpy(tmp, w, sizeof(w), cudaMemcpyHostToDevice);
+      c->ops.init(P, c->stream, tmp, c->Uin, 1);
+      cudaStreamSynchronize(c->stream);
+      cudaFree(tmp);
+    }
+  }
+  if (!rc) rc = check_launch(c, "create");
+  if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = fail(c, MPMC_CUDA_ERROR, "create sync");
+  if (rc) {
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return MPMC_OK;
+}
+
+extern "C" void mpmc_destroy(mpmc_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+extern "C" int mpmc_set_stream(mpmc_ctx* c, void* stream) {
+  if (!c) return MPMC_INVALID_ARG;
+  c->stream = (cudaStream_t)stream;
+  return MPMC_OK;
+}
+
+extern "C" int mpmc_nvars(const mpmc_ctx* c) { return c ? c->P.nv : 0; }
+extern "C" size_t mpmc_ncells(const mpmc_ctx* c) { return c ? (size_t)c->P.ncell : 0; }
+extern "C" const char* mpmc_last_error(const mpmc_ctx* c) { return c ? c->err : "null context"; }
+
+extern "C" int mpmc_init_state(mpmc_ctx* c, const double* prim, double* U) {
+  if (!c || !prim || !U) return fail(c, MPMC_INVALID_ARG, "init_state: null argument");
+  c->ops.init(c->P, c->stream, prim, U, c->P.ncell);
+  return check_launch(c, "init_state");
+}
+
+// ---------------------------------------------------------------------------
+// one stage: faces of every direction from the primitive cache of Uk, then
+// the fused divergence / RK combination
+static void stage(mpmc_ctx* c, cudaStream_t s, const double* Un, const double* Uk, double rk0, double rk1, double rk2,
+                  double* Uout, double* dUdt, uint32_t* flags) {
+  const KParams& P = c->P;
+  long long off = 0;
+  for (int d = 0; d < P.dim; ++d) {
+    ProfScope ps(c, FAM_FACE, s);
+    c->ops.face(P, s, d, c->Wc, Un, Uk, c->Uin, c->scal, rk0, rk1, rk2, c->F[d], flags ? flags + off : nullptr,
+                c->stats);
+    off += c->nface[d];
+  }
+  ProfScope ps(c, FAM_UPDATE, s);
+  c->ops.update(P, s, Un, Uk, c->F, c->scal, rk0, rk1, rk2, Uout, dUdt, c->status);
+}
+
+static void prim(mpmc_ctx* c, cudaStream_t s, const double* U, unsigned long long* red) {
+  ProfScope ps(c, FAM_PRIM, s);
+  c->ops.prim(c->P, s, U, c->Uin, c->Wc, red, c->status);
+}
+
+// dt and Gamma from U (prim pass with the block maxima), then k_dt
+static void dt_gamma(mpmc_ctx* c, cudaStream_t s, const double* U, double dt_fixed, double gamma_fixed,
+                     double* hist) {
+  prim(c, s, U, c->red);
+  ProfScope ps(c, FAM_DT, s);
+  k_dt<<<1, 1, 0, s>>>(c->P, c->red, c->scal, dt_fixed, gamma_fixed, hist, c->counter);
+}
+
+// Eq. SSPRK3 with U^n = U, result written back to U
+static void rk3(mpmc_ctx* c, cudaStream_t s, double* U, double dt, uint32_t* tape, double* hist) {
+  dt_gamma(c, s, U, dt, -1.0, hist);
+  const long long nf = c->nface_total;
+  stage(c, s, U, U, 1.0, 0.0, 1.0, c->U1, nullptr, tape);
+  prim(c, s, c->U1, nullptr);
+  stage(c, s, U, c->U1, 0.75, 0.25, 0.25, c->U2, nullptr, tape ? tape + nf : nullptr);
+  prim(c, s, c->U2, nullptr);
+  stage(c, s, U, c->U2, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, U, nullptr, tape ? tape + 2 * nf : nullptr);
+}
+
+extern "C" int mpmc_rhs(mpmc_ctx* c, const double* U, double* dUdt, const mpmc_stage* st, uint32_t* flags) {
+  if (!c || !U || !dUdt) return fail(c, MPMC_INVALID_ARG, "rhs: null argument");
+  const double* Un = st && st->U_n ? st->U_n : U;
+  const double rk0 = st ? st->rk0 : 1.0, rk1 = st ? st->rk1 : 0.0, rk2 = st ? st->rk2 : 1.0;
+  const double dt = st ? st->dt : 0.0, G = st ? st->Gamma : -1.0;
+  cudaStream_t s = c->stream;
+  // dt / Gamma from U^n (always run so that the prim pass of U_n also
+  // validates it); then the primitive cache of U
+  dt_gamma(c, s, Un, dt, G, nullptr);
+  if (Un != U) prim(c, s, U, nullptr);
+  stage(c, s, Un, U, rk0, rk1, rk2, nullptr, dUdt, flags);
+  c->faces_done += c->nface_total;
+  return check_launch(c, "rhs");
+}
+
+extern "C" int mpmc_rk_step(mpmc_ctx* c, double* U, double dt, uint32_t* tape) {
+  if (!c || !U) return fail(c, MPMC_INVALID_ARG, "rk_step: null argument");
+  rk3(c, c->stream, U, dt, tape, nullptr);
+  c->faces_done += 3ull * c->nface_total;
+  return check_launch(c, "rk_step");
+}
+
+extern "C" int mpmc_step_n(mpmc_ctx* c, double* U, int n, double* dt_out) {
+  if (!c || !U || n < 0) return fail(c, MPMC_INVALID_ARG, "step_n: bad argument");
+  if (n == 0) return MPMC_OK;
+  cudaStream_t s = c->stream;
+  if (!c->gexec || c->g_U != U || c->g_hist != dt_out) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return fail(c, MPMC_CUDA_ERROR, "step_n: capture begin failed");
+    c->capturing = true;
+    rk3(c, c->cap, U, 0.0, nullptr, dt_out);
+    c->capturing = false;
+    if (cudaStreamEndCapture(c->cap, &graph) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, MPMC_CUDA_ERROR, "step_n: capture failed");
+    }
+    cudaError_t e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->gexec = nullptr;
+      return fail(c, MPMC_CUDA_ERROR, "step_n: instantiate: %s", cudaGetErrorString(e));
+    }
+    c->g_U = U;
+    c->g_hist = dt_out;
+  }
+  if (dt_out) cudaMemsetAsync(c->counter, 0, sizeof(int), s);
+  for (int i = 0; i < n; ++i) {
+    cudaError_t e = cudaGraphLaunch(c->gexec, s);
+    if (e != cudaSuccess) return fail(c, MPMC_CUDA_ERROR, "step_n: graph launch: %s", cudaGetErrorString(e));
+  }
+  c->faces_done += 3ull * c->nface_total * (unsigned long long)n;
+  return check_launch(c, "step_n");
+}
+
+extern "C" int mpmc_step_n_host(mpmc_ctx* c, double* U_host, int n) {
+  if (!c || !U_host || n < 0) return fail(c, MPMC_INVALID_ARG, "step_n_host: bad argument");
+  const size_t bytes = (size_t)c->P.nv * c->P.ncell * sizeof(double);
+  if (!c->Ud) {
+    int rc = alloc(c, (void**)&c->Ud, bytes);
+    if (rc) return rc;
+  }
+  cudaStream_t s = c->stream;
+  if (cudaMemcpyAsync(c->Ud, U_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(c, MPMC_CUDA_ERROR, "step_n_host: copy in");
+  int rc = mpmc_step_n(c, c->Ud, n, nullptr);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(U_host, c->Ud, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return fail(c, MPMC_CUDA_ERROR, "step_n_host: copy out");
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(c, MPMC_CUDA_ERROR, "step_n_host: sync");
+  return MPMC_OK;
+}
+
+extern "C" int mpmc_dt_gamma(mpmc_ctx* c, const double* U, double* out_dev) {
+  if (!c || !U || !out_dev) return fail(c, MPMC_INVALID_ARG, "dt_gamma: null argument");
+  dt_gamma(c, c->stream, U, 0.0, -1.0, nullptr);
+  cudaMemcpyAsync(out_dev, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  return check_launch(c, "dt_gamma");
+}
+
+extern "C" int mpmc_rhs_adjoint(mpmc_ctx* c, const double* U, const mpmc_stage* st, const uint32_t* tape,
+                                const double* lam_dUdt, double* lam_U) {
+  (void)U; (void)st; (void)tape; (void)lam_dUdt; (void)lam_U;
+  return fail(c, MPMC_INVALID_ARG, "rhs_adjoint: not available in this build");
+}
+
+extern "C" int mpmc_get_status(mpmc_ctx* c, int reset) {
+  if (!c) return MPMC_INVALID_ARG;
+  int st = 0;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, MPMC_CUDA_ERROR, "get_status: sync");
+  cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (reset) cudaMemset(c->status, 0, sizeof(int));
+  return st;
+}
+
+extern "C" int mpmc_get_stats(mpmc_ctx* c, mpmc_stats* out, int reset) {
+  if (!c || !out) return MPMC_INVALID_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, MPMC_CUDA_ERROR, "get_stats: sync");
+  unsigned long long s[8];
+  cudaMemcpy(s, c->stats, sizeof(s), cudaMemcpyDeviceToHost);
+  out->faces = c->faces_done;
+  out->hllc_fallback = s[1];
+  out->cdi_dropped = s[2];
+  out->theta_p = s[3];
+  out->theta_t = s[4];
+  out->ylim = s[5];
+  if (reset) {
+    cudaMemset(c->stats, 0, sizeof(s));
+    c->faces_done = 0;
+  }
+  return MPMC_OK;
+}
+
+extern "C" int mpmc_set_profiling(mpmc_ctx* c, int enable) {
+  if (!c) return MPMC_INVALID_ARG;
+  c->profiling = enable != 0;
+  return MPMC_OK;
+}
+
+extern "C" int mpmc_get_profile(mpmc_ctx* c, double* ms, uint64_t* launches, int reset) {
+  if (!c) return MPMC_INVALID_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, MPMC_CUDA_ERROR, "get_profile: sync");
+  for (auto& m : c->marks) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) {
+      c->prof_ms[m.fam] += t;
+      c->prof_n[m.fam] += 1;
+    }
+    c->pool.push_back(m.a);
+    c->pool.push_back(m.b);
+  }
+  c->marks.clear();
+  for (int f = 0; f < 4; ++f) {
+    if (ms) ms[f] = c->prof_ms[f];
+    if (launches) launches[f] = c->prof_n[f];
+    if (reset) {
+      c->prof_ms[f] = 0.0;
+      c->prof_n[f] = 0;
+    }
+  }
+  return MPMC_OK;
+}

@@ -1,0 +1,431 @@
+// Device building blocks of the MPMC right-hand side (arXiv 2504.14063):
+// kernel parameters, boundary index mapping, NASG mixture EOS, WENO5-Z,
+// HLLC, admissibility.  Everything here is FP64; the mixed-precision path
+// adds its own FP32 pieces in mpmc_mixed.cuh.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpmc {
+
+constexpr int MAXS = 4;
+// round-off allowance on partial densities in every admissibility test
+constexpr double YTOL = 1e-14;
+// threshold below which a phase (or species) counts as absent
+constexpr double ABSENT = 1e-300;
+// |grad psi| below which the interface normal of the regularization is zero
+constexpr double GTOL = 1e-8;
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_ZEROGRAD = 2, BC_INFLOW = 3 };
+enum { ST_OK = 0, ST_INADMISSIBLE = 3, ST_EOS_NO_CONVERGE = 4 };
+enum : uint32_t {
+  F_THETA_T_L = 1u << 0, F_THETA_T_R = 1u << 1, F_THETA_P_L = 1u << 2, F_THETA_P_R = 1u << 3,
+  F_HLLC_FALLBACK = 1u << 4, F_CDI_DROPPED = 1u << 5, F_YLIM_L = 1u << 6, F_YLIM_R = 1u << 7
+};
+
+// Everything a kernel needs, passed by value (lives in the constant bank).
+struct KParams {
+  int dim, ns, nv;
+  int n[3];
+  long long ncell;
+  double dx, inv_dx;
+  int bc_lo[3], bc_hi[3];
+  int phase[MAXS];
+  double cv[MAXS], gam[MAXS], q[MAXS], b[MAXS], pinf[MAXS], W[MAXS], mu[MAXS], Sc[MAXS];
+  double Rk[MAXS], cp[MAXS];
+  double wilke[MAXS][MAXS];  // (W_i / W_j) Phi_ij of Wilke's rule (gas species)
+  double weno_eps;
+  int cdi, diffusion, pos_limiter, two_phase, has_inflow;
+  double cdi_eps, cdi_gamma, phi_min, psi_delta, cfl, mu_liquid, sharp0;
+  // primitive cache: field f of cell c at Wc[f * wstride + c]; slot ncell
+  // holds the inflow state
+  int wT, wP, wRho, wA, wY, wU, wPhi0, wPsi, wYrho, wHrho, wXr, wB, nW;
+  long long wstride;
+};
+
+// ---------------------------------------------------------------------------
+// boundary ghosts by index mapping.  Directions are resolved in order x, y,
+// z: periodic and zero-gradient remap the coordinate, a wall mirrors it and
+// negates that velocity component, an inflow face replaces the cell by the
+// inflow state (later walls still mirror it).
+struct CRef {
+  long long idx;   // cell index, or ncell for the inflow state
+  unsigned flip;   // bit d: negate u_d / m_d
+};
+
+__device__ __forceinline__ CRef map_cell(const KParams& P, int i, int j, int k) {
+  int c[3] = {i, j, k};
+  unsigned flip = 0u;
+  bool inflow = false;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (d < P.dim) {
+      const int n = P.n[d];
+      if (c[d] < 0 || c[d] >= n) {
+        const bool lo = c[d] < 0;
+        const int bc = lo ? P.bc_lo[d] : P.bc_hi[d];
+        const int l = lo ? -1 - c[d] : c[d] - n;
+        if (bc == BC_PERIODIC) {
+          c[d] = lo ? c[d] + n : c[d] - n;
+        } else if (bc == BC_WALL) {
+          c[d] = lo ? l : n - 1 - l;
+          flip ^= 1u << d;
+        } else if (bc == BC_ZEROGRAD) {
+          c[d] = lo ? 0 : n - 1;
+        } else {
+          inflow = true;
+          flip = 0u;
+        }
+      }
+    }
+  }
+  CRef r;
+  r.flip = flip;
+  r.idx = inflow ? P.ncell : ((long long)c[2] * P.n[1] + c[1]) * P.n[0] + c[0];
+  return r;
+}
+
+__device__ __forceinline__ double sgn_flip(unsigned flip, int d) { return (flip >> d) & 1u ? -1.0 : 1.0; }
+
+// conserved vector of a mapped cell (U has ncell entries per component; the
+// inflow state comes from Uin)
+template <int NS, int D>
+__device__ __forceinline__ void load_U(const KParams& P, const double* __restrict__ U,
+                                       const double* __restrict__ Uin, CRef r, double* out) {
+  constexpr int NV = NS + D + 1;
+  if (r.idx == P.ncell) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = Uin[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = U[(long long)v * P.ncell + r.idx];
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) out[NS + d] *= sgn_flip(r.flip, d);
+}
+
+__device__ __forceinline__ double wget(const KParams& P, const double* __restrict__ Wc, int f, CRef r) {
+  return Wc[(long long)f * P.wstride + r.idx];
+}
+
+// ---------------------------------------------------------------------------
+// NASG EOS per species (Eq. NASG_EOS)
+__device__ __forceinline__ double v_k(const KParams& P, int k, double p, double T) {
+  return P.Rk[k] * T / (p + P.pinf[k]) + P.b[k];
+}
+__device__ __forceinline__ double e_k(const KParams& P, int k, double p, double T) {
+  return P.cv[k] * T * (p + P.gam[k] * P.pinf[k]) / (p + P.pinf[k]) + P.q[k];
+}
+__device__ __forceinline__ double h_k(const KParams& P, int k, double p, double T) {
+  return P.cp[k] * T + P.b[k] * p + P.q[k];
+}
+
+// common-pressure residual of NASG_T1 = NASG_T2 and its derivative
+template <int NS>
+__device__ __forceinline__ void pt_residual(const KParams& P, const double* Y, double Ep, double Cv, double x,
+                                            double& f, double& df) {
+  f = -Cv;
+  df = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    if (Y[k] != 0.0) {
+      const double w = Y[k] * P.Rk[k] * (Ep - P.pinf[k]);
+      const double r = 1.0 / (x + P.pinf[k]);
+      f += w * r;
+      df -= w * r * r;
+    }
+  }
+}
+
+// p-T equilibrium from mass fractions, specific internal energy and volume
+// (Eqs. NASG_T1, NASG_T2, NASG_P).  One stiffened component (or several
+// sharing Pinf): the quadratic of NASG_P, larger root in cancellation-free
+// form, linear root without gas.  Several distinct Pinf: safeguarded Newton
+// on the common-pressure residual, started from the quadratic with a
+// Y-weighted Pinf, at most 100 iterations.
+// Non-contracting arithmetic for the inversion U -> (P, T).  The pressure of
+// a stiff liquid (P << Pinf) is the small difference of terms ~ gamma Pinf,
+// so it inherits the rounding of every operation before it; evaluating in
+// a fixed order without fused multiply-adds makes it reproducible.
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+
+// mixture decode of a conserved vector: rho, Y, |u|^2, specific e, v
+template <int NS, int D>
+__device__ __forceinline__ void decode(const double* U, double& rho, double* Y, double* u, double& e, double& v) {
+  rho = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) rho = add_(rho, U[k]);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) Y[k] = U[k] / rho;
+  double ke = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    u[d] = d < D ? U[NS + d] / rho : 0.0;
+    ke = add_(ke, mul_(u[d], u[d]));
+  }
+  e = sub_(U[NS + D] / rho, mul_(0.5, ke));
+  v = 1.0 / rho;
+}
+
+// p-T equilibrium from mass fractions, specific internal energy and volume
+// (Eqs. NASG_T1, NASG_T2, NASG_P).  One stiffened component (or several
+// sharing Pinf): the quadratic of NASG_P, larger root in cancellation-free
+// form, linear root without gas.  Several distinct Pinf: safeguarded Newton
+// on the common-pressure residual, started from the quadratic with a
+// Y-weighted Pinf, at most 100 iterations.
+template <int NS>
+__device__ int pt_equilibrium(const KParams& P, const double* Y, double e, double v, double& p, double& T) {
+  double Cv = 0.0, q = 0.0, b = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    Cv = add_(Cv, mul_(Y[k], P.cv[k]));
+    q = add_(q, mul_(Y[k], P.q[k]));
+    b = add_(b, mul_(Y[k], P.b[k]));
+  }
+  const double em = sub_(e, q), vm = sub_(v, b);
+  int st = ST_OK;
+  if (!(em > 0.0) || !(vm > 0.0)) st = ST_INADMISSIBLE;
+  const double Ep = em / vm;
+  double pl = -1.0, pmin = 1e300, Rg = 0.0, Rl = 0.0, wpl = 0.0;
+  bool multi = false, gas = false;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    if (Y[k] > 0.0) {
+      pmin = fmin(pmin, P.pinf[k]);
+      if (P.pinf[k] > 0.0) {
+        if (pl < 0.0) pl = P.pinf[k];
+        else if (P.pinf[k] != pl) multi = true;
+        Rl = add_(Rl, mul_(Y[k], P.Rk[k]));
+        wpl += Y[k] * P.Rk[k] * P.pinf[k];
+      } else {
+        gas = true;
+        Rg = add_(Rg, mul_(Y[k], P.Rk[k]));
+      }
+    }
+  }
+  if (!multi) {
+    if (pl < 0.0) {
+      p = mul_(Ep, Rg) / Cv;
+    } else if (!gas) {
+      p = sub_(sub_(mul_(Ep, Rl), mul_(pl, Cv)), mul_(pl, Rl)) / Cv;
+    } else {
+      const double a1 = Cv;
+      const double a2 = sub_(sub_(mul_(Ep, add_(Rg, Rl)), mul_(pl, Cv)), mul_(pl, Rl));
+      const double a3 = mul_(mul_(Ep, pl), Rg);
+      const double sq = sqrt(add_(mul_(a2, a2), mul_(mul_(4.0, a1), a3)));
+      p = a2 >= 0.0 ? add_(a2, sq) / mul_(2.0, a1) : mul_(2.0, a3) / sub_(sq, a2);
+    }
+  } else {
+    const double lo = -pmin;
+    double hi = fmax(fabs(Ep), 1.0) + fabs(lo);
+    double f, df;
+    int it = 0;
+    pt_residual<NS>(P, Y, Ep, Cv, hi, f, df);
+    while (f >= 0.0 && it < 200) {
+      hi *= 2.0;
+      pt_residual<NS>(P, Y, Ep, Cv, hi, f, df);
+      ++it;
+    }
+    double a = lo, bb = hi;
+    // initial guess: the quadratic with the liquids merged into one
+    const double pe = wpl / Rl;
+    const double a2 = Ep * (Rg + Rl) - pe * Cv - pe * Rl, a3 = Ep * pe * Rg;
+    double x = gas ? (a2 >= 0.0 ? (a2 + sqrt(a2 * a2 + 4.0 * Cv * a3)) / (2.0 * Cv)
+                                : 2.0 * a3 / (sqrt(a2 * a2 + 4.0 * Cv * a3) - a2))
+                   : (Ep * Rl - pe * Cv - pe * Rl) / Cv;
+    if (!(x > a && x < bb)) x = 0.5 * (a + bb);
+    bool conv = false;
+    for (it = 0; it < 100; ++it) {
+      pt_residual<NS>(P, Y, Ep, Cv, x, f, df);
+      if (f > 0.0) a = x;
+      else bb = x;
+      if (f == 0.0) { conv = true; break; }
+      double xn = x - f / df;
+      if (!(xn > a && xn < bb)) {
+        const double da = a - lo, db = bb - lo;
+        xn = (da > 0.0 && db > 16.0 * da) ? lo + sqrt(da * db) : 0.5 * (a + bb);
+      }
+      const double dxn = fabs(xn - x);
+      x = xn;
+      if (dxn <= 4.5e-16 * fabs(x) || !(bb > a)) {
+        pt_residual<NS>(P, Y, Ep, Cv, x, f, df);
+        x = x - f / df;   // one more Newton step at full accuracy
+        conv = true;
+        break;
+      }
+    }
+    if (!conv && st == ST_OK) st = ST_EOS_NO_CONVERGE;
+    p = x;
+  }
+  double den = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+    if (Y[k] != 0.0)
+      den = add_(den, mul_(mul_(Y[k], P.cv[k]), add_(p, mul_(P.gam[k], P.pinf[k]))) / add_(p, P.pinf[k]));
+  T = em / den;
+  return st;
+}
+
+// forward EOS at (P, T, Y): density (Amagat), specific internal energy and
+// the sound speed of Eq. SpeedOfSound with the NASG alpha, beta
+template <int NS>
+__device__ __forceinline__ void eos_forward(const KParams& P, const double* Y, double p, double T, double& rho,
+                                            double& e, double& a, double& alpha, double& beta) {
+  double v = 0.0, cp = 0.0, sa = 0.0, sb = 0.0;
+  e = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    if (Y[k] != 0.0) {
+      const double pp = p + P.pinf[k];
+      const double r = 1.0 / pp;
+      const double RT = P.Rk[k] * T;
+      v += Y[k] * (RT * r + P.b[k]);
+      e += Y[k] * (P.cv[k] * T * (p + P.gam[k] * P.pinf[k]) * r + P.q[k]);
+      cp += Y[k] * P.cp[k];
+      sa += Y[k] * P.Rk[k] * r;
+      sb += Y[k] * RT * r * r;
+    }
+  }
+  rho = 1.0 / v;
+  alpha = rho * sa;
+  beta = rho * sb;
+  a = sqrt(cp / (rho * beta * cp - alpha * alpha * T));
+}
+
+// ---------------------------------------------------------------------------
+// WENO5-Z (Borges et al. 2008), exponent 1: value at the right face of v2
+__device__ __forceinline__ double weno5z(double v0, double v1, double v2, double v3, double v4, double eps) {
+  const double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
+  const double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) * (1.0 / 6.0);
+  const double q2 = (2.0 * v2 + 5.0 * v3 - v4) * (1.0 / 6.0);
+  double t = v0 - 2.0 * v1 + v2, s = v0 - 4.0 * v1 + 3.0 * v2;
+  const double b0 = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  t = v1 - 2.0 * v2 + v3;
+  s = v1 - v3;
+  const double b1 = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  t = v2 - 2.0 * v3 + v4;
+  s = 3.0 * v2 - 4.0 * v3 + v4;
+  const double b2 = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  const double tau = fabs(b0 - b2);
+  // alpha_k = d_k (1 + tau/(b_k+eps)) brought to one common denominator
+  const double c0 = b0 + eps, c1 = b1 + eps, c2 = b2 + eps;
+  const double a0 = 0.1 * (c0 + tau) * c1 * c2;
+  const double a1 = 0.6 * (c1 + tau) * c0 * c2;
+  const double a2 = 0.3 * (c2 + tau) * c0 * c1;
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// ---------------------------------------------------------------------------
+// HLLC (Appendix B)
+template <int NS>
+struct State {
+  double rho, rhoY[NS], u[3], m[3], p, E, a;
+};
+
+template <int NS, int D>
+__device__ __forceinline__ void hllc(int d, const State<NS>& L, const State<NS>& R, double* F) {
+  const double ub = 0.5 * (L.u[d] + R.u[d]), ab = 0.5 * (L.a + R.a);
+  const double sL = fmin(ub - ab, L.u[d] - L.a);
+  const double sR = fmax(ub + ab, R.u[d] + R.a);
+  const double sm = fmin(0.0, sL), sp = fmax(0.0, sR);
+  const double dL = sL - L.u[d], dR = sR - R.u[d];
+  const double ss = (R.p - L.p + L.rho * L.u[d] * dL - R.rho * R.u[d] * dR) / (L.rho * dL - R.rho * dR);
+  // sign(0) = 0: both branches with weight 1/2
+  const double wl = ss > 0.0 ? 1.0 : (ss < 0.0 ? 0.0 : 0.5);
+  const double wr = 1.0 - wl;
+  const double fL = dL / (sL - ss), fR = dR / (sR - ss);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const double FL = L.rhoY[k] * L.u[d], FR = R.rhoY[k] * R.u[d];
+    F[k] = wl * (FL + sm * (fL * L.rhoY[k] - L.rhoY[k])) + wr * (FR + sp * (fR * R.rhoY[k] - R.rhoY[k]));
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const double FL = L.rho * L.u[d] * L.u[j] + (j == d ? L.p : 0.0);
+    const double FR = R.rho * R.u[d] * R.u[j] + (j == d ? R.p : 0.0);
+    const double UsL = fL * L.rho * (j == d ? ss : L.u[j]);
+    const double UsR = fR * R.rho * (j == d ? ss : R.u[j]);
+    F[NS + j] = wl * (FL + sm * (UsL - L.m[j])) + wr * (FR + sp * (UsR - R.m[j]));
+  }
+  {
+    const double FL = L.u[d] * (L.E + L.p), FR = R.u[d] * (R.E + R.p);
+    const double UsL = fL * (L.E + (ss - L.u[d]) * (L.rho * ss + L.p / dL));
+    const double UsR = fR * (R.E + (ss - R.u[d]) * (R.rho * ss + R.p / dR));
+    F[NS + D] = wl * (FL + sm * (UsL - L.E)) + wr * (FR + sp * (UsR - R.E));
+  }
+}
+
+// face-side state from reconstructed (Y, u, P, T) (steps 4-5 of Sec. 3.1.3)
+template <int NS>
+__device__ __forceinline__ void state_from_primitive(const KParams& P, const double* Y, const double* u, double p,
+                                                     double T, State<NS>& s) {
+  double e, al, be;
+  eos_forward<NS>(P, Y, p, T, s.rho, e, s.a, al, be);
+  double ke = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    s.u[d] = u[d];
+    s.m[d] = s.rho * u[d];
+    ke += u[d] * u[d];
+  }
+#pragma unroll
+  for (int k = 0; k < NS; ++k) s.rhoY[k] = s.rho * Y[k];
+  s.p = p;
+  s.E = s.rho * (e + 0.5 * ke);
+}
+
+// Eqs. PositivityReqs1/2 on a conserved vector, division free:
+// rhoY_k >= -YTOL rho, rho > 0, 1 - sum rhoY_k b_k > 0,
+// rho E - |m|^2/2 - rho sum rhoY_k q_k > 0
+template <int NS, int D>
+__device__ __forceinline__ bool admissible(const KParams& P, const double* U) {
+  double rho = 0.0, sb = 0.0, sq = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    rho += U[k];
+    sb += U[k] * P.b[k];
+    sq += U[k] * P.q[k];
+  }
+  bool ok = rho > 0.0 && (1.0 - sb) > 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) ok = ok && (U[k] >= -YTOL * rho);
+  double mm = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) mm += U[NS + d] * U[NS + d];
+  return ok && (rho * U[NS + D] - 0.5 * mm - rho * sq > 0.0);
+}
+
+// mass-fraction limiter of Sec. 3.3.1 on one face side (Yc: cell values)
+template <int NS>
+__device__ __forceinline__ bool y_limiter(double* Y, const double* Yc) {
+  bool active = false;
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+    if (Y[k] < 0.0) {
+      Y[k] = 0.0;
+      active = true;
+    }
+  double sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) sum += Y[k];
+  if (sum != 1.0) {
+    const bool over = sum > 1.0;
+    double dd[NS], Sig = 0.0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      dd[k] = (over ? fmin(Y[k], Yc[k]) : fmax(Y[k], Yc[k])) - Y[k];
+      Sig += dd[k];
+    }
+    if (Sig != 0.0) {
+      const double f = (1.0 - sum) / Sig;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) Y[k] += f * dd[k];
+      active = true;
+    }
+  }
+  return active;
+}
+
+}  // namespace mpmc

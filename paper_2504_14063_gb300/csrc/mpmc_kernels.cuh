@@ -1,0 +1,577 @@
+// FP64 kernels of the MPMC stage (arXiv 2504.14063), templated on the
+// species count NS and the dimension D, and their launchers.
+//   k_init   : primitive fields -> U (Eq. NASG_EOS, Amagat mixing)
+//   k_prim   : U -> primitive cache (Sec. 2.2-2.3, Eq. SpeedOfSound, the CDI
+//              and diffusion ingredients) + CFL / Gamma block maxima
+//   k_face   : one face of direction d: Godunov approach of Sec. 3.1.3 with
+//              limiters (Sec. 3.3), HLLC (App. B), CDI (Sec. 3.2), diffusion
+//   k_update : divergence (Eq. DiscreteGoverningEquations) + SSP-RK
+//              combination (Eq. SSPRK3)
+#pragma once
+#include "mpmc_device.cuh"
+#include "mpmc_ops.h"
+
+namespace mpmc {
+
+constexpr int FACE_THREADS = 128;
+constexpr int CELL_THREADS = 256;
+
+// ---------------------------------------------------------------------------
+template <int NS, int D>
+__global__ void __launch_bounds__(CELL_THREADS) k_init(const KParams P, const double* __restrict__ prim,
+                                                       double* __restrict__ U, long long n) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const double p = prim[(long long)(NS + D) * n + c];
+  const double T = prim[(long long)(NS + D + 1) * n + c];
+  double rho = 0.0, e = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const double a = prim[(long long)k * n + c];
+    double ry = 0.0;
+    if (a != 0.0) {
+      ry = a / v_k(P, k, p, T);
+      e += ry * e_k(P, k, p, T);
+    }
+    U[(long long)k * n + c] = ry;
+    rho += ry;
+  }
+  double ke = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double u = prim[(long long)(NS + d) * n + c];
+    U[(long long)(NS + d) * n + c] = rho * u;
+    ke += rho * u * u;
+  }
+  U[(long long)(NS + D) * n + c] = e + 0.5 * ke;
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block maxima of two non-negative values -> atomicMax on their bit patterns
+// (IEEE order of non-negative doubles equals the order of their bits).
+__device__ __forceinline__ void block_max2(double a, double b, unsigned long long* red) {
+  __shared__ double sa[32], sb[32];
+  a = warp_max(a);
+  b = warp_max(b);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sa[wid] = a;
+    sb[wid] = b;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    a = lane < nw ? sa[lane] : 0.0;
+    b = lane < nw ? sb[lane] : 0.0;
+    a = warp_max(a);
+    b = warp_max(b);
+    if (lane == 0) {
+      atomicMax(red + 0, (unsigned long long)__double_as_longlong(a));
+      atomicMax(red + 1, (unsigned long long)__double_as_longlong(b));
+    }
+  }
+}
+
+template <int NS, int D>
+__global__ void __launch_bounds__(CELL_THREADS)
+    k_prim(const KParams P, const double* __restrict__ U, const double* __restrict__ Uin, double* __restrict__ Wc,
+           unsigned long long* __restrict__ red, int* __restrict__ status) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double smax = 0.0, gmax = 0.0;
+  if (c < P.ncell + P.has_inflow) {
+    constexpr int NV = NS + D + 1;
+    double Uc[NV];
+    if (c == P.ncell) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uc[v] = Uin[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uc[v] = U[(long long)v * P.ncell + c];
+    }
+    const long long ws = P.wstride;
+    double rho, Y[NS], u[3], e, irho;
+    decode<NS, D>(Uc, rho, Y, u, e, irho);
+    int st = rho > 0.0 ? ST_OK : ST_INADMISSIBLE;
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+      if (Uc[k] < -YTOL * rho) st = ST_INADMISSIBLE;
+    double p, T;
+    const int st2 = pt_equilibrium<NS>(P, Y, e, irho, p, T);
+    if (st == ST_OK) st = st2;
+    double r2, e2, a, al, be;
+    eos_forward<NS>(P, Y, p, T, r2, e2, a, al, be);
+    Wc[P.wT * ws + c] = T;
+    Wc[P.wP * ws + c] = p;
+    Wc[P.wRho * ws + c] = rho;
+    Wc[P.wA * ws + c] = a;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) Wc[(P.wY + k) * ws + c] = Y[k];
+#pragma unroll
+    for (int d = 0; d < D; ++d) Wc[(P.wU + d) * ws + c] = u[d];
+
+    double mu = 0.0;
+    if (P.cdi || P.diffusion) {
+      double phi[2], Yp[2];
+#pragma unroll
+      for (int ph = 0; ph < 2; ++ph) {
+        double f = 0.0, hr = 0.0, yp = 0.0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+          if (P.phase[k] == ph) {
+            yp += Y[k];
+            if (Uc[k] != 0.0) {
+              // the oracle's operation order without contraction
+              const double vk = add_(mul_(P.Rk[k], T) / add_(p, P.pinf[k]), P.b[k]);
+              const double hk = add_(add_(mul_(P.cp[k], T), mul_(P.b[k], p)), P.q[k]);
+              f = add_(f, mul_(Uc[k], vk));
+              hr = add_(hr, mul_(Uc[k], hk));
+            }
+          }
+        phi[ph] = f;
+        Yp[ph] = yp;
+        if (P.cdi) {
+          const bool present = yp >= ABSENT;
+          Wc[(P.wHrho + ph) * ws + c] = present ? hr / f : 0.0;
+#pragma unroll
+          for (int k = 0; k < NS; ++k)
+            if (P.phase[k] == ph) Wc[(P.wYrho + k) * ws + c] = present ? Uc[k] / f : 0.0;
+        }
+      }
+      if (P.cdi) {
+        Wc[P.wPhi0 * ws + c] = phi[0];
+        Wc[P.wPsi * ws + c] = P.cdi_eps * log((phi[0] + P.psi_delta) / (phi[1] + P.psi_delta));
+      }
+      if (P.diffusion) {
+        // phase viscosities: liquid constant, gas by Wilke's rule
+        double mup[2];
+        mup[0] = P.mu_liquid;
+        double num = 0.0;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+          if (P.phase[i] != 1) continue;
+          double den = 0.0;
+#pragma unroll
+          for (int j = 0; j < NS; ++j)
+            if (P.phase[j] == 1) den += Y[j] * P.wilke[i][j];
+          if (den > 0.0) num += Y[i] * P.mu[i] / den;
+        }
+        mup[1] = Yp[1] >= ABSENT ? num : 0.0;
+        mu = phi[0] * mup[0] + phi[1] * mup[1];
+#pragma unroll
+        for (int ph = 0; ph < 2; ++ph) {
+          double sY = 0.0;
+#pragma unroll
+          for (int j = 0; j < NS; ++j)
+            if (P.phase[j] == ph) sY += Y[j] / P.W[j];
+          const bool present = Yp[ph] >= ABSENT && sY >= ABSENT;
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            if (P.phase[k] != ph) continue;
+            double xr = 0.0, B = 0.0;
+            if (present) {
+              xr = (Y[k] / P.W[k]) / sY;
+              const double WcWp = P.W[k] * sY / Yp[ph];
+              const double rho_p = rho * Yp[ph] / phi[ph];
+              B = WcWp * (mup[ph] / (rho_p * P.Sc[k]));
+            }
+            Wc[(P.wXr + k) * ws + c] = xr;
+            Wc[(P.wB + k) * ws + c] = B;
+          }
+        }
+      }
+    }
+    if (st != ST_OK) atomicMax(status, st);
+    if (c < P.ncell) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const double ud = fabs(u[d]);
+        smax = fmax(smax, (ud + a) * P.inv_dx);
+        gmax = fmax(gmax, ud);
+      }
+      if (P.diffusion) smax = fmax(smax, 4.0 * mu / rho * (P.inv_dx * P.inv_dx));
+    }
+  }
+  if (red) block_max2(smax, gmax, red);
+}
+
+
+// ---------------------------------------------------------------------------
+template <int NS, int D>
+__global__ void __launch_bounds__(FACE_THREADS)
+    k_face(const KParams P, const int d, const double* __restrict__ Wc, const double* __restrict__ Un,
+           const double* __restrict__ Uk, const double* __restrict__ Uin, const double* __restrict__ scal,
+           const double rk0, const double rk1, const double rk2, double* __restrict__ F,
+           uint32_t* __restrict__ flags, unsigned long long* __restrict__ stats) {
+  constexpr int NV = NS + D + 1;
+  const int f0 = P.n[0] + (d == 0), f1 = P.n[1] + (d == 1), f2 = P.n[2] + (d == 2);
+  const long long nf = (long long)f0 * f1 * f2;
+  const long long fid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (fid >= nf) return;
+  int fc[3];
+  fc[0] = (int)(fid % f0);
+  const long long rr = fid / f0;
+  fc[1] = (int)(rr % f1);
+  fc[2] = (int)(rr / f1);
+  int ci[3] = {fc[0], fc[1], fc[2]};
+  ci[d] -= 1;  // the cell on the low side of the face
+  const double dt = scal[0], Gamma = scal[1];
+  const long long ws = P.wstride;
+
+  CRef cr[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    int cc[3] = {ci[0], ci[1], ci[2]};
+    cc[d] += j - 2;
+    cr[j] = map_cell(P, cc[0], cc[1], cc[2]);
+  }
+  const CRef ri = cr[2], rj = cr[3];
+  uint32_t fl = 0u;
+
+  // step 1: averaged conserved state on the face, its EOS, the scalars of
+  // the characteristic matrices (Appendix A)
+  double X, c, ic;
+  {
+    double Ui[NV], Uj[NV];
+    load_U<NS, D>(P, Uk, Uin, ri, Ui);
+    load_U<NS, D>(P, Uk, Uin, rj, Uj);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Ui[v] = mul_(0.5, add_(Ui[v], Uj[v]));
+    double rho, Y[NS], uu[3], e, vol;
+    decode<NS, D>(Ui, rho, Y, uu, e, vol);
+    double p, T, r2, e2, a, al, be;
+    pt_equilibrium<NS>(P, Y, e, vol, p, T);
+    eos_forward<NS>(P, Y, p, T, r2, e2, a, al, be);
+    X = (rho * a * a * be - 1.0) / (al * a * a * rho);
+    c = a * rho;
+    ic = 1.0 / c;
+  }
+
+  // steps 2-3: project, WENO5-Z both sides, back to physical space
+  double YL[NS], YR[NS], uL[3] = {0.0, 0.0, 0.0}, uR[3] = {0.0, 0.0, 0.0}, PL, PR, TL, TR;
+  const double eps = P.weno_eps;
+  {
+    double w1[6], w5[6], w6[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const double T = wget(P, Wc, P.wT, cr[j]);
+      const double p = wget(P, Wc, P.wP, cr[j]);
+      const double un = wget(P, Wc, P.wU + d, cr[j]) * sgn_flip(cr[j].flip, d);
+      w1[j] = T - X * p;
+      w5[j] = (0.5 * c) * un + 0.5 * p;
+      w6[j] = (-0.5 * c) * un + 0.5 * p;
+    }
+    const double w1L = weno5z(w1[0], w1[1], w1[2], w1[3], w1[4], eps);
+    const double w1R = weno5z(w1[5], w1[4], w1[3], w1[2], w1[1], eps);
+    const double w5L = weno5z(w5[0], w5[1], w5[2], w5[3], w5[4], eps);
+    const double w5R = weno5z(w5[5], w5[4], w5[3], w5[2], w5[1], eps);
+    const double w6L = weno5z(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
+    const double w6R = weno5z(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+    TL = w1L + X * w5L + X * w6L;
+    TR = w1R + X * w5R + X * w6R;
+    uL[d] = ic * w5L + (-ic) * w6L;
+    uR[d] = ic * w5R + (-ic) * w6R;
+    PL = w5L + w6L;
+    PR = w5R + w6R;
+  }
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    double y[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) y[j] = wget(P, Wc, P.wY + k, cr[j]);
+    YL[k] = weno5z(y[0], y[1], y[2], y[3], y[4], eps);
+    YR[k] = weno5z(y[5], y[4], y[3], y[2], y[1], eps);
+  }
+#pragma unroll
+  for (int t = 0; t < D; ++t) {
+    if (t == d) continue;
+    double y[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) y[j] = wget(P, Wc, P.wU + t, cr[j]) * sgn_flip(cr[j].flip, t);
+    uL[t] = weno5z(y[0], y[1], y[2], y[3], y[4], eps);
+    uR[t] = weno5z(y[5], y[4], y[3], y[2], y[1], eps);
+  }
+
+  // cell values of the two face neighbours
+  double Yi[NS], Yj[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    Yi[k] = wget(P, Wc, P.wY + k, ri);
+    Yj[k] = wget(P, Wc, P.wY + k, rj);
+  }
+  const double Ti = wget(P, Wc, P.wT, ri), Tj = wget(P, Wc, P.wT, rj);
+  const double Pi = wget(P, Wc, P.wP, ri), Pj = wget(P, Wc, P.wP, rj);
+
+  // interpolation limiters (Sec. 3.3.1)
+  if (P.pos_limiter) {
+    if (y_limiter<NS>(YL, Yi)) fl |= F_YLIM_L;
+    if (y_limiter<NS>(YR, Yj)) fl |= F_YLIM_R;
+    if (!(TL > 0.0)) { TL = Ti; fl |= F_THETA_T_L; }
+    if (!(TR > 0.0)) { TR = Tj; fl |= F_THETA_T_R; }
+    bool okL = true, okR = true;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      if (YL[k] > 0.0 && !(PL + P.pinf[k] > 0.0)) okL = false;
+      if (YR[k] > 0.0 && !(PR + P.pinf[k] > 0.0)) okR = false;
+    }
+    if (!okL) { PL = Pi; fl |= F_THETA_P_L; }
+    if (!okR) { PR = Pj; fl |= F_THETA_P_R; }
+  }
+
+  // steps 4-6: face EOS, conserved face states, HLLC
+  double Fx[NV];
+  {
+    State<NS> sL, sR;
+    state_from_primitive<NS>(P, YL, uL, PL, TL, sL);
+    state_from_primitive<NS>(P, YR, uR, PR, TR, sR);
+    hllc<NS, D>(d, sL, sR, Fx);
+  }
+
+  // flux limiter (Sec. 3.3.2): pseudo-updates of both cells
+  double Uni[NV], Unj[NV], Uki[NV], Ukj[NV];
+  const double lam = 2.0 * D * rk2 * dt * P.inv_dx;
+  if (P.pos_limiter || P.cdi) {
+    load_U<NS, D>(P, Un, Uin, ri, Uni);
+    load_U<NS, D>(P, Un, Uin, rj, Unj);
+    load_U<NS, D>(P, Uk, Uin, ri, Uki);
+    load_U<NS, D>(P, Uk, Uin, rj, Ukj);
+  }
+  auto passes = [&](const double* Ft) {
+    double Ti_[NV], Tj_[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double base_i = rk0 * Uni[v] + rk1 * Uki[v];
+      const double base_j = rk0 * Unj[v] + rk1 * Ukj[v];
+      Ti_[v] = base_i - lam * Ft[v];
+      Tj_[v] = base_j + lam * Ft[v];
+    }
+    return admissible<NS, D>(P, Ti_) && admissible<NS, D>(P, Tj_);
+  };
+  if (P.pos_limiter && !passes(Fx)) {
+    State<NS> si, sj;
+    si.rho = wget(P, Wc, P.wRho, ri);
+    sj.rho = wget(P, Wc, P.wRho, rj);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      si.rhoY[k] = Uki[k];
+      sj.rhoY[k] = Ukj[k];
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      si.u[t] = t < D ? wget(P, Wc, P.wU + t, ri) * sgn_flip(ri.flip, t) : 0.0;
+      sj.u[t] = t < D ? wget(P, Wc, P.wU + t, rj) * sgn_flip(rj.flip, t) : 0.0;
+      si.m[t] = t < D ? Uki[NS + t] : 0.0;
+      sj.m[t] = t < D ? Ukj[NS + t] : 0.0;
+    }
+    si.p = Pi;
+    sj.p = Pj;
+    si.E = Uki[NS + D];
+    sj.E = Ukj[NS + D];
+    si.a = wget(P, Wc, P.wA, ri);
+    sj.a = wget(P, Wc, P.wA, rj);
+    hllc<NS, D>(d, si, sj, Fx);
+    fl |= F_HLLC_FALLBACK;
+  }
+
+  // interface regularization (Sec. 3.2), KEEP split form, with its limiter
+  if (P.cdi && P.two_phase) {
+    bool pres_i[2] = {false, false}, pres_j[2] = {false, false};
+    {
+      double ypi[2] = {0.0, 0.0}, ypj[2] = {0.0, 0.0};
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        ypi[P.phase[k]] += Yi[k];
+        ypj[P.phase[k]] += Yj[k];
+      }
+#pragma unroll
+      for (int ph = 0; ph < 2; ++ph) {
+        pres_i[ph] = ypi[ph] >= ABSENT;
+        pres_j[ph] = ypj[ph] >= ABSENT;
+      }
+    }
+    if ((pres_i[0] || pres_j[0]) && (pres_i[1] || pres_j[1])) {
+      const double ceps = P.cdi_eps;
+      const double psi_i = wget(P, Wc, P.wPsi, ri), psi_j = wget(P, Wc, P.wPsi, rj);
+      const double dphi = (wget(P, Wc, P.wPhi0, rj) - wget(P, Wc, P.wPhi0, ri)) * P.inv_dx;
+      double g[3] = {0.0, 0.0, 0.0};
+      g[d] = (psi_j - psi_i) * P.inv_dx;
+#pragma unroll
+      for (int t = 0; t < D; ++t) {
+        if (t == d) continue;
+        int a0[3] = {ci[0], ci[1], ci[2]}, a1[3] = {ci[0], ci[1], ci[2]};
+        int b0[3] = {ci[0], ci[1], ci[2]}, b1[3] = {ci[0], ci[1], ci[2]};
+        a0[t] += 1;
+        a1[t] -= 1;
+        b0[t] += 1;
+        b1[t] -= 1;
+        b0[d] += 1;
+        b1[d] += 1;
+        const double pip = wget(P, Wc, P.wPsi, map_cell(P, a0[0], a0[1], a0[2]));
+        const double pim = wget(P, Wc, P.wPsi, map_cell(P, a1[0], a1[1], a1[2]));
+        const double pjp = wget(P, Wc, P.wPsi, map_cell(P, b0[0], b0[1], b0[2]));
+        const double pjm = wget(P, Wc, P.wPsi, map_cell(P, b1[0], b1[1], b1[2]));
+        g[t] = 0.5 * ((pip - pim) * (0.5 * P.inv_dx) + (pjp - pjm) * (0.5 * P.inv_dx));
+      }
+      const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+      const double nd = gn >= GTOL ? g[d] / gn : 0.0;
+      const double th = tanh((0.5 * (psi_i + psi_j)) / (2.0 * ceps));
+      const double ahat0 = Gamma * (ceps * dphi - 0.25 * (1.0 - th * th - P.sharp0) * nd);
+      double Fdi[NV], Rtot = 0.0, hR = 0.0;
+#pragma unroll
+      for (int ph = 0; ph < 2; ++ph) {
+        const double ahat = ph == 0 ? ahat0 : -ahat0;
+        const bool pi = pres_i[ph], pj = pres_j[ph];
+        auto keep = [&](double a, double b) { return pi && pj ? 0.5 * (a + b) : (pi ? a : (pj ? b : 0.0)); };
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          if (P.phase[k] != ph) continue;
+          const double R = -keep(wget(P, Wc, P.wYrho + k, ri), wget(P, Wc, P.wYrho + k, rj)) * ahat;
+          Fdi[k] = R;
+          Rtot += R;
+        }
+        hR -= keep(wget(P, Wc, P.wHrho + ph, ri), wget(P, Wc, P.wHrho + ph, rj)) * ahat;
+      }
+      double kb = 0.0;
+#pragma unroll
+      for (int t = 0; t < D; ++t) {
+        const double ui = wget(P, Wc, P.wU + t, ri) * sgn_flip(ri.flip, t);
+        const double uj = wget(P, Wc, P.wU + t, rj) * sgn_flip(rj.flip, t);
+        kb += ui * uj;
+        Fdi[NS + t] = 0.5 * (ui + uj) * Rtot;
+      }
+      Fdi[NS + D] = 0.5 * kb * Rtot + hR;
+      double Ft[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Ft[v] = Fx[v] + Fdi[v];
+      if (P.pos_limiter && !passes(Ft)) {
+        fl |= F_CDI_DROPPED;
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fx[v] = Ft[v];
+      }
+    }
+  }
+
+  // species diffusion (Eq. SpeciesMassDiffusion), not limited
+  if (P.diffusion) {
+    const double rb = 0.5 * (wget(P, Wc, P.wRho, ri) + wget(P, Wc, P.wRho, rj));
+    double Jh = 0.0;
+#pragma unroll
+    for (int ph = 0; ph < 2; ++ph) {
+      double Yp = 0.0, S = 0.0, Bf[NS], G[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        Bf[k] = 0.0;
+        G[k] = 0.0;
+        if (P.phase[k] != ph) continue;
+        Yp += 0.5 * (Yi[k] + Yj[k]);
+        Bf[k] = 0.5 * (wget(P, Wc, P.wB + k, ri) + wget(P, Wc, P.wB + k, rj));
+        G[k] = (wget(P, Wc, P.wXr + k, rj) - wget(P, Wc, P.wXr + k, ri)) * P.inv_dx;
+        S += Bf[k] * G[k];
+      }
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        if (P.phase[k] != ph) continue;
+        const double J = -rb * (Yp * Bf[k] * G[k] - 0.5 * (Yi[k] + Yj[k]) * S);
+        Fx[k] += J;
+        Jh += J * (0.5 * (h_k(P, k, Pi, Ti) + h_k(P, k, Pj, Tj)));
+      }
+    }
+    Fx[NS + D] += Jh;
+  }
+
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[(long long)v * nf + fid] = Fx[v];
+  if (flags) flags[fid] = fl;
+  if (stats && fl) {
+    if (fl & F_HLLC_FALLBACK) atomicAdd(stats + 1, 1ull);
+    if (fl & F_CDI_DROPPED) atomicAdd(stats + 2, 1ull);
+    if (fl & (F_THETA_P_L | F_THETA_P_R)) atomicAdd(stats + 3, 1ull);
+    if (fl & (F_THETA_T_L | F_THETA_T_R)) atomicAdd(stats + 4, 1ull);
+    if (fl & (F_YLIM_L | F_YLIM_R)) atomicAdd(stats + 5, 1ull);
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int NS, int D>
+__global__ void __launch_bounds__(CELL_THREADS)
+    k_update(const KParams P, const double* __restrict__ Un, const double* __restrict__ Uk,
+             const double* __restrict__ F0, const double* __restrict__ F1, const double* __restrict__ F2,
+             const double* __restrict__ scal, const double rk0, const double rk1, const double rk2,
+             double* __restrict__ Uout, double* __restrict__ dUdt, int* __restrict__ status) {
+  constexpr int NV = NS + D + 1;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.ncell) return;
+  const int n0 = P.n[0], n1 = P.n[1];
+  const int i = (int)(c % n0);
+  const long long r = c / n0;
+  const int j = (int)(r % n1), k = (int)(r / n1);
+  const double* Fd[3] = {F0, F1, F2};
+  long long fm[3], fp[3], nf[3];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int f0 = n0 + (d == 0), f1 = n1 + (d == 1), f2 = P.n[2] + (d == 2);
+    nf[d] = (long long)f0 * f1 * f2;
+    fm[d] = ((long long)k * f1 + j) * f0 + i;
+    fp[d] = fm[d] + (d == 0 ? 1 : (d == 1 ? f0 : (long long)f0 * f1));
+  }
+  const double dt = scal[0];
+  double Uo[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double L = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) L -= (Fd[d][(long long)v * nf[d] + fp[d]] - Fd[d][(long long)v * nf[d] + fm[d]]) * P.inv_dx;
+    if (dUdt) dUdt[(long long)v * P.ncell + c] = L;
+    Uo[v] = rk0 * Un[(long long)v * P.ncell + c] + rk1 * Uk[(long long)v * P.ncell + c] + (rk2 * dt) * L;
+  }
+  if (Uout) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Uout[(long long)v * P.ncell + c] = Uo[v];
+    if (!admissible<NS, D>(P, Uo)) atomicMax(status, (int)ST_INADMISSIBLE);
+  }
+}
+
+// ---------------------------------------------------------------------------
+inline unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <int NS, int D>
+struct Impl {
+  static void init(const KParams& P, cudaStream_t s, const double* prim, double* U, long long n) {
+    if (n > 0) k_init<NS, D><<<nblocks(n, CELL_THREADS), CELL_THREADS, 0, s>>>(P, prim, U, n);
+  }
+  static void prim(const KParams& P, cudaStream_t s, const double* U, const double* Uin, double* Wc,
+                   unsigned long long* red, int* status) {
+    k_prim<NS, D><<<nblocks(P.ncell + P.has_inflow, CELL_THREADS), CELL_THREADS, 0, s>>>(P, U, Uin, Wc, red,
+                                                                                            status);
+  }
+  static void face(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* Un, const double* Uk,
+                   const double* Uin, const double* scal, double rk0, double rk1, double rk2, double* F,
+                   uint32_t* flags, unsigned long long* stats) {
+    long long nf = 1;
+    for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
+    k_face<NS, D><<<nblocks(nf, FACE_THREADS), FACE_THREADS, 0, s>>>(P, d, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F,
+                                                                       flags, stats);
+  }
+  static void update(const KParams& P, cudaStream_t s, const double* Un, const double* Uk, double* const* F,
+                     const double* scal, double rk0, double rk1, double rk2, double* Uout, double* dUdt,
+                     int* status) {
+    k_update<NS, D><<<nblocks(P.ncell, CELL_THREADS), CELL_THREADS, 0, s>>>(
+        P, Un, Uk, F[0], D > 1 ? F[1] : F[0], D > 2 ? F[2] : F[0], scal, rk0, rk1, rk2, Uout, dUdt, status);
+  }
+  static Ops ops() {
+    Ops o;
+    o.init = &init;
+    o.prim = &prim;
+    o.face = &face;
+    o.update = &update;
+    return o;
+  }
+};
+
+}  // namespace mpmc

@@ -119,6 +119,13 @@ def tanh_profile(dist, dx):
     return 0.5 * (1.0 + np.tanh(dist / (2.0 * dx)))
 
 
+def floored(phi, floor):
+    """Phase volume fraction kept within [floor, 1 - floor].  With floor =
+    phi_min the far field starts at the equilibrium of the regularization
+    term (Eq. MPMC_ACDI), which relaxes phase fractions towards phi_min."""
+    return np.clip(phi, floor, 1.0 - floor) if floor > 0.0 else phi
+
+
 def normal_shock(mach, gamma, W, P1, T1):
     """Post-shock (P, T, u) of a shock of Mach `mach` moving into gas at rest."""
     Rg = R_UNIVERSAL / W
@@ -208,7 +215,7 @@ def sod(n=200, gamma=1.4, W=0.029):
 
 
 def shock_bubble_2d(nx=1024, ny=512, seed=0, mach=1.5, bubble_radius=None, liquid_cols=None,
-                    shock_col=None, bubble_center=None, cdi=1, diffusion=0, nsteps=2000):
+                    shock_col=None, bubble_center=None, cdi=1, diffusion=0, nsteps=2000, phase_floor=1e-8):
     """Mach 1.5 planar shock in air moving +x into a helium bubble whose
     interface carries 8 seeded Fourier modes (peak amplitude one cell), with a
     stiffened liquid layer against a reflecting wall at x = Lx.  Inflow at
@@ -227,7 +234,7 @@ def shock_bubble_2d(nx=1024, ny=512, seed=0, mach=1.5, bubble_radius=None, liqui
     th = np.arctan2(Y - cy, X - cx)
     d_bub = fourier_radius(th, R, amps) - np.hypot(X - cx, Y - cy)
     phi_b = tanh_profile(d_bub, 1.0)
-    phi_l = tanh_profile(X - (nx - lc), 1.0)
+    phi_l = floored(tanh_profile(X - (nx - lc), 1.0), phase_floor)
     P1, T1 = 1e5, 300.0
     P2, T2, u2 = normal_shock(mach, AIR.gamma, AIR.W, P1, T1)
     post = X < sc
@@ -239,7 +246,7 @@ def shock_bubble_2d(nx=1024, ny=512, seed=0, mach=1.5, bubble_radius=None, liqui
     pr[4, 0] = 0.0
     pr[5, 0] = np.where(post, P2, P1)
     pr[6, 0] = np.where(post, T2, T1)
-    inflow = np.array([1.0, 0.0, 0.0, u2, 0.0, P2, T2])
+    inflow = np.array([1.0 - phase_floor, 0.0, phase_floor, u2, 0.0, P2, T2])
     m = Model(cdi=cdi, diffusion=diffusion)
     return Problem("shock_bubble_2d", 2, (nx, ny, 1), dx, sp, m, pr,
                    bc_lo=(BC_INFLOW, BC_WALL, BC_PERIODIC), bc_hi=(BC_WALL, BC_WALL, BC_PERIODIC),
@@ -312,7 +319,7 @@ def solenoidal_velocity(rng, shape, kmax, urms):
 
 
 def droplet_field_3d(n=256, ndrops=32, seed=2, rmin=8.0, rmax=20.0, urms=50.0, nsteps=500,
-                     cdi=1, diffusion=1):
+                     cdi=1, diffusion=1, phase_floor=1e-8):
     """Periodic box with seed-placed droplets of a two-liquid mixture
     (composition by volume U[0.2, 0.8] per droplet) in an air/helium gas whose
     helium fraction is 0.1 +- 0.05 (smooth random); solenoidal random
@@ -354,6 +361,7 @@ def droplet_field_3d(n=256, ndrops=32, seed=2, rmin=8.0, rmax=20.0, urms=50.0, n
     he = he[0]
     he = 0.1 + 0.05 * he / np.abs(he).max()
     u = solenoidal_velocity(rng, (n, n, n), 4 if n >= 16 else 1, urms)
+    phi = floored(phi, phase_floor)
     pr = _prim(4, 3, (n, n, n))
     pr[0] = phi * fa
     pr[1] = phi * (1.0 - fa)
@@ -367,7 +375,7 @@ def droplet_field_3d(n=256, ndrops=32, seed=2, rmin=8.0, rmax=20.0, urms=50.0, n
                    nsteps=nsteps)
 
 
-def shock_droplet_3d(n=512, seed=4, mach=2.0, nsteps=200, cdi=1, diffusion=1):
+def shock_droplet_3d(n=512, seed=4, mach=2.0, nsteps=200, cdi=1, diffusion=1, phase_floor=1e-8):
     """Mach 2 shock in air onto a stiffened-liquid droplet (radius 48 cells at
     (160, 256, 256) for n = 512) whose surface carries a seeded perturbation
     spanning the spherical harmonics of degree <= 4 (peak one cell); a
@@ -388,7 +396,7 @@ def shock_droplet_3d(n=512, seed=4, mach=2.0, nsteps=200, cdi=1, diffusion=1):
     coef = rng.standard_normal(len(mons))
     pert = sum(cf * nrm[0] ** a * nrm[1] ** b * nrm[2] ** cc for cf, (a, b, cc) in zip(coef, mons))
     pert = pert / np.abs(pert).max()
-    phi_l = tanh_profile(48.0 * s + pert - r, 1.0)
+    phi_l = floored(tanh_profile(48.0 * s + pert - r, 1.0), phase_floor)
     cg = np.array([320.0, 256.0, 256.0]) * s
     rg = np.sqrt((X - cg[0]) ** 2 + (Yg - cg[1]) ** 2 + (Z - cg[2]) ** 2)
     he = 0.5 * tanh_profile(32.0 * s - rg, 1.0)
@@ -402,7 +410,7 @@ def shock_droplet_3d(n=512, seed=4, mach=2.0, nsteps=200, cdi=1, diffusion=1):
     pr[3] = np.where(post, u2, 0.0)
     pr[6] = np.where(post, P2, P1)
     pr[7] = np.where(post, T2, T1)
-    inflow = np.array([1.0, 0.0, 0.0, u2, 0.0, 0.0, P2, T2])
+    inflow = np.array([1.0 - phase_floor, 0.0, phase_floor, u2, 0.0, 0.0, P2, T2])
     return Problem("shock_droplet_3d", 3, (n, n, n), dx, [AIR, HELIUM, LIQUID_SG],
                    Model(cdi=cdi, diffusion=diffusion), pr,
                    bc_lo=(BC_INFLOW, BC_PERIODIC, BC_PERIODIC), bc_hi=(BC_ZEROGRAD, BC_PERIODIC, BC_PERIODIC),

@@ -1,0 +1,75 @@
+"""The C ABI library loads without a GPU, exports every function that
+include/mpmc.h declares, and the binding's struct layouts match the header
+(sizes and offsets printed by a gcc-compiled probe of the header)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HDR = os.path.join(ROOT, "include", "mpmc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2504_14063_gb300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def declared_functions():
+    txt = open(HDR).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpmc_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mpmc_init_state", "mpmc_rhs", "mpmc_rk_step", "mpmc_step_n", "mpmc_rhs_adjoint"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_layouts_match_header(tmp_path):
+    from paper_2504_14063_gb300 import binding as b
+    probe = tmp_path / "probe.c"
+    probe.write_text(f"""
+#include <stdio.h>
+#include <stddef.h>
+#include "{HDR}"
+int main(void) {{
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(mpmc_grid), sizeof(mpmc_eos), sizeof(mpmc_model),
+         sizeof(mpmc_stage), sizeof(mpmc_stats));
+  printf("%zu %zu %zu %zu\\n", offsetof(mpmc_grid, inflow), offsetof(mpmc_eos, Sc),
+         offsetof(mpmc_model, precision), offsetof(mpmc_stage, Gamma));
+  return 0;
+}}
+""")
+    exe = tmp_path / "probe"
+    subprocess.check_call(["gcc", "-o", str(exe), str(probe)])
+    out = subprocess.check_output([str(exe)]).decode().split()
+    sizes = [int(x) for x in out[:5]]
+    offs = [int(x) for x in out[5:]]
+    assert sizes == [ctypes.sizeof(t) for t in (b.Grid, b.Eos, b.ModelC, b.StageC, b.StatsC)]
+    assert offs == [b.Grid.inflow.offset, b.Eos.Sc.offset, b.ModelC.precision.offset, b.StageC.Gamma.offset]
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu(lib):
+    """Host-side validation happens before any CUDA call."""
+    from paper_2504_14063_gb300 import binding as b
+    from paper_2504_14063_gb300 import workloads as W
+    p = W.interface_advection_1d(n=16)
+    g, e, m = b.structs_from_problem(p)
+    h = ctypes.c_void_p()
+    e.n_species = 9
+    assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
+    e.n_species = 2
+    g.n[0] = 2
+    assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
+    assert h.value is None
