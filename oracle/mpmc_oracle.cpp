@@ -913,9 +913,13 @@ struct Solver {
        * field gives round-off, whose normalized direction is noise) */
       R nd = val(gn) >= GTOL ? g[d] / gn : R(0.0);
       R psib = 0.5 * (ci.psi + cj.psi);
-      R th = tanh(psib / (2.0 * eps));
+      /* 1 - tanh^2(x) written as 1 / cosh^2(x): the same quantity without the
+       * cancellation that 1 - tanh^2 suffers where the phase fraction is
+       * near the phi_min floor and the bracket below nearly vanishes */
+      R ch = cosh(psib / (2.0 * eps));
+      R sech2 = 1.0 / (ch * ch);
       /* Eq. SkewSymmetricSplitting_Regularization_Expanded */
-      R ahat0 = Gamma * (eps * dphi - 0.25 * (1.0 - th * th - sharp0) * nd);
+      R ahat0 = Gamma * (eps * dphi - 0.25 * (sech2 - sharp0) * nd);
       for (int ph = 0; ph < 2; ++ph) {
         R ahat = ph == 0 ? ahat0 : -ahat0;
         /* KEEP face interpolation of a phase quantity.  reading: where the

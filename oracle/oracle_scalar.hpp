@@ -12,6 +12,7 @@
 
 namespace orc {
 
+using std::cosh;
 using std::fabs;
 using std::log;
 using std::sqrt;
@@ -90,6 +91,12 @@ template <int N> inline Dual<N> log(const Dual<N>& a) {
 template <int N> inline Dual<N> tanh(const Dual<N>& a) {
   Dual<N> r; r.v = std::tanh(a.v);
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * (1.0 - r.v * r.v);
+  return r;
+}
+template <int N> inline Dual<N> cosh(const Dual<N>& a) {
+  Dual<N> r; r.v = std::cosh(a.v);
+  const double sh = std::sinh(a.v);
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * sh;
   return r;
 }
 template <int N> inline Dual<N> fabs(const Dual<N>& a) { return a.v < 0.0 ? -a : a; }
