@@ -419,8 +419,10 @@ __global__ void __launch_bounds__(FACE_THREADS)
       }
       const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
       const double nd = gn >= GTOL ? g[d] / gn : 0.0;
-      const double th = tanh((0.5 * (psi_i + psi_j)) / (2.0 * ceps));
-      const double ahat0 = Gamma * (ceps * dphi - 0.25 * (1.0 - th * th - P.sharp0) * nd);
+      // 1 - tanh^2 as 1 / cosh^2 (no cancellation near the phi_min floor)
+      const double ch = cosh((0.5 * (psi_i + psi_j)) / (2.0 * ceps));
+      const double sech2 = 1.0 / (ch * ch);
+      const double ahat0 = Gamma * (ceps * dphi - 0.25 * (sech2 - P.sharp0) * nd);
       double Fdi[NV], Rtot = 0.0, hR = 0.0;
 #pragma unroll
       for (int ph = 0; ph < 2; ++ph) {

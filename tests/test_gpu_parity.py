@@ -240,7 +240,7 @@ def test_100_steps_shock_bubble_2d(mp):
 
 
 def test_100_steps_droplet_field_3d(mp):
-    _steps_parity(mp, W.droplet_field_3d(n=20, ndrops=3, seed=2, rmin=3.0, rmax=5.0), 100)
+    _steps_parity(mp, W.droplet_field_3d(n=24, ndrops=3, seed=2, rmin=4.0, rmax=6.0, urms=20.0), 100)
 
 
 def test_100_steps_shock_bubble_2d_cdi(mp):
