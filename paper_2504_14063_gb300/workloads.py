@@ -278,42 +278,39 @@ def _with_amplitudes(p, n, s, amps):
     return p
 
 
-def _smooth_random_field(rng, shape, kmax, ncomp=1):
-    """Sum of random Fourier modes with |k| <= kmax (integer wavenumbers)."""
+def _wavenumbers(shape):
     nz, ny, nx = shape
-    zz, yy, xx = np.meshgrid(np.arange(nz) / nz, np.arange(ny) / ny, np.arange(nx) / nx, indexing="ij")
+    kz = np.fft.fftfreq(nz) * nz
+    ky = np.fft.fftfreq(ny) * ny
+    kx = np.fft.rfftfreq(nx) * nx
+    return np.meshgrid(kz, ky, kx, indexing="ij")   # each [nz, ny, nx//2+1]
+
+
+def _smooth_random_field(rng, shape, kmax, ncomp=1):
+    """Periodic random fields made of the Fourier modes with |k| <= kmax
+    (integer wavenumbers), seeded Gaussian amplitudes, synthesised by FFT."""
+    KZ, KY, KX = _wavenumbers(shape)
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    mask = (k2 > 0) & (k2 <= kmax * kmax)
     out = np.zeros((ncomp,) + tuple(shape))
-    ks = [(a, b, c) for a in range(-kmax, kmax + 1) for b in range(-kmax, kmax + 1) for c in range(0, kmax + 1)
-          if 0 < a * a + b * b + c * c <= kmax * kmax]
-    for (a, b, c) in ks:
-        ph = 2.0 * np.pi * (a * xx + b * yy + c * zz)
-        for q in range(ncomp):
-            amp = rng.standard_normal(2)
-            out[q] += amp[0] * np.cos(ph) + amp[1] * np.sin(ph)
-    return out, ks
+    for q in range(ncomp):
+        A = (rng.standard_normal(KX.shape) + 1j * rng.standard_normal(KX.shape)) * mask
+        out[q] = np.fft.irfftn(A, s=shape, axes=(0, 1, 2))
+    return out, int(mask.sum())
 
 
 def solenoidal_velocity(rng, shape, kmax, urms):
-    """Seeded divergence-free random field: each mode's amplitude is projected
-    normal to its wavevector; scaled to the requested rms speed."""
-    nz, ny, nx = shape
-    zz, yy, xx = np.meshgrid(np.arange(nz) / nz, np.arange(ny) / ny, np.arange(nx) / nx, indexing="ij")
-    u = np.zeros((3,) + tuple(shape))
-    for a in range(-kmax, kmax + 1):
-        for b in range(-kmax, kmax + 1):
-            for c in range(0, kmax + 1):
-                k2 = a * a + b * b + c * c
-                if k2 == 0 or k2 > kmax * kmax:
-                    continue
-                kv = np.array([a, b, c], dtype=np.float64)
-                A = rng.standard_normal(3)
-                Bv = rng.standard_normal(3)
-                A -= kv * (A @ kv) / k2
-                Bv -= kv * (Bv @ kv) / k2
-                ph = 2.0 * np.pi * (a * xx + b * yy + c * zz)
-                cs, sn = np.cos(ph), np.sin(ph)
-                for q in range(3):
-                    u[q] += A[q] * cs + Bv[q] * sn
+    """Seeded divergence-free random field: Gaussian mode amplitudes with
+    |k| <= kmax, projected normal to their wavevector, synthesised by FFT and
+    scaled to the requested rms speed.  Component order (u_x, u_y, u_z)."""
+    KZ, KY, KX = _wavenumbers(shape)
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    mask = (k2 > 0) & (k2 <= kmax * kmax)
+    A = [(rng.standard_normal(KX.shape) + 1j * rng.standard_normal(KX.shape)) * mask for _ in range(3)]
+    kv = (KX, KY, KZ)
+    dot = sum(kv[q] * A[q] for q in range(3))
+    inv = np.where(k2 > 0, 1.0 / np.where(k2 > 0, k2, 1.0), 0.0)
+    u = np.stack([np.fft.irfftn(A[q] - kv[q] * dot * inv, s=shape, axes=(0, 1, 2)) for q in range(3)])
     rms = np.sqrt((u ** 2).sum(axis=0).mean())
     return u * (urms / rms)
 
@@ -347,16 +344,20 @@ def droplet_field_3d(n=256, ndrops=32, seed=2, rmin=8.0, rmax=20.0, urms=50.0, n
     comp = rng.uniform(0.2, 0.8, len(centers))
     g = np.arange(n) + 0.5
     Z, Yg, X = np.meshgrid(g, g, g, indexing="ij")
-    phi = np.zeros((n, n, n))
+    # each cell takes the profile and the liquid composition of the droplet
+    # whose surface is nearest, so that trace liquid in the gas carries a
+    # continuous composition
+    best = np.full((n, n, n), np.inf)
     fa = np.zeros((n, n, n))
     for c, r, ca in zip(centers, radii, comp):
         dxv = np.abs(X - c[0]); dxv = np.minimum(dxv, n - dxv)
         dyv = np.abs(Yg - c[1]); dyv = np.minimum(dyv, n - dyv)
         dzv = np.abs(Z - c[2]); dzv = np.minimum(dzv, n - dzv)
-        ph = tanh_profile(r - np.sqrt(dxv ** 2 + dyv ** 2 + dzv ** 2), 1.0)
-        take = ph > phi
-        phi = np.where(take, ph, phi)
+        dist = np.sqrt(dxv ** 2 + dyv ** 2 + dzv ** 2) - r
+        take = dist < best
+        best = np.where(take, dist, best)
         fa = np.where(take, ca, fa)
+    phi = tanh_profile(-best, 1.0)
     he, _ = _smooth_random_field(rng, (n, n, n), 2)
     he = he[0]
     he = 0.1 + 0.05 * he / np.abs(he).max()

@@ -171,7 +171,11 @@ def test_rhs_parity_sod_single_species(mp):
 
 
 def test_rhs_parity_shock_bubble_2d(mp):
-    rhs_parity(mp, W.shock_bubble_2d(nx=100, ny=52, seed=1), pre_steps=4)
+    """From a state after the shock has entered the bubble: earlier, the
+    helium rate is only the residual of the far-field phi_min balance of
+    Eq. MPMC_ACDI (two ~4e-8 terms that nearly cancel), which has no
+    meaningful relative precision."""
+    rhs_parity(mp, W.shock_bubble_2d(nx=100, ny=52, seed=1), pre_steps=60)
 
 
 def test_rhs_parity_periodic_diffusion_cdi_2d(mp):
