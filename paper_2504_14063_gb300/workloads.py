@@ -106,6 +106,10 @@ class Problem:
         return self.ns + self.dim + 1
 
     def __post_init__(self):
+        # private copies: callers may tune a problem's species or model
+        # without touching the module's material table
+        self.species = [dataclasses.replace(s) for s in self.species]
+        self.model = dataclasses.replace(self.model)
         if self.model.cdi_eps <= 0.0:
             self.model.cdi_eps = self.dx
         self.prim = np.ascontiguousarray(self.prim, dtype=np.float64)
