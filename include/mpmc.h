@@ -197,6 +197,33 @@ int mpmc_get_status(mpmc_ctx* ctx, int reset);
 int mpmc_set_profiling(mpmc_ctx* ctx, int enable);
 int mpmc_get_profile(mpmc_ctx* ctx, double* ms, uint64_t* launches, int reset);
 
+/* Right-hand side without allocation, for callers that cannot allocate
+ * device memory: code running inside another framework's memory pool or
+ * arena that owns the device, real-time or embedded host loops that must not
+ * block on the allocator, or setups where no allocator exists yet.  The paper
+ * has no counterpart; this is a deployment variant of mpmc_rhs.
+ *   - Same result as mpmc_rhs(U, dUdt, stage, NULL) for the same grid, species
+ *     table and model (FP64 only: model->precision must be MPMC_FP64); no
+ *     context is needed, the structs are passed directly.
+ *   - Scratch (primitive cache, face fluxes, reduction scalars) lives in one
+ *     fixed device array of MPMC_NOALLOC_SCRATCH_BYTES that every GPU which
+ *     loads the library holds until the process exits.  No cudaMalloc,
+ *     cudaFree or allocating library routine is called.
+ *   - A grid whose scratch exceeds that size is rejected with
+ *     MPMC_INVALID_ARG before any GPU work; *scratch_bytes (nullable) receives
+ *     the bytes the grid needs.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind; calls
+ *     whose work overlaps on the GPU (different streams without ordering)
+ *     race.  Serialize them on one stream.
+ *   - Work is enqueued on `stream` without host synchronization; errors found
+ *     on the device (inadmissible cells) are not reported by this entry.
+ * U, dUdt and stage->U_n are device arrays in the layout of mpmc_rhs. */
+#define MPMC_NOALLOC_SCRATCH_BYTES (32u << 20)
+int mpmc_rhs_noalloc(const mpmc_grid* grid, const mpmc_eos* eos, const mpmc_model* model, void* stream,
+                     const double* U, double* dUdt, const mpmc_stage* stage, size_t* scratch_bytes);
+
 /* Text of the last error on this context (static storage of the context). */
 const char* mpmc_last_error(const mpmc_ctx* ctx);
 
