@@ -171,6 +171,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--compare-steps", type=int, default=100)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -233,6 +235,56 @@ def main():
     achieved = fpf * faces_per_launch / (face_ms / face_n / 1e3) / 1e12
     launches = int(sum(n for _, n in prof.values()))
 
+    # ---- mixed precision: same workload, same timing; error vs FP64 --------
+    mixed = None
+    if not args.no_mixed:
+        ctxm = mp.Context(p, precision=mp.MIXED)
+        Um = ctxm.init_state(torch.from_numpy(p.prim))
+        for _ in range(args.warmup):
+            ctxm.rk_step(Um)
+        torch.cuda.synchronize()
+        ctxm.profile(reset=True)
+        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        ctxm.set_profiling(True)
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            evm[k][0].record()
+            ctxm.rk_step(Um)
+            evm[k][1].record()
+        torch.cuda.synchronize()
+        ctxm.set_profiling(False)
+        mstat = ctxm.status()
+        mprof = ctxm.profile(reset=True)
+        tm = sum(a.elapsed_time(b) for a, b in evm) / 1e3
+        if world > 1:
+            t = torch.tensor([tm], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tm = float(t.item())
+        # accuracy: 100 steps from the initial state, FP64 path vs mixed path
+        A = ctx.init_state(torch.from_numpy(p.prim))
+        B = ctxm.init_state(torch.from_numpy(p.prim))
+        ctx.step_n(A, args.compare_steps)
+        ctxm.step_n(B, args.compare_steps)
+        Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
+        ns, D = p.ns, p.dim
+        rho1, rhoi = np.abs(Ah[:ns].sum(0)).sum(), np.abs(Ah[:ns].sum(0)).max()
+        names = [f"rhoY_{s.name}" for s in p.species] + [f"m_{'xyz'[d]}" for d in range(D)] + ["E"]
+        l1, li = {}, {}
+        for v in range(Ah.shape[0]):
+            s1 = rho1 if v < ns else (rho1 * 1000.0 if v < ns + D else np.abs(Ah[v]).sum())
+            si = rhoi if v < ns else (rhoi * 1000.0 if v < ns + D else np.abs(Ah[v]).max())
+            l1[names[v]] = float(np.abs(Bh[v] - Ah[v]).sum() / s1)
+            li[names[v]] = float(np.abs(Bh[v] - Ah[v]).max() / si)
+        mixed = {"value": world * p.ncells * args.steps / tm, "unit": UNIT, "ms_per_step": 1e3 * tm / args.steps,
+                 "speedup_vs_fp64": (world * p.ncells * args.steps / tm) / value,
+                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in mprof.items()},
+                 "error_vs_fp64": {"steps": args.compare_steps,
+                                   "norm": "state-scaled (partial densities by rho, momenta by rho*1000 m/s, "
+                                           "energy by E)", "l1": l1, "linf": li},
+                 "status": mstat}
+        del ctxm, Um, A, B
+
     # ---- end to end through the host-buffer entry --------------------------
     H = U.cpu().pin_memory()
     ctx.step_n_host(H, 1)
@@ -262,6 +314,8 @@ def main():
                                  ("hllc_fallback", "cdi_dropped", "theta_p", "theta_t", "ylim")},
             "status": status,
         }
+        if mixed is not None:
+            line["mixed"] = mixed
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
         print(json.dumps(line), flush=True)

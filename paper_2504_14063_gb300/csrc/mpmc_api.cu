@@ -243,10 +243,11 @@ extern "C" int mpmc_create(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_m
   P.wstride = P.ncell + 1;
   c->precision = m->precision;
 
+  const bool mixed = m->precision == MPMC_MIXED;
   switch (D) {
-    case 1: c->ops = ops_fp64_d1(ns); break;
-    case 2: c->ops = ops_fp64_d2(ns); break;
-    default: c->ops = ops_fp64_d3(ns); break;
+    case 1: c->ops = mixed ? ops_mixed_d1(ns) : ops_fp64_d1(ns); break;
+    case 2: c->ops = mixed ? ops_mixed_d2(ns) : ops_fp64_d2(ns); break;
+    default: c->ops = mixed ? ops_mixed_d3(ns) : ops_fp64_d3(ns); break;
   }
   if (!c->ops.face) {
     delete c;

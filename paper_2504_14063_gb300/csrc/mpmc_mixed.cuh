@@ -1,0 +1,773 @@
+// Mixed-precision kernels of the MPMC stage: reconstruction, face EOS,
+// HLLC, regularization and diffusion fluxes in FP32 with FP32 accumulation;
+// the cell p-T equilibrium inversion, the positivity-limiter pseudo-updates
+// and the conservative RK accumulation in FP64.
+//
+// Uniform fields stay exactly uniform: every stencil value is reconstructed
+// as its deviation from the face's left cell (W_j - W_i, zero where P, T, u
+// are uniform), and the HLLC contact speed is written as u_L plus a term
+// that vanishes when P and u are continuous.
+#pragma once
+#include "mpmc_device.cuh"
+#include "mpmc_ops.h"
+
+namespace mpmc {
+namespace mx {
+
+constexpr int FACE_THREADS = 128;
+constexpr int CELL_THREADS = 256;
+constexpr float WENO_EPS32 = 1e-30f;   // reading: FP32 epsilon kept normal
+constexpr float DELTA32 = 1e-30f;      // psi transform delta in FP32 (1e-100 underflows)
+constexpr float GTOL32 = 1e-6f;        // |grad psi| threshold at FP32 round-off
+
+// ---------------------------------------------------------------------------
+// FP32 species EOS (Eq. NASG_EOS) with constants cast once
+struct SpeciesF {
+  float cv, gam, q, b, pinf, Rk, cp;
+};
+
+template <int NS>
+__device__ __forceinline__ void load_species(const KParams& P, SpeciesF* s) {
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    s[k].cv = (float)P.cv[k];
+    s[k].gam = (float)P.gam[k];
+    s[k].q = (float)P.q[k];
+    s[k].b = (float)P.b[k];
+    s[k].pinf = (float)P.pinf[k];
+    s[k].Rk = (float)P.Rk[k];
+    s[k].cp = (float)P.cp[k];
+  }
+}
+
+// forward EOS at (p, T, Y) in FP32: density, internal energy, sound speed
+template <int NS>
+__device__ __forceinline__ void eos_forward_f(const SpeciesF* s, const float* Y, float p, float T, float& rho,
+                                              float& e, float& a) {
+  float v = 0.f, cp = 0.f, sa = 0.f, sb = 0.f;
+  e = 0.f;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    if (Y[k] != 0.f) {
+      const float r = __frcp_rn(p + s[k].pinf);
+      const float RT = s[k].Rk * T;
+      v += Y[k] * (RT * r + s[k].b);
+      e += Y[k] * (s[k].cv * T * (p + s[k].gam * s[k].pinf) * r + s[k].q);
+      cp += Y[k] * s[k].cp;
+      sa += Y[k] * s[k].Rk * r;
+      sb += Y[k] * RT * r * r;
+    }
+  }
+  rho = __frcp_rn(v);
+  const float al = rho * sa, be = rho * sb;
+  a = sqrtf(cp / (rho * be * cp - al * al * T));
+}
+
+// p-T equilibrium in FP32 (face average only: feeds the characteristic
+// matrices, whose scalars depend on P through P + Pinf)
+template <int NS>
+__device__ __forceinline__ void pt_equilibrium_f(const SpeciesF* s, const float* Y, float e, float v, float& p,
+                                                 float& T) {
+  float Cv = 0.f, q = 0.f, b = 0.f, Rg = 0.f, Rl = 0.f, wpl = 0.f;
+  float pl = -1.f;
+  bool gas = false;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    Cv += Y[k] * s[k].cv;
+    q += Y[k] * s[k].q;
+    b += Y[k] * s[k].b;
+    if (Y[k] > 0.f) {
+      if (s[k].pinf > 0.f) {
+        Rl += Y[k] * s[k].Rk;
+        wpl += Y[k] * s[k].Rk * s[k].pinf;
+        pl = 1.f;
+      } else {
+        gas = true;
+        Rg += Y[k] * s[k].Rk;
+      }
+    }
+  }
+  const float em = e - q, Ep = em / (v - b);
+  if (pl < 0.f) {
+    p = Ep * Rg / Cv;
+  } else {
+    // several liquids merged into one with a Y-weighted Pinf (only the
+    // characteristic scalars use this pressure)
+    const float pe = wpl / Rl;
+    const float a2 = Ep * (Rg + Rl) - pe * Cv - pe * Rl;
+    if (!gas) {
+      p = a2 / Cv;
+    } else {
+      const float a3 = Ep * pe * Rg;
+      const float sq = sqrtf(a2 * a2 + 4.f * Cv * a3);
+      p = a2 >= 0.f ? (a2 + sq) / (2.f * Cv) : 2.f * a3 / (sq - a2);
+    }
+  }
+  float den = 0.f;
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+    if (Y[k] != 0.f) den += Y[k] * s[k].cv * (p + s[k].gam * s[k].pinf) / (p + s[k].pinf);
+  T = em / den;
+}
+
+// WENO5-Z in FP32 on deviations (exponent 1)
+__device__ __forceinline__ float weno5z_f(float v0, float v1, float v2, float v3, float v4) {
+  const float q0 = (2.f * v0 - 7.f * v1 + 11.f * v2) * (1.f / 6.f);
+  const float q1 = (-v1 + 5.f * v2 + 2.f * v3) * (1.f / 6.f);
+  const float q2 = (2.f * v2 + 5.f * v3 - v4) * (1.f / 6.f);
+  float t = v0 - 2.f * v1 + v2, s = v0 - 4.f * v1 + 3.f * v2;
+  const float b0 = (13.f / 12.f) * t * t + 0.25f * s * s;
+  t = v1 - 2.f * v2 + v3;
+  s = v1 - v3;
+  const float b1 = (13.f / 12.f) * t * t + 0.25f * s * s;
+  t = v2 - 2.f * v3 + v4;
+  s = 3.f * v2 - 4.f * v3 + v4;
+  const float b2 = (13.f / 12.f) * t * t + 0.25f * s * s;
+  const float tau = fabsf(b0 - b2);
+  // tau / (beta + eps) clamped at 1e30: with eps = 1e-30 the ratio of a
+  // stencil that is flat next to a jump would overflow FP32 (in FP64 it
+  // reaches 1e50 harmlessly); at 1e30 that stencil already carries all the
+  // weight, so the clamp changes the weights by 1 part in 1e30
+  const float a0 = 0.1f * (1.f + fminf(tau / (b0 + WENO_EPS32), 1e30f));
+  const float a1 = 0.6f * (1.f + fminf(tau / (b1 + WENO_EPS32), 1e30f));
+  const float a2 = 0.3f * (1.f + fminf(tau / (b2 + WENO_EPS32), 1e30f));
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+template <int NS>
+struct StateF {
+  float rho, rhoY[NS], u[3], m[3], p, E, a;
+};
+
+// HLLC (Appendix B) in FP32; the contact speed in the form
+// s* = u_L + (P_R - P_L - rho_R d_R (u_R - u_L)) / (rho_L d_L - rho_R d_R),
+// algebraically the printed one, exactly u where P and u are continuous
+template <int NS, int D>
+__device__ __forceinline__ void hllc_f(int d, const StateF<NS>& L, const StateF<NS>& R, float* F) {
+  const float ub = 0.5f * (L.u[d] + R.u[d]), ab = 0.5f * (L.a + R.a);
+  const float sL = fminf(ub - ab, L.u[d] - L.a);
+  const float sR = fmaxf(ub + ab, R.u[d] + R.a);
+  const float sm = fminf(0.f, sL), sp = fmaxf(0.f, sR);
+  const float dL = sL - L.u[d], dR = sR - R.u[d];
+  const float ss = L.u[d] + (R.p - L.p - R.rho * dR * (R.u[d] - L.u[d])) / (L.rho * dL - R.rho * dR);
+  const float wl = ss > 0.f ? 1.f : (ss < 0.f ? 0.f : 0.5f);
+  const float wr = 1.f - wl;
+  const float fL = dL / (sL - ss), fR = dR / (sR - ss);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const float FL = L.rhoY[k] * L.u[d], FR = R.rhoY[k] * R.u[d];
+    F[k] = wl * (FL + sm * (fL * L.rhoY[k] - L.rhoY[k])) + wr * (FR + sp * (fR * R.rhoY[k] - R.rhoY[k]));
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const float FL = L.rho * L.u[d] * L.u[j] + (j == d ? L.p : 0.f);
+    const float FR = R.rho * R.u[d] * R.u[j] + (j == d ? R.p : 0.f);
+    const float UsL = fL * L.rho * (j == d ? ss : L.u[j]);
+    const float UsR = fR * R.rho * (j == d ? ss : R.u[j]);
+    F[NS + j] = wl * (FL + sm * (UsL - L.m[j])) + wr * (FR + sp * (UsR - R.m[j]));
+  }
+  {
+    const float FL = L.u[d] * (L.E + L.p), FR = R.u[d] * (R.E + R.p);
+    const float UsL = fL * (L.E + (ss - L.u[d]) * (L.rho * ss + L.p / dL));
+    const float UsR = fR * (R.E + (ss - R.u[d]) * (R.rho * ss + R.p / dR));
+    F[NS + D] = wl * (FL + sm * (UsL - L.E)) + wr * (FR + sp * (UsR - R.E));
+  }
+}
+
+template <int NS>
+__device__ __forceinline__ void state_from_primitive_f(const SpeciesF* s, const float* Y, const float* u, float p,
+                                                       float T, StateF<NS>& st) {
+  float e;
+  eos_forward_f<NS>(s, Y, p, T, st.rho, e, st.a);
+  float ke = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    st.u[d] = u[d];
+    st.m[d] = st.rho * u[d];
+    ke += u[d] * u[d];
+  }
+#pragma unroll
+  for (int k = 0; k < NS; ++k) st.rhoY[k] = st.rho * Y[k];
+  st.p = p;
+  st.E = st.rho * (e + 0.5f * ke);
+}
+
+template <int NS>
+__device__ __forceinline__ bool y_limiter_f(float* Y, const float* Yc) {
+  bool active = false;
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+    if (Y[k] < 0.f) {
+      Y[k] = 0.f;
+      active = true;
+    }
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) sum += Y[k];
+  // a sum within FP32 rounding of one needs no correction (correcting it
+  // would move trace species by ~1e-7 absolute)
+  if (fabsf(sum - 1.f) > (float)NS * 1.2e-7f) {
+    const bool over = sum > 1.f;
+    float dd[NS], Sig = 0.f;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      dd[k] = (over ? fminf(Y[k], Yc[k]) : fmaxf(Y[k], Yc[k])) - Y[k];
+      Sig += dd[k];
+    }
+    if (Sig != 0.f) {
+      const float f = (1.f - sum) / Sig;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) Y[k] += f * dd[k];
+      active = true;
+    }
+  }
+  return active;
+}
+
+__device__ __forceinline__ float wgetf(const KParams& P, const float* __restrict__ Wc, int f, CRef r) {
+  return Wc[(long long)f * P.wstride + r.idx];
+}
+__device__ __forceinline__ float sgnf(unsigned flip, int d) { return (flip >> d) & 1u ? -1.f : 1.f; }
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ void block_max2f(float a, float b, unsigned long long* red) {
+  __shared__ float sa[32], sb[32];
+  a = warp_maxf(a);
+  b = warp_maxf(b);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sa[wid] = a;
+    sb[wid] = b;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    a = lane < nw ? sa[lane] : 0.f;
+    b = lane < nw ? sb[lane] : 0.f;
+    a = warp_maxf(a);
+    b = warp_maxf(b);
+    if (lane == 0) {
+      atomicMax(red + 0, (unsigned long long)__double_as_longlong((double)a));
+      atomicMax(red + 1, (unsigned long long)__double_as_longlong((double)b));
+    }
+  }
+}
+
+// per cell: FP64 inversion, FP32 cache
+template <int NS, int D>
+__global__ void __launch_bounds__(CELL_THREADS)
+    k_prim(const KParams P, const double* __restrict__ U, const double* __restrict__ Uin, float* __restrict__ Wc,
+           unsigned long long* __restrict__ red, int* __restrict__ status) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float smax = 0.f, gmax = 0.f;
+  if (c < P.ncell + P.has_inflow) {
+    constexpr int NV = NS + D + 1;
+    double Uc[NV];
+    if (c == P.ncell) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uc[v] = Uin[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uc[v] = U[(long long)v * P.ncell + c];
+    }
+    const long long ws = P.wstride;
+    double rho, Y[NS], u[3], e, vol;
+    decode<NS, D>(Uc, rho, Y, u, e, vol);
+    int st = rho > 0.0 ? ST_OK : ST_INADMISSIBLE;
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+      if (Uc[k] < -YTOL * rho) st = ST_INADMISSIBLE;
+    double pd, Td;
+    const int st2 = pt_equilibrium<NS>(P, Y, e, vol, pd, Td);
+    if (st == ST_OK) st = st2;
+    SpeciesF sp[NS];
+    load_species<NS>(P, sp);
+    float Yf[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) Yf[k] = (float)Y[k];
+    const float p = (float)pd, T = (float)Td;
+    float r2, e2, a;
+    eos_forward_f<NS>(sp, Yf, p, T, r2, e2, a);
+    Wc[P.wT * ws + c] = T;
+    Wc[P.wP * ws + c] = p;
+    Wc[P.wRho * ws + c] = (float)rho;
+    Wc[P.wA * ws + c] = a;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) Wc[(P.wY + k) * ws + c] = Yf[k];
+#pragma unroll
+    for (int d = 0; d < D; ++d) Wc[(P.wU + d) * ws + c] = (float)u[d];
+    float mu = 0.f;
+    const float rhof = (float)rho;
+    if (P.cdi || P.diffusion) {
+      float phi[2], Yp[2];
+#pragma unroll
+      for (int ph = 0; ph < 2; ++ph) {
+        float f = 0.f, hr = 0.f, yp = 0.f;
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+          if (P.phase[k] == ph) {
+            yp += Yf[k];
+            const float ry = (float)Uc[k];
+            if (ry != 0.f) {
+              f += ry * (sp[k].Rk * T / (p + sp[k].pinf) + sp[k].b);
+              hr += ry * (sp[k].cp * T + sp[k].b * p + sp[k].q);
+            }
+          }
+        phi[ph] = f;
+        Yp[ph] = yp;
+        if (P.cdi) {
+          // a phase whose FP32 volume fraction underflows counts as absent
+          const bool present = f > 0.f;
+          Wc[(P.wHrho + ph) * ws + c] = present ? hr / f : 0.f;
+#pragma unroll
+          for (int k = 0; k < NS; ++k)
+            if (P.phase[k] == ph) Wc[(P.wYrho + k) * ws + c] = present ? (float)Uc[k] / f : 0.f;
+        }
+      }
+      if (P.cdi) {
+        Wc[P.wPhi0 * ws + c] = phi[0];
+        Wc[P.wPsi * ws + c] = (float)P.cdi_eps * __logf((phi[0] + DELTA32) / (phi[1] + DELTA32));
+      }
+      if (P.diffusion) {
+        float mup[2];
+        mup[0] = (float)P.mu_liquid;
+        float num = 0.f;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+          if (P.phase[i] != 1) continue;
+          float den = 0.f;
+#pragma unroll
+          for (int j = 0; j < NS; ++j)
+            if (P.phase[j] == 1) den += Yf[j] * (float)P.wilke[i][j];
+          if (den > 0.f) num += Yf[i] * (float)P.mu[i] / den;
+        }
+        mup[1] = Yp[1] > 0.f ? num : 0.f;
+        mu = phi[0] * mup[0] + phi[1] * mup[1];
+#pragma unroll
+        for (int ph = 0; ph < 2; ++ph) {
+          float sY = 0.f;
+#pragma unroll
+          for (int j = 0; j < NS; ++j)
+            if (P.phase[j] == ph) sY += Yf[j] / (float)P.W[j];
+          const bool present = Yp[ph] > 0.f && sY > 0.f && phi[ph] > 0.f;
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            if (P.phase[k] != ph) continue;
+            float xr = 0.f, B = 0.f;
+            if (present) {
+              xr = (Yf[k] / (float)P.W[k]) / sY;
+              const float WcWp = (float)P.W[k] * sY / Yp[ph];
+              const float rho_p = rhof * Yp[ph] / phi[ph];
+              B = WcWp * (mup[ph] / (rho_p * (float)P.Sc[k]));
+            }
+            Wc[(P.wXr + k) * ws + c] = xr;
+            Wc[(P.wB + k) * ws + c] = B;
+          }
+        }
+      }
+    }
+    if (st != ST_OK) atomicMax(status, st);
+    if (c < P.ncell) {
+      const float idx = (float)P.inv_dx;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const float ud = fabsf((float)u[d]);
+        smax = fmaxf(smax, (ud + a) * idx);
+        gmax = fmaxf(gmax, ud);
+      }
+      if (P.diffusion) smax = fmaxf(smax, 4.f * mu / rhof * (idx * idx));
+    }
+  }
+  if (red) block_max2f(smax, gmax, red);
+}
+
+// per face: FP32 pipeline, FP64 pseudo-updates for the limiter decisions
+template <int NS, int D>
+__global__ void __launch_bounds__(FACE_THREADS)
+    k_face(const KParams P, const int d, const float* __restrict__ Wc, const double* __restrict__ Un,
+           const double* __restrict__ Uk, const double* __restrict__ Uin, const double* __restrict__ scal,
+           const double rk0, const double rk1, const double rk2, float* __restrict__ F,
+           uint32_t* __restrict__ flags, unsigned long long* __restrict__ stats) {
+  constexpr int NV = NS + D + 1;
+  const int f0 = P.n[0] + (d == 0), f1 = P.n[1] + (d == 1), f2 = P.n[2] + (d == 2);
+  const long long nf = (long long)f0 * f1 * f2;
+  const long long fid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (fid >= nf) return;
+  int fc[3];
+  fc[0] = (int)(fid % f0);
+  const long long rr = fid / f0;
+  fc[1] = (int)(rr % f1);
+  fc[2] = (int)(rr / f1);
+  int ci[3] = {fc[0], fc[1], fc[2]};
+  ci[d] -= 1;
+  const double dt = scal[0];
+  const float Gamma = (float)scal[1];
+  SpeciesF sp[NS];
+  load_species<NS>(P, sp);
+
+  CRef cr[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    int cc[3] = {ci[0], ci[1], ci[2]};
+    cc[d] += j - 2;
+    cr[j] = map_cell(P, cc[0], cc[1], cc[2]);
+  }
+  const CRef ri = cr[2], rj = cr[3];
+  uint32_t fl = 0u;
+
+  // FP64 conserved states of the two neighbours (face average, limiter)
+  double Uni[NV], Unj[NV], Uki[NV], Ukj[NV];
+  load_U<NS, D>(P, Uk, Uin, ri, Uki);
+  load_U<NS, D>(P, Uk, Uin, rj, Ukj);
+  if (P.pos_limiter) {
+    load_U<NS, D>(P, Un, Uin, ri, Uni);
+    load_U<NS, D>(P, Un, Uin, rj, Unj);
+  }
+
+  // characteristic scalars at the averaged state (FP32 EOS)
+  float X, c, ic;
+  {
+    float Ub[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Ub[v] = (float)(0.5 * (Uki[v] + Ukj[v]));
+    float rho = 0.f, Y[NS], ke = 0.f;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) rho += Ub[k];
+    const float ir = __frcp_rn(rho);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) Y[k] = Ub[k] * ir;
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      const float u = Ub[NS + t] * ir;
+      ke += u * u;
+    }
+    const float e = Ub[NS + D] * ir - 0.5f * ke;
+    float p, T, r2, e2, a;
+    pt_equilibrium_f<NS>(sp, Y, e, ir, p, T);
+    // alpha, beta at the averaged state
+    float sa = 0.f, sb = 0.f, cp = 0.f;
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+      if (Y[k] != 0.f) {
+        const float r = __frcp_rn(p + sp[k].pinf);
+        sa += Y[k] * sp[k].Rk * r;
+        sb += Y[k] * sp[k].Rk * T * r * r;
+        cp += Y[k] * sp[k].cp;
+      }
+    eos_forward_f<NS>(sp, Y, p, T, r2, e2, a);
+    const float al = r2 * sa, be = r2 * sb;
+    X = (rho * a * a * be - 1.f) / (al * a * a * rho);
+    c = a * rho;
+    ic = __frcp_rn(c);
+  }
+
+  // deviations from the left cell, projection, WENO5-Z, back-projection
+  const float Ti = wgetf(P, Wc, P.wT, ri), Tj = wgetf(P, Wc, P.wT, rj);
+  const float Pi = wgetf(P, Wc, P.wP, ri), Pj = wgetf(P, Wc, P.wP, rj);
+  float YL[NS], YR[NS], uL[3] = {0.f, 0.f, 0.f}, uR[3] = {0.f, 0.f, 0.f}, PL, PR, TL, TR;
+  {
+    const float uni = wgetf(P, Wc, P.wU + d, ri) * sgnf(ri.flip, d);
+    float w1[6], w5[6], w6[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const float dT = wgetf(P, Wc, P.wT, cr[j]) - Ti;
+      const float dp = wgetf(P, Wc, P.wP, cr[j]) - Pi;
+      const float du = wgetf(P, Wc, P.wU + d, cr[j]) * sgnf(cr[j].flip, d) - uni;
+      w1[j] = dT - X * dp;
+      w5[j] = (0.5f * c) * du + 0.5f * dp;
+      w6[j] = (-0.5f * c) * du + 0.5f * dp;
+    }
+    const float w1L = weno5z_f(w1[0], w1[1], w1[2], w1[3], w1[4]);
+    const float w1R = weno5z_f(w1[5], w1[4], w1[3], w1[2], w1[1]);
+    const float w5L = weno5z_f(w5[0], w5[1], w5[2], w5[3], w5[4]);
+    const float w5R = weno5z_f(w5[5], w5[4], w5[3], w5[2], w5[1]);
+    const float w6L = weno5z_f(w6[0], w6[1], w6[2], w6[3], w6[4]);
+    const float w6R = weno5z_f(w6[5], w6[4], w6[3], w6[2], w6[1]);
+    TL = Ti + (w1L + X * (w5L + w6L));
+    TR = Ti + (w1R + X * (w5R + w6R));
+    uL[d] = uni + ic * (w5L - w6L);
+    uR[d] = uni + ic * (w5R - w6R);
+    PL = Pi + (w5L + w6L);
+    PR = Pi + (w5R + w6R);
+  }
+  float Yi[NS], Yj[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    Yi[k] = wgetf(P, Wc, P.wY + k, ri);
+    Yj[k] = wgetf(P, Wc, P.wY + k, rj);
+    float y[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) y[j] = wgetf(P, Wc, P.wY + k, cr[j]) - Yi[k];
+    YL[k] = Yi[k] + weno5z_f(y[0], y[1], y[2], y[3], y[4]);
+    YR[k] = Yi[k] + weno5z_f(y[5], y[4], y[3], y[2], y[1]);
+  }
+#pragma unroll
+  for (int t = 0; t < D; ++t) {
+    if (t == d) continue;
+    const float ut = wgetf(P, Wc, P.wU + t, ri) * sgnf(ri.flip, t);
+    float y[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) y[j] = wgetf(P, Wc, P.wU + t, cr[j]) * sgnf(cr[j].flip, t) - ut;
+    uL[t] = ut + weno5z_f(y[0], y[1], y[2], y[3], y[4]);
+    uR[t] = ut + weno5z_f(y[5], y[4], y[3], y[2], y[1]);
+  }
+
+  if (P.pos_limiter) {
+    if (y_limiter_f<NS>(YL, Yi)) fl |= F_YLIM_L;
+    if (y_limiter_f<NS>(YR, Yj)) fl |= F_YLIM_R;
+    if (!(TL > 0.f)) { TL = Ti; fl |= F_THETA_T_L; }
+    if (!(TR > 0.f)) { TR = Tj; fl |= F_THETA_T_R; }
+    bool okL = true, okR = true;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      if (YL[k] > 0.f && !(PL + sp[k].pinf > 0.f)) okL = false;
+      if (YR[k] > 0.f && !(PR + sp[k].pinf > 0.f)) okR = false;
+    }
+    if (!okL) { PL = Pi; fl |= F_THETA_P_L; }
+    if (!okR) { PR = Pj; fl |= F_THETA_P_R; }
+  }
+
+  float Fx[NV];
+  {
+    StateF<NS> sL, sR;
+    state_from_primitive_f<NS>(sp, YL, uL, PL, TL, sL);
+    state_from_primitive_f<NS>(sp, YR, uR, PR, TR, sR);
+    hllc_f<NS, D>(d, sL, sR, Fx);
+  }
+
+  // positivity decisions on FP64 pseudo-updates
+  const double lam = 2.0 * D * rk2 * dt * P.inv_dx;
+  auto passes = [&](const float* Ft) {
+    double Ti_[NV], Tj_[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double f = (double)Ft[v];
+      Ti_[v] = rk0 * Uni[v] + rk1 * Uki[v] - lam * f;
+      Tj_[v] = rk0 * Unj[v] + rk1 * Ukj[v] + lam * f;
+    }
+    return admissible<NS, D>(P, Ti_) && admissible<NS, D>(P, Tj_);
+  };
+  if (P.pos_limiter && !passes(Fx)) {
+    StateF<NS> si, sj;
+    si.rho = wgetf(P, Wc, P.wRho, ri);
+    sj.rho = wgetf(P, Wc, P.wRho, rj);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      si.rhoY[k] = (float)Uki[k];
+      sj.rhoY[k] = (float)Ukj[k];
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      si.u[t] = t < D ? wgetf(P, Wc, P.wU + t, ri) * sgnf(ri.flip, t) : 0.f;
+      sj.u[t] = t < D ? wgetf(P, Wc, P.wU + t, rj) * sgnf(rj.flip, t) : 0.f;
+      si.m[t] = t < D ? (float)Uki[NS + t] : 0.f;
+      sj.m[t] = t < D ? (float)Ukj[NS + t] : 0.f;
+    }
+    si.p = Pi;
+    sj.p = Pj;
+    si.E = (float)Uki[NS + D];
+    sj.E = (float)Ukj[NS + D];
+    si.a = wgetf(P, Wc, P.wA, ri);
+    sj.a = wgetf(P, Wc, P.wA, rj);
+    hllc_f<NS, D>(d, si, sj, Fx);
+    fl |= F_HLLC_FALLBACK;
+  }
+
+  if (P.cdi && P.two_phase) {
+    bool pres_i[2] = {false, false}, pres_j[2] = {false, false};
+    {
+      float ypi[2] = {0.f, 0.f}, ypj[2] = {0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        ypi[P.phase[k]] += Yi[k];
+        ypj[P.phase[k]] += Yj[k];
+      }
+#pragma unroll
+      for (int ph = 0; ph < 2; ++ph) {
+        pres_i[ph] = ypi[ph] > 0.f;
+        pres_j[ph] = ypj[ph] > 0.f;
+      }
+    }
+    if ((pres_i[0] || pres_j[0]) && (pres_i[1] || pres_j[1])) {
+      const float ceps = (float)P.cdi_eps, idx = (float)P.inv_dx;
+      const float psi_i = wgetf(P, Wc, P.wPsi, ri), psi_j = wgetf(P, Wc, P.wPsi, rj);
+      const float dphi = (wgetf(P, Wc, P.wPhi0, rj) - wgetf(P, Wc, P.wPhi0, ri)) * idx;
+      float g[3] = {0.f, 0.f, 0.f};
+      g[d] = (psi_j - psi_i) * idx;
+#pragma unroll
+      for (int t = 0; t < D; ++t) {
+        if (t == d) continue;
+        int a0[3] = {ci[0], ci[1], ci[2]}, a1[3] = {ci[0], ci[1], ci[2]};
+        a0[t] += 1;
+        a1[t] -= 1;
+        int b0[3] = {a0[0], a0[1], a0[2]}, b1[3] = {a1[0], a1[1], a1[2]};
+        b0[d] += 1;
+        b1[d] += 1;
+        const float pip = wgetf(P, Wc, P.wPsi, map_cell(P, a0[0], a0[1], a0[2]));
+        const float pim = wgetf(P, Wc, P.wPsi, map_cell(P, a1[0], a1[1], a1[2]));
+        const float pjp = wgetf(P, Wc, P.wPsi, map_cell(P, b0[0], b0[1], b0[2]));
+        const float pjm = wgetf(P, Wc, P.wPsi, map_cell(P, b1[0], b1[1], b1[2]));
+        g[t] = 0.25f * idx * ((pip - pim) + (pjp - pjm));
+      }
+      const float gn = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+      const float nd = gn >= GTOL32 ? g[d] / gn : 0.f;
+      const float ch = coshf((0.5f * (psi_i + psi_j)) / (2.f * ceps));
+      const float sech2 = __frcp_rn(ch * ch);
+      const float ahat0 = Gamma * (ceps * dphi - 0.25f * (sech2 - (float)P.sharp0) * nd);
+      float Fdi[NV], Rtot = 0.f, hR = 0.f;
+#pragma unroll
+      for (int ph = 0; ph < 2; ++ph) {
+        const float ahat = ph == 0 ? ahat0 : -ahat0;
+        const bool pi = pres_i[ph], pj = pres_j[ph];
+        auto keep = [&](float a, float b) { return pi && pj ? 0.5f * (a + b) : (pi ? a : (pj ? b : 0.f)); };
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          if (P.phase[k] != ph) continue;
+          const float R = -keep(wgetf(P, Wc, P.wYrho + k, ri), wgetf(P, Wc, P.wYrho + k, rj)) * ahat;
+          Fdi[k] = R;
+          Rtot += R;
+        }
+        hR -= keep(wgetf(P, Wc, P.wHrho + ph, ri), wgetf(P, Wc, P.wHrho + ph, rj)) * ahat;
+      }
+      float kb = 0.f;
+#pragma unroll
+      for (int t = 0; t < D; ++t) {
+        const float ui = wgetf(P, Wc, P.wU + t, ri) * sgnf(ri.flip, t);
+        const float uj = wgetf(P, Wc, P.wU + t, rj) * sgnf(rj.flip, t);
+        kb += ui * uj;
+        Fdi[NS + t] = 0.5f * (ui + uj) * Rtot;
+      }
+      Fdi[NS + D] = 0.5f * kb * Rtot + hR;
+      float Ft[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Ft[v] = Fx[v] + Fdi[v];
+      if (P.pos_limiter && !passes(Ft)) {
+        fl |= F_CDI_DROPPED;
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fx[v] = Ft[v];
+      }
+    }
+  }
+
+  if (P.diffusion) {
+    const float idx = (float)P.inv_dx;
+    const float rb = 0.5f * (wgetf(P, Wc, P.wRho, ri) + wgetf(P, Wc, P.wRho, rj));
+    float Jh = 0.f;
+#pragma unroll
+    for (int ph = 0; ph < 2; ++ph) {
+      float Yp = 0.f, S = 0.f, Bf[NS], G[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        Bf[k] = 0.f;
+        G[k] = 0.f;
+        if (P.phase[k] != ph) continue;
+        Yp += 0.5f * (Yi[k] + Yj[k]);
+        Bf[k] = 0.5f * (wgetf(P, Wc, P.wB + k, ri) + wgetf(P, Wc, P.wB + k, rj));
+        G[k] = (wgetf(P, Wc, P.wXr + k, rj) - wgetf(P, Wc, P.wXr + k, ri)) * idx;
+        S += Bf[k] * G[k];
+      }
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        if (P.phase[k] != ph) continue;
+        const float J = -rb * (Yp * Bf[k] * G[k] - 0.5f * (Yi[k] + Yj[k]) * S);
+        Fx[k] += J;
+        const float hi = sp[k].cp * Ti + sp[k].b * Pi + sp[k].q;
+        const float hj = sp[k].cp * Tj + sp[k].b * Pj + sp[k].q;
+        Jh += J * (0.5f * (hi + hj));
+      }
+    }
+    Fx[NS + D] += Jh;
+  }
+
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[(long long)v * nf + fid] = Fx[v];
+  if (flags) flags[fid] = fl;
+  if (stats && fl) {
+    if (fl & F_HLLC_FALLBACK) atomicAdd(stats + 1, 1ull);
+    if (fl & F_CDI_DROPPED) atomicAdd(stats + 2, 1ull);
+    if (fl & (F_THETA_P_L | F_THETA_P_R)) atomicAdd(stats + 3, 1ull);
+    if (fl & (F_THETA_T_L | F_THETA_T_R)) atomicAdd(stats + 4, 1ull);
+    if (fl & (F_YLIM_L | F_YLIM_R)) atomicAdd(stats + 5, 1ull);
+  }
+}
+
+// divergence of the FP32 fluxes and the RK combination, both in FP64
+template <int NS, int D>
+__global__ void __launch_bounds__(CELL_THREADS)
+    k_update(const KParams P, const double* __restrict__ Un, const double* __restrict__ Uk,
+             const float* __restrict__ F0, const float* __restrict__ F1, const float* __restrict__ F2,
+             const double* __restrict__ scal, const double rk0, const double rk1, const double rk2,
+             double* __restrict__ Uout, double* __restrict__ dUdt, int* __restrict__ status) {
+  constexpr int NV = NS + D + 1;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.ncell) return;
+  const int n0 = P.n[0], n1 = P.n[1];
+  const int i = (int)(c % n0);
+  const long long r = c / n0;
+  const int j = (int)(r % n1), k = (int)(r / n1);
+  const float* Fd[3] = {F0, F1, F2};
+  long long fm[3], fp[3], nf[3];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int f0 = n0 + (d == 0), f1 = n1 + (d == 1), f2 = P.n[2] + (d == 2);
+    nf[d] = (long long)f0 * f1 * f2;
+    fm[d] = ((long long)k * f1 + j) * f0 + i;
+    fp[d] = fm[d] + (d == 0 ? 1 : (d == 1 ? f0 : (long long)f0 * f1));
+  }
+  const double s = rk2 * scal[0];
+  double Uo[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double L = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+      L -= (double)Fd[d][(long long)v * nf[d] + fp[d]] - (double)Fd[d][(long long)v * nf[d] + fm[d]];
+    L *= P.inv_dx;
+    if (dUdt) dUdt[(long long)v * P.ncell + c] = L;
+    Uo[v] = rk0 * Un[(long long)v * P.ncell + c] + rk1 * Uk[(long long)v * P.ncell + c] + s * L;
+  }
+  if (Uout) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Uout[(long long)v * P.ncell + c] = Uo[v];
+    if (!admissible<NS, D>(P, Uo)) atomicMax(status, (int)ST_INADMISSIBLE);
+  }
+}
+
+inline unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <int NS, int D>
+struct Impl {
+  static void prim(const KParams& P, cudaStream_t s, const double* U, const double* Uin, double* Wc,
+                   unsigned long long* red, int* status) {
+    k_prim<NS, D><<<nblocks(P.ncell + P.has_inflow, CELL_THREADS), CELL_THREADS, 0, s>>>(
+        P, U, Uin, reinterpret_cast<float*>(Wc), red, status);
+  }
+  static void face(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* Un, const double* Uk,
+                   const double* Uin, const double* scal, double rk0, double rk1, double rk2, double* F,
+                   uint32_t* flags, unsigned long long* stats) {
+    long long nf = 1;
+    for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
+    k_face<NS, D><<<nblocks(nf, FACE_THREADS), FACE_THREADS, 0, s>>>(
+        P, d, reinterpret_cast<const float*>(Wc), Un, Uk, Uin, scal, rk0, rk1, rk2, reinterpret_cast<float*>(F),
+        flags, stats);
+  }
+  static void update(const KParams& P, cudaStream_t s, const double* Un, const double* Uk, double* const* F,
+                     const double* scal, double rk0, double rk1, double rk2, double* Uout, double* dUdt,
+                     int* status) {
+    const float* F0 = reinterpret_cast<const float*>(F[0]);
+    const float* F1 = reinterpret_cast<const float*>(D > 1 ? F[1] : F[0]);
+    const float* F2 = reinterpret_cast<const float*>(D > 2 ? F[2] : F[0]);
+    k_update<NS, D><<<nblocks(P.ncell, CELL_THREADS), CELL_THREADS, 0, s>>>(P, Un, Uk, F0, F1, F2, scal, rk0, rk1,
+                                                                             rk2, Uout, dUdt, status);
+  }
+};
+
+}  // namespace mx
+}  // namespace mpmc

@@ -1,0 +1,25 @@
+// Mixed-precision kernel instantiations for dimension 3, species counts 1..4.
+#include "mpmc_mixed.cuh"
+
+namespace mpmc {
+
+template <int NS>
+static Ops mixed_ops() {
+  Ops o = ops_fp64_d3(NS);
+  o.prim = &mx::Impl<NS, 3>::prim;
+  o.face = &mx::Impl<NS, 3>::face;
+  o.update = &mx::Impl<NS, 3>::update;
+  return o;
+}
+
+Ops ops_mixed_d3(int ns) {
+  switch (ns) {
+    case 1: return mixed_ops<1>();
+    case 2: return mixed_ops<2>();
+    case 3: return mixed_ops<3>();
+    case 4: return mixed_ops<4>();
+    default: return Ops{nullptr, nullptr, nullptr, nullptr};
+  }
+}
+
+}  // namespace mpmc

@@ -19,9 +19,13 @@ struct Ops {
                  const double* scal, double rk0, double rk1, double rk2, double* Uout, double* dUdt, int* status);
 };
 
-// per-dimension tables, defined in mpmc_kernels_d{1,2,3}.cu
+// per-dimension tables, defined in mpmc_kernels_d{1,2,3}.cu (FP64) and
+// mpmc_mixed_d{1,2,3}.cu (mixed precision; init is the FP64 one)
 Ops ops_fp64_d1(int ns);
 Ops ops_fp64_d2(int ns);
 Ops ops_fp64_d3(int ns);
+Ops ops_mixed_d1(int ns);
+Ops ops_mixed_d2(int ns);
+Ops ops_mixed_d3(int ns);
 
 }  // namespace mpmc
