@@ -44,6 +44,8 @@ constexpr int MAXV = MAXS + 4;   // conserved variables
 constexpr int MAXC = MAXS + 4;   // characteristic variables
 constexpr double YTOL = 1e-14;   // round-off allowance on partial densities
 constexpr double GTOL = 1e-8;    // |grad psi| below which the interface normal is zero
+constexpr double YSUM_TOL = 1e-15;  // per species: |sum Y - 1| treated as rounding
+constexpr double WENO_FLAT = 1e-10; // relative stencil variation treated as noise (derivative only)
 
 using std::vector;
 
@@ -384,7 +386,23 @@ R weno5z(const R& v0, const R& v1, const R& v2, const R& v3, const R& v4, double
   R a0 = 0.1 * (1.0 + tau5 / (b0 + eps));
   R a1 = 0.6 * (1.0 + tau5 / (b1 + eps));
   R a2 = 0.3 * (1.0 + tau5 / (b2 + eps));
-  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+  R out = (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+  if (is_dual<R>::value) {
+    /* reading (derivative only): on a stencil flat to rounding (every
+     * smoothness indicator below (WENO_FLAT max|v|)^2) the weights are
+     * ratios of rounding errors whose derivative grows like 1/eps, while
+     * the value is each candidate to rounding; the tangent there is taken
+     * with the ideal weights (the linear fifth-order scheme). */
+    double M = 0.0;
+    const double vv[5] = {val(v0), val(v1), val(v2), val(v3), val(v4)};
+    for (int j = 0; j < 5; ++j) M = std::max(M, std::fabs(vv[j]));
+    const double tol = (WENO_FLAT * M) * (WENO_FLAT * M);
+    if (val(b0) <= tol && val(b1) <= tol && val(b2) <= tol) {
+      R lin = 0.1 * q0 + 0.6 * q1 + 0.3 * q2;
+      return with_value(lin, val(out));
+    }
+  }
+  return out;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -591,7 +609,8 @@ struct Solver {
   }
 
   /* init: rhoY_k = alpha_k / v_k(P, T), m = rho u, E = sum rhoY_k e_k + rho|u|^2/2 */
-  void conserved_from_primitive(const double* w, R* U) const {
+  template <class Wt>
+  void conserved_from_primitive(const Wt* w, R* U) const {
     R P(w[ns + D]), T(w[ns + D + 1]);
     R rho(0.0), e(0.0);
     for (int k = 0; k < ns; ++k) {
@@ -691,6 +710,12 @@ struct Solver {
       }
     R sum(0.0);
     for (int k = 0; k < ns; ++k) sum = sum + Y[k];
+    /* reading: no renormalization when sum Y is one to rounding
+     * (|sum Y - 1| <= ns YSUM_TOL).  The correction would then be below the
+     * resolution of the data, distributed by a ratio of rounding errors
+     * (Sigma itself is rounding-level where the reconstruction equals the
+     * cell values), which makes the limiter discontinuous to round-off. */
+    if (std::fabs(val(sum) - 1.0) <= ns * YSUM_TOL) return active;
     if (val(sum) > 1.0) {
       R d[MAXS], Sig(0.0);
       for (int k = 0; k < ns; ++k) {
@@ -1250,6 +1275,109 @@ int orc_cons_from_point(const orc_params* p, const double* W, double* U) {
   State<double> s;
   point_state(p, W, s);
   conserved_of<double>(p->ns, p->dim, s, U);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward-mode tangents: the same routines evaluated in Dual<1> arithmetic,  */
+/* i.e. exact directional derivatives of the oracle's own discrete map (with  */
+/* its branches taken on values).  dt and Gamma are inputs and carry no       */
+/* tangent.  The CPU reference for the discrete adjoint.                      */
+/* ------------------------------------------------------------------------ */
+typedef Dual<1> D1;
+
+static std::vector<D1> dual_of(const double* v, const double* dv, size_t n) {
+  std::vector<D1> out(n);
+  for (size_t i = 0; i < n; ++i) {
+    out[i].v = v[i];
+    out[i].d[0] = dv ? dv[i] : 0.0;
+  }
+  return out;
+}
+
+static void split(const std::vector<D1>& x, double* v, double* dv) {
+  for (size_t i = 0; i < x.size(); ++i) {
+    if (v) v[i] = x[i].v;
+    if (dv) dv[i] = x[i].d[0];
+  }
+}
+
+int orc_stage_jvp(const orc_params* p, const double* U_n, const double* U_k, const double* dU_k, double rk0,
+                  double rk1, double rk2, double dt, double Gamma, double* dUdt, double* d_dUdt) {
+  if (check(p)) return ORC_INVALID;
+  Solver<D1> s(*p);
+  const size_t n = (size_t)s.nv * s.G.ncell;
+  std::vector<D1> Un = dual_of(U_n, nullptr, n), Uk = dual_of(U_k, dU_k, n), L(n);
+  int st = s.stage(Un.data(), Uk.data(), rk0, rk1, rk2, dt, D1(Gamma), nullptr, L.data(), nullptr);
+  split(L, dUdt, d_dUdt);
+  return st;
+}
+
+int orc_rk_step_jvp(const orc_params* p, const double* U, const double* dU, double dt, double Gamma,
+                    double* U_out, double* dU_out) {
+  if (check(p) || !(dt > 0.0) || !(Gamma >= 0.0)) return ORC_INVALID;
+  Solver<D1> s(*p);
+  const size_t n = (size_t)s.nv * s.G.ncell;
+  std::vector<D1> Un = dual_of(U, dU, n), U1(n), U2(n), U3(n);
+  const D1 G(Gamma);
+  int st = s.stage(Un.data(), Un.data(), 1.0, 0.0, 1.0, dt, G, U1.data(), nullptr, nullptr);
+  st = std::max(st, s.stage(Un.data(), U1.data(), 0.75, 0.25, 0.25, dt, G, U2.data(), nullptr, nullptr));
+  st = std::max(st, s.stage(Un.data(), U2.data(), 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, dt, G, U3.data(), nullptr,
+                            nullptr));
+  split(U3, U_out, dU_out);
+  return st;
+}
+
+int orc_primitives_jvp(const orc_params* p, const double* U, const double* dU, double* out, double* dout) {
+  if (check(p)) return ORC_INVALID;
+  Solver<D1> s(*p);
+  const int nv = s.nv;
+  int st = ORC_OK;
+  for (size_t c = 0; c < s.G.ncell; ++c) {
+    D1 Uc[MAXV];
+    for (int v = 0; v < nv; ++v) {
+      Uc[v].v = U[(size_t)v * s.G.ncell + c];
+      Uc[v].d[0] = dU[(size_t)v * s.G.ncell + c];
+    }
+    Cell<D1> cl;
+    cell_from_conserved(*p, p->dim, Uc, cl);
+    st = std::max(st, cl.status);
+    D1 o[8] = {cl.P, cl.T, cl.a, cl.rho, cl.phi[0], cl.phi[1], cl.psi, -cl.psi};
+    for (int v = 0; v < 8; ++v) {
+      out[(size_t)v * s.G.ncell + c] = o[v].v;
+      dout[(size_t)v * s.G.ncell + c] = o[v].d[0];
+    }
+  }
+  return st;
+}
+
+double orc_weno5z_jvp(const double* v5, const double* dv5, double eps, double* dout) {
+  D1 v[5];
+  for (int j = 0; j < 5; ++j) {
+    v[j].v = v5[j];
+    v[j].d[0] = dv5[j];
+  }
+  D1 r = weno5z(v[0], v[1], v[2], v[3], v[4], eps);
+  *dout = r.d[0];
+  return r.v;
+}
+
+int orc_init_state_jvp(const orc_params* p, const double* prim, const double* dprim, double* U, double* dU) {
+  if (check(p)) return ORC_INVALID;
+  Solver<D1> s(*p);
+  const int ns = p->ns, D = p->dim, nv = ns + D + 1, nw = ns + D + 2;
+  for (size_t c = 0; c < s.G.ncell; ++c) {
+    D1 w[MAXV + 1], Uc[MAXV];
+    for (int v = 0; v < nw; ++v) {
+      w[v].v = prim[(size_t)v * s.G.ncell + c];
+      w[v].d[0] = dprim[(size_t)v * s.G.ncell + c];
+    }
+    s.conserved_from_primitive(w, Uc);
+    for (int v = 0; v < nv; ++v) {
+      U[(size_t)v * s.G.ncell + c] = Uc[v].v;
+      dU[(size_t)v * s.G.ncell + c] = Uc[v].d[0];
+    }
+  }
   return ORC_OK;
 }
 

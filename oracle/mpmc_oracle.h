@@ -115,6 +115,21 @@ int orc_physical_flux(const orc_params* p, int d, const double* W, double* F);
 /* conserved vector of a primitive point state W (layout as in orc_hllc_prim) */
 int orc_cons_from_point(const orc_params* p, const double* W, double* U);
 
+/* Forward-mode tangents (directional derivatives of the discrete map, its
+ * branches taken on values; dt and Gamma frozen), the CPU reference for the
+ * discrete adjoint.  Each returns the primal outputs as well. */
+int orc_stage_jvp(const orc_params* p, const double* U_n, const double* U_k, const double* dU_k,
+                  double rk0, double rk1, double rk2, double dt, double Gamma, double* dUdt,
+                  double* d_dUdt);
+/* one SSP-RK3 step with the given dt > 0 and Gamma >= 0 */
+int orc_rk_step_jvp(const orc_params* p, const double* U, const double* dU, double dt, double Gamma,
+                    double* U_out, double* dU_out);
+/* the eight fields of orc_primitives and their tangents */
+int orc_primitives_jvp(const orc_params* p, const double* U, const double* dU, double* out, double* dout);
+int orc_init_state_jvp(const orc_params* p, const double* prim, const double* dprim, double* U, double* dU);
+/* WENO5-Z value and tangent (ideal weights on a stencil flat to 1e-10) */
+double orc_weno5z_jvp(const double* v5, const double* dv5, double eps, double* dout);
+
 #ifdef __cplusplus
 }
 #endif

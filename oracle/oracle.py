@@ -90,6 +90,10 @@ def _declare(L):
         "orc_hllc_prim": [P, i, _dp, _dp, _dp],
         "orc_physical_flux": [P, i, _dp, _dp],
         "orc_cons_from_point": [P, _dp, _dp],
+        "orc_stage_jvp": [P, _dp, _dp, _dp, d, d, d, d, d, _dp, _dp],
+        "orc_rk_step_jvp": [P, _dp, _dp, d, d, _dp, _dp],
+        "orc_primitives_jvp": [P, _dp, _dp, _dp, _dp],
+        "orc_init_state_jvp": [P, _dp, _dp, _dp, _dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -97,6 +101,8 @@ def _declare(L):
         f.restype = ctypes.c_int
     L.orc_weno5z.argtypes = [_dp, d]
     L.orc_weno5z.restype = d
+    L.orc_weno5z_jvp.argtypes = [_dp, _dp, d, _dp]
+    L.orc_weno5z_jvp.restype = d
 
 
 def _ptr(a):
@@ -205,6 +211,42 @@ class Oracle:
         used = ctypes.c_double()
         st = self.lib.orc_rk_step(self.pp, _ptr(U), dt, ctypes.byref(used))
         return U, used.value, st
+
+    # ---- forward-mode tangents (dt and Gamma frozen) ----------------------------
+    def stage_jvp(self, U_n, U_k, dU_k, rk, dt, Gamma):
+        """(dUdt, d(dUdt)) of the stage at U_k in direction dU_k."""
+        U_n, U_k, dU_k = (np.ascontiguousarray(a, dtype=np.float64) for a in (U_n, U_k, dU_k))
+        L, dL = np.zeros_like(U_k), np.zeros_like(U_k)
+        st = self.lib.orc_stage_jvp(self.pp, _ptr(U_n), _ptr(U_k), _ptr(dU_k), rk[0], rk[1], rk[2], dt, Gamma,
+                                    _ptr(L), _ptr(dL))
+        return L, dL, st
+
+    def rk_step_jvp(self, U, dU, dt, Gamma):
+        U, dU = (np.ascontiguousarray(a, dtype=np.float64) for a in (U, dU))
+        Uo, dUo = np.zeros_like(U), np.zeros_like(U)
+        st = self.lib.orc_rk_step_jvp(self.pp, _ptr(U), _ptr(dU), dt, Gamma, _ptr(Uo), _ptr(dUo))
+        return Uo, dUo, st
+
+    def primitives_jvp(self, U, dU):
+        U, dU = (np.ascontiguousarray(a, dtype=np.float64) for a in (U, dU))
+        out, dout = np.zeros((8,) + self.shape), np.zeros((8,) + self.shape)
+        st = self.lib.orc_primitives_jvp(self.pp, _ptr(U), _ptr(dU), _ptr(out), _ptr(dout))
+        names = ("P", "T", "a", "rho", "phi0", "phi1", "psi0", "psi1")
+        return {k: out[i] for i, k in enumerate(names)}, {k: dout[i] for i, k in enumerate(names)}, st
+
+    def weno5z_jvp(self, v5, dv5, eps=None):
+        v5 = np.ascontiguousarray(v5, dtype=np.float64)
+        dv5 = np.ascontiguousarray(dv5, dtype=np.float64)
+        out = ctypes.c_double()
+        val = self.lib.orc_weno5z_jvp(_ptr(v5), _ptr(dv5), self.p.weno_eps if eps is None else eps,
+                                      ctypes.byref(out))
+        return val, out.value
+
+    def init_state_jvp(self, prim, dprim):
+        prim, dprim = (np.ascontiguousarray(a, dtype=np.float64) for a in (prim, dprim))
+        U, dU = np.zeros((self.nv,) + self.shape), np.zeros((self.nv,) + self.shape)
+        st = self.lib.orc_init_state_jvp(self.pp, _ptr(prim), _ptr(dprim), _ptr(U), _ptr(dU))
+        return U, dU, st
 
     def run(self, U, nsteps, t_end=0.0):
         U = np.ascontiguousarray(U).copy()

@@ -101,6 +101,14 @@ template <int N> inline Dual<N> cosh(const Dual<N>& a) {
 }
 template <int N> inline Dual<N> fabs(const Dual<N>& a) { return a.v < 0.0 ? -a : a; }
 
+/* x with its value replaced by v and its tangent kept */
+inline double with_value(double, double v) { return v; }
+template <int N> inline Dual<N> with_value(const Dual<N>& x, double v) {
+  Dual<N> r = x;
+  r.v = v;
+  return r;
+}
+
 /* value-based min / max that keep the chosen operand (and its tangent) */
 template <class R> inline R rmin(const R& a, const R& b) { return val(b) < val(a) ? b : a; }
 template <class R> inline R rmax(const R& a, const R& b) { return val(b) > val(a) ? b : a; }

@@ -15,6 +15,8 @@ constexpr double YTOL = 1e-14;
 constexpr double ABSENT = 1e-300;
 // |grad psi| below which the interface normal of the regularization is zero
 constexpr double GTOL = 1e-8;
+// per species: |sum Y - 1| up to which the Y limiter does not renormalize
+constexpr double YSUM_TOL = 1e-15;
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_ZEROGRAD = 2, BC_INFLOW = 3 };
 enum { ST_OK = 0, ST_INADMISSIBLE = 3, ST_EOS_NO_CONVERGE = 4 };
@@ -410,7 +412,9 @@ __device__ __forceinline__ bool y_limiter(double* Y, const double* Yc) {
   double sum = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) sum += Y[k];
-  if (sum != 1.0) {
+  // a sum that is one to rounding is left alone: the correction would be
+  // below the data's resolution and split by a ratio of rounding errors
+  if (fabs(sum - 1.0) > NS * YSUM_TOL) {
     const bool over = sum > 1.0;
     double dd[NS], Sig = 0.0;
 #pragma unroll
