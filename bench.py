@@ -163,6 +163,60 @@ def run_reference(args, rank, world):
     return 0
 
 
+def adjoint_section(mp, torch, nsteps=200, every=20, n=512):
+    """Reverse mode over `nsteps` SSP-RK3 steps of the 512 x 512 shock-interface
+    workload with a checkpoint every `every` steps: gradient of a
+    time-integrated pressure probe (one column of cells, x = 140 n/512) with
+    respect to the 16 Fourier amplitudes of the initial interface.  Forward
+    and backward are timed with CUDA events; the ratio is backward/forward."""
+    from paper_2504_14063_gb300 import autograd as ag
+    from paper_2504_14063_gb300 import workloads as W
+    p = W.shock_interface_2d(n=n, seed=3)
+    ctx = mp.Context(p)
+    col = int(round(140 * n / 512))
+    w = np.zeros(p.prim.shape[1:])
+    w[..., col] = 1.0 / w[..., col].size
+    probe = torch.from_numpy(w).cuda()
+    phi_l = torch.from_numpy(p.prim[2, 0]).cuda()
+    rest = torch.from_numpy(p.prim[2:]).cuda()
+    amps0 = torch.from_numpy(W.seeded_fourier_amplitudes(3, 8, 1.0)).cuda()
+
+    def forward(amps, steps):
+        a0, a1 = W.interface_fractions(n, amps, phi_l, xp=torch)
+        prim = torch.cat([a0[None, None], a1[None, None], rest], 0)
+        U0 = ag.init_state(ctx, prim)
+        return ag.rollout(ctx, U0, steps, every=every, probe=probe)
+
+    # warm-up (graph capture, adjoint scratch)
+    a = amps0.clone().requires_grad_(True)
+    _, J, _ = forward(a, 3)
+    torch.autograd.grad(J, a)
+    torch.cuda.synchronize()
+    a = amps0.clone().requires_grad_(True)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ctx.profile(reset=True)
+    e[0].record()
+    UN, J, dts = forward(a, nsteps)
+    e[1].record()
+    ctx.set_profiling(True)
+    grad, = torch.autograd.grad(J, a)
+    e[2].record()
+    torch.cuda.synchronize()
+    ctx.set_profiling(False)
+    prof = ctx.profile(reset=True)
+    fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    state_mb = ctx.nv * ctx.ncells * 8 / 2 ** 20
+    return {"workload": f"shock_interface_2d {n}x{n}, {nsteps} SSP-RK3 steps, checkpoint every {every} steps",
+            "functional": f"sum_k dt_k mean_y P(x={col}, y, t_k); gradient w.r.t. 16 interface Fourier amplitudes",
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms, "ratio": bwd_ms / fwd_ms,
+            "backward_kernel_ms": {k: v[0] for k, v in prof.items() if v[1]},
+            "memory_mb": {"state": state_mb, "checkpoints": state_mb * len(range(0, nsteps, every)),
+                          "segment_states": state_mb * (every + 1)},
+            "J": float(J), "grad_norm": float(grad.norm()), "status": ctx.status(),
+            "note": "backward = per segment one forward replay step per step + per step the reverse of "
+                    "SSP-RK3 (stage states recomputed inside the reverse call)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,6 +227,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--compare-steps", type=int, default=100)
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -285,6 +340,10 @@ def main():
                  "status": mstat}
         del ctxm, Um, A, B
 
+    adjoint = None
+    if not args.no_adjoint and rank == 0:
+        adjoint = adjoint_section(mp, torch)
+
     # ---- end to end through the host-buffer entry --------------------------
     H = U.cpu().pin_memory()
     ctx.step_n_host(H, 1)
@@ -316,6 +375,8 @@ def main():
         }
         if mixed is not None:
             line["mixed"] = mixed
+        if adjoint is not None:
+            line["adjoint"] = adjoint
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
         print(json.dumps(line), flush=True)

@@ -174,14 +174,51 @@ int mpmc_step_n_host(mpmc_ctx* ctx, double* U_host, int n);
  * writes [dt, Gamma] to out_dev (2 doubles, device). */
 int mpmc_dt_gamma(mpmc_ctx* ctx, const double* U, double* out_dev);
 
-/* Discrete adjoint of one stage (vector-Jacobian product of L with the
- * limiter decisions of the forward pass replayed from `tape`, dt and Gamma
- * frozen): lam_U += (dL/dU)^T lam_dUdt.  U: the stage input U^(k); stage:
- * as for mpmc_rhs (U_n, rk, dt, Gamma, all explicit: dt > 0, Gamma >= 0);
- * tape: flags of that stage (from mpmc_rhs or mpmc_rk_step); lam_dUdt,
- * lam_U: device, layout of U. */
+/* ---- Discrete adjoint (FP64 contexts; MPMC_INVALID_ARG on a mixed one) ----
+ * The adjoint of the discrete map itself: every discrete decision of the
+ * forward pass (interpolation limiters theta_T / theta_P of Sec. 3.3.1,
+ * first-order fallback of the flux limiter of Sec. 3.3.2, dropped
+ * regularization flux) is replayed from its flag bits, the Y limiter of
+ * Sec. 3.3.1 is differentiated on the branch the forward took, and dt and
+ * Gamma (Sec. 3.4, Sec. 3.2) are frozen at the forward values.  A species
+ * with Y_k = 0 exactly contributes no sensitivity (the forward omits it).
+ * Adjoint scratch (cache adjoint, two state-sized buffers, one step of flags)
+ * is allocated on the first call; MPMC_OUT_OF_MEMORY if that fails.
+ *
+ * lam_U += (dL/dU)^T lam_dUdt for the stage of mpmc_rhs at U.  stage: as for
+ * mpmc_rhs (nullable; dt <= 0 / Gamma < 0 are recomputed from U_n exactly as
+ * the forward did); tape: that call's flags (nullable: the decisions are
+ * recomputed); lam_dUdt, lam_U: device, layout of U. */
 int mpmc_rhs_adjoint(mpmc_ctx* ctx, const double* U, const mpmc_stage* stage, const uint32_t* tape,
                      const double* lam_dUdt, double* lam_U);
+
+/* One SSP-RK3 step like mpmc_rk_step that also keeps what its reverse needs:
+ * U_stages (device, 2 x nv x ncells, caller-owned) receives the stage states
+ * U^(1) and U^(2); tape (nullable, device, 3 x faces uint32) the flags. */
+int mpmc_rk_step_record(mpmc_ctx* ctx, double* U, double dt, uint32_t* tape, double* U_stages);
+
+/* Reverse of one SSP-RK3 step (Eq. SSPRK3) from U_n:
+ *   lam_n = (dU^{n+1}/dU^n)^T lam_next.
+ * dt: as passed to mpmc_rk_step (<= 0: the CFL step of U_n, recomputed
+ * bit-identically).  U_stages (nullable): the step's stage states from
+ * mpmc_rk_step_record; recomputed from U_n when null.  tape: that step's
+ * 3 x faces flags (nullable: recomputed).  lam_n may equal lam_next (in
+ * place).  Device arrays, layout of U.  The result does not depend on the
+ * order in which the GPU runs threads (no atomic accumulation). */
+int mpmc_rk_step_adjoint(mpmc_ctx* ctx, const double* U_n, const double* U_stages, double dt, const uint32_t* tape,
+                         const double* lam_next, double* lam_n);
+
+/* Reverse of mpmc_init_state: lam_prim = (dU/dprim)^T lam_U, layouts as for
+ * mpmc_init_state (prim: the forward's input). */
+int mpmc_init_state_adjoint(mpmc_ctx* ctx, const double* prim, const double* lam_U, double* lam_prim);
+
+/* Primitive variables of U (Sec. 2.2-2.3): out (device, (4 + ns + dim) x
+ * ncells FP64) = [T, P, rho, a, Y_0..Y_{ns-1}, u_0..u_{dim-1}], each a row of
+ * ncells in the cell order of U.  FP64 contexts. */
+int mpmc_primitives(mpmc_ctx* ctx, const double* U, double* out);
+
+/* lam_U += (dW/dU)^T lam_W for W = mpmc_primitives(U); lam_W in that layout. */
+int mpmc_primitives_adjoint(mpmc_ctx* ctx, const double* U, const double* lam_W, double* lam_U);
 
 /* Statistics of the limiters since the last reset (synchronizes). */
 int mpmc_get_stats(mpmc_ctx* ctx, mpmc_stats* out, int reset);
@@ -193,7 +230,8 @@ int mpmc_get_status(mpmc_ctx* ctx, int reset);
  * synchronization).  mpmc_get_profile synchronizes and returns, per kernel
  * family, the summed device time in ms and the launch count:
  * [0] primitive recovery, [1] face fluxes, [2] divergence + RK update,
- * [3] time-step scalars.  reset != 0 clears the sums. */
+ * [3] time-step scalars, [4] adjoint face kernels, [5] adjoint primitive
+ * kernels: ms and launches must hold 6 entries.  reset != 0 clears the sums. */
 int mpmc_set_profiling(mpmc_ctx* ctx, int enable);
 int mpmc_get_profile(mpmc_ctx* ctx, double* ms, uint64_t* launches, int reset);
 

@@ -75,6 +75,11 @@ def _load():
         "mpmc_step_n_host": (i, [vp, vp, i]),
         "mpmc_dt_gamma": (i, [vp, vp, vp]),
         "mpmc_rhs_adjoint": (i, [vp, vp, ctypes.POINTER(StageC), vp, vp, vp]),
+        "mpmc_rk_step_record": (i, [vp, vp, d, vp, vp]),
+        "mpmc_rk_step_adjoint": (i, [vp, vp, vp, d, vp, vp, vp]),
+        "mpmc_init_state_adjoint": (i, [vp, vp, vp, vp]),
+        "mpmc_primitives": (i, [vp, vp, vp]),
+        "mpmc_primitives_adjoint": (i, [vp, vp, vp, vp]),
         "mpmc_get_stats": (i, [vp, ctypes.POINTER(StatsC), i]),
         "mpmc_get_status": (i, [vp, i]),
         "mpmc_last_error": (ctypes.c_char_p, [vp]),
@@ -217,26 +222,78 @@ class Context:
         self._check(lib.mpmc_dt_gamma(self.h, _dev(U), _dev(out)))
         return out
 
-    def rhs_adjoint(self, U, stage, tape, lam_dUdt, lam_U=None):
-        lam_U = torch.zeros_like(U) if lam_U is None else lam_U
+    @staticmethod
+    def _stage(stage):
+        if stage is None:
+            return None
         sc = StageC()
-        sc.U_n = _dev(stage["U_n"])
-        sc.rk0, sc.rk1, sc.rk2 = stage["rk"]
-        sc.dt = stage["dt"]
-        sc.Gamma = stage["Gamma"]
-        self._check(lib.mpmc_rhs_adjoint(self.h, _dev(U), ctypes.byref(sc), _ptr(tape), _dev(lam_dUdt),
-                                         _dev(lam_U)))
+        sc.U_n = _dev(stage["U_n"]) if stage.get("U_n") is not None else None
+        sc.rk0, sc.rk1, sc.rk2 = stage.get("rk", (1.0, 0.0, 1.0))
+        sc.dt = stage.get("dt", 0.0)
+        sc.Gamma = stage.get("Gamma", -1.0)
+        return sc
+
+    # ---- discrete adjoint (FP64 contexts) ------------------------------------
+    def rhs_adjoint(self, U, stage, tape, lam_dUdt, lam_U=None):
+        """lam_U += (dL/dU)^T lam_dUdt with the decisions of the forward stage
+        (tape from rhs(flags=...), or None to recompute them)."""
+        lam_U = torch.zeros_like(U) if lam_U is None else lam_U
+        sc = self._stage(stage)
+        self._check(lib.mpmc_rhs_adjoint(self.h, _dev(U), ctypes.byref(sc) if sc is not None else None, _ptr(tape),
+                                         _dev(lam_dUdt), _dev(lam_U)))
+        return lam_U
+
+    def rk_step_record(self, U, dt=0.0, tape=None, stages=None):
+        """One SSP-RK3 step in place that also returns its stage states
+        (2 x state: U^(1), U^(2)) and fills `tape` (3 x faces uint32) if given."""
+        stages = torch.empty((2,) + tuple(U.shape), dtype=U.dtype, device=U.device) if stages is None else stages
+        self._check(lib.mpmc_rk_step_record(self.h, _dev(U), float(dt), _ptr(tape), _dev(stages)))
+        return stages
+
+    def rk_step_adjoint(self, U_n, lam_next, dt=0.0, tape=None, lam_n=None, stages=None):
+        """lam_n = (dU^{n+1}/dU^n)^T lam_next for the SSP-RK3 step from U_n
+        (dt and Gamma frozen; dt <= 0: the CFL step of U_n).  stages/tape:
+        from rk_step_record (recomputed when None).  lam_n may be lam_next
+        (in place)."""
+        lam_n = torch.empty_like(lam_next) if lam_n is None else lam_n
+        self._check(lib.mpmc_rk_step_adjoint(self.h, _dev(U_n), _ptr(stages), float(dt), _ptr(tape),
+                                             _dev(lam_next), _dev(lam_n)))
+        return lam_n
+
+    def init_state_adjoint(self, prim, lam_U):
+        prim = prim.to(self.device, torch.float64).contiguous()
+        lam_prim = torch.empty_like(prim)
+        self._check(lib.mpmc_init_state_adjoint(self.h, _dev(prim), _dev(lam_U), _dev(lam_prim)))
+        return lam_prim
+
+    @property
+    def prim_fields(self):
+        ns, D = self.problem.ns, self.problem.dim
+        return ["T", "P", "rho", "a"] + [f"Y{k}" for k in range(ns)] + [f"u{d}" for d in range(D)]
+
+    def primitives(self, U, out=None):
+        """[T, P, rho, a, Y_k, u_d] per cell, shape (4 + ns + D, nz, ny, nx)."""
+        if out is None:
+            out = torch.empty((len(self.prim_fields),) + self.shape[1:], dtype=torch.float64, device=self.device)
+        self._check(lib.mpmc_primitives(self.h, _dev(U), _dev(out)))
+        return out
+
+    def primitives_adjoint(self, U, lam_W, lam_U=None):
+        """lam_U += (dW/dU)^T lam_W, W as returned by primitives()."""
+        lam_U = torch.zeros_like(U) if lam_U is None else lam_U
+        self._check(lib.mpmc_primitives_adjoint(self.h, _dev(U), _dev(lam_W.contiguous()), _dev(lam_U)))
         return lam_U
 
     def set_profiling(self, enable=True):
         self._check(lib.mpmc_set_profiling(self.h, 1 if enable else 0))
 
     def profile(self, reset=False):
-        """{family: (ms, launches)} for prim, face, update, dt."""
-        ms = (ctypes.c_double * 4)()
-        n = (ctypes.c_uint64 * 4)()
+        """{family: (ms, launches)} for prim, face, update, dt and the adjoint's
+        face and prim kernels."""
+        ms = (ctypes.c_double * 6)()
+        n = (ctypes.c_uint64 * 6)()
         self._check(lib.mpmc_get_profile(self.h, ms, n, 1 if reset else 0))
-        return {k: (ms[i], n[i]) for i, k in enumerate(("prim", "face", "update", "dt"))}
+        return {k: (ms[i], n[i]) for i, k in enumerate(("prim", "face", "update", "dt", "adj_face", "adj_prim"))}
 
     def status(self, reset=False):
         return lib.mpmc_get_status(self.h, 1 if reset else 0)
@@ -270,6 +327,26 @@ def step_n(ctx, U, n, dt_out=None):
 
 def rhs_adjoint(ctx, U, stage, tape, lam_dUdt, lam_U=None):
     return ctx.rhs_adjoint(U, stage, tape, lam_dUdt, lam_U)
+
+
+def rk_step_record(ctx, U, dt=0.0, tape=None, stages=None):
+    return ctx.rk_step_record(U, dt, tape, stages)
+
+
+def rk_step_adjoint(ctx, U_n, lam_next, dt=0.0, tape=None, lam_n=None, stages=None):
+    return ctx.rk_step_adjoint(U_n, lam_next, dt, tape, lam_n, stages)
+
+
+def init_state_adjoint(ctx, prim, lam_U):
+    return ctx.init_state_adjoint(prim, lam_U)
+
+
+def primitives(ctx, U, out=None):
+    return ctx.primitives(U, out)
+
+
+def primitives_adjoint(ctx, U, lam_W, lam_U=None):
+    return ctx.primitives_adjoint(U, lam_W, lam_U)
 
 
 workloads = _wl

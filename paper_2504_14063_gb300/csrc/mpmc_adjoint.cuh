@@ -1,0 +1,426 @@
+// Discrete adjoint of the FP64 stage (reverse of k_prim / k_face / k_update)
+// with the discrete decisions of the forward pass (interpolation limiters,
+// first-order fallback, dropped regularization flux) replayed from the tape;
+// dt and Gamma are frozen.  Each block of the face pipeline is recomputed
+// forward and swept in reverse by hand.  The p-T equilibrium is reversed
+// through the implicit-function theorem of its two defining equations
+// (NASG_T1 and NASG_T2), which holds for the closed form and for the Newton
+// solve alike.
+#pragma once
+#include "mpmc_device.cuh"
+
+namespace mpmc {
+namespace adj {
+
+// ---------------------------------------------------------------------------
+// WENO5-Z (the kernel's form with one common denominator) and its reverse
+struct Weno {
+  double v[5], q[3], t[3], s[3], c[3], A[3], tau, S, out;
+  int sg;
+  bool flat;
+};
+
+// relative stencil variation below which the weights are noise: the
+// derivative there is taken with the ideal weights (the value is each
+// candidate to rounding, and the weights' own derivative grows like 1/eps)
+constexpr double WENO_FLAT = 1e-10;
+
+__device__ __forceinline__ double weno_fwd(Weno& w, double v0, double v1, double v2, double v3, double v4,
+                                           double eps) {
+  w.v[0] = v0; w.v[1] = v1; w.v[2] = v2; w.v[3] = v3; w.v[4] = v4;
+  w.q[0] = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
+  w.q[1] = (-v1 + 5.0 * v2 + 2.0 * v3) * (1.0 / 6.0);
+  w.q[2] = (2.0 * v2 + 5.0 * v3 - v4) * (1.0 / 6.0);
+  w.t[0] = v0 - 2.0 * v1 + v2;
+  w.s[0] = v0 - 4.0 * v1 + 3.0 * v2;
+  w.t[1] = v1 - 2.0 * v2 + v3;
+  w.s[1] = v1 - v3;
+  w.t[2] = v2 - 2.0 * v3 + v4;
+  w.s[2] = 3.0 * v2 - 4.0 * v3 + v4;
+  double b[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) b[k] = (13.0 / 12.0) * w.t[k] * w.t[k] + 0.25 * w.s[k] * w.s[k];
+  {
+    double M = 0.0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) M = fmax(M, fabs(w.v[j]));
+    const double tol = (WENO_FLAT * M) * (WENO_FLAT * M);
+    w.flat = b[0] <= tol && b[1] <= tol && b[2] <= tol;
+  }
+  w.sg = (b[0] - b[2]) >= 0.0 ? 1 : -1;
+  w.tau = fabs(b[0] - b[2]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w.c[k] = b[k] + eps;
+  w.A[0] = 0.1 * (w.c[0] + w.tau) * w.c[1] * w.c[2];
+  w.A[1] = 0.6 * (w.c[1] + w.tau) * w.c[0] * w.c[2];
+  w.A[2] = 0.3 * (w.c[2] + w.tau) * w.c[0] * w.c[1];
+  w.S = w.A[0] + w.A[1] + w.A[2];
+  w.out = (w.A[0] * w.q[0] + w.A[1] * w.q[1] + w.A[2] * w.q[2]) / w.S;
+  return w.out;
+}
+
+// adds d(out)/d(v) * lam to gv[0..4]
+__device__ __forceinline__ void weno_rev(const Weno& w, double lam, double* gv) {
+  if (w.flat) {
+    // ideal weights 1/10, 6/10, 3/10 on the three candidates
+    gv[0] += lam * (1.0 / 30.0);
+    gv[1] += lam * (-13.0 / 60.0);
+    gv[2] += lam * (47.0 / 60.0);
+    gv[3] += lam * (9.0 / 20.0);
+    gv[4] += lam * (-1.0 / 20.0);
+    return;
+  }
+  const double lN = lam / w.S, lS = -lam * w.out / w.S;
+  double lA[3], lc[3] = {0.0, 0.0, 0.0}, ltau = 0.0, lq[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lA[k] = lN * w.q[k] + lS;
+    lq[k] = lN * w.A[k];
+  }
+  const double* c = w.c;
+  const double tau = w.tau;
+  double a = lA[0] * 0.1;
+  lc[0] += a * c[1] * c[2]; ltau += a * c[1] * c[2]; lc[1] += a * (c[0] + tau) * c[2]; lc[2] += a * (c[0] + tau) * c[1];
+  a = lA[1] * 0.6;
+  lc[1] += a * c[0] * c[2]; ltau += a * c[0] * c[2]; lc[0] += a * (c[1] + tau) * c[2]; lc[2] += a * (c[1] + tau) * c[0];
+  a = lA[2] * 0.3;
+  lc[2] += a * c[0] * c[1]; ltau += a * c[0] * c[1]; lc[0] += a * (c[2] + tau) * c[1]; lc[1] += a * (c[2] + tau) * c[0];
+  double lb[3] = {lc[0], lc[1], lc[2]};
+  lb[0] += w.sg * ltau;
+  lb[2] -= w.sg * ltau;
+  double lt[3], ls[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lt[k] = lb[k] * (13.0 / 6.0) * w.t[k];
+    ls[k] = lb[k] * 0.5 * w.s[k];
+  }
+  gv[0] += lt[0] + ls[0] + lq[0] * (2.0 / 6.0);
+  gv[1] += -2.0 * lt[0] - 4.0 * ls[0] + lt[1] + ls[1] - lq[0] * (7.0 / 6.0) - lq[1] * (1.0 / 6.0);
+  gv[2] += lt[0] + 3.0 * ls[0] - 2.0 * lt[1] + lt[2] + 3.0 * ls[2] + lq[0] * (11.0 / 6.0) + lq[1] * (5.0 / 6.0) +
+           lq[2] * (2.0 / 6.0);
+  gv[3] += lt[1] - ls[1] - 2.0 * lt[2] - 4.0 * ls[2] + lq[1] * (2.0 / 6.0) + lq[2] * (5.0 / 6.0);
+  gv[4] += lt[2] + ls[2] - lq[2] * (1.0 / 6.0);
+}
+
+// ---------------------------------------------------------------------------
+// Thermodynamic sums at (P, T, Y) shared by the forward EOS, the sound speed
+// and their reverse.
+template <int NS>
+struct Thermo {
+  double Y[NS], p, T;
+  double r[NS];          // 1 / (P + Pinf_k)
+  double v, e, cp, sa, sb, rho, al, be, den, a;
+};
+
+template <int NS>
+__device__ __forceinline__ void thermo_fwd(const KParams& P, Thermo<NS>& t) {
+  t.v = 0.0; t.e = 0.0; t.cp = 0.0; t.sa = 0.0; t.sb = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    t.r[k] = 1.0 / (t.p + P.pinf[k]);
+    if (t.Y[k] != 0.0) {
+      const double RT = P.Rk[k] * t.T;
+      t.v += t.Y[k] * (RT * t.r[k] + P.b[k]);
+      t.e += t.Y[k] * (P.cv[k] * t.T * (t.p + P.gam[k] * P.pinf[k]) * t.r[k] + P.q[k]);
+      t.cp += t.Y[k] * P.cp[k];
+      t.sa += t.Y[k] * P.Rk[k] * t.r[k];
+      t.sb += t.Y[k] * RT * t.r[k] * t.r[k];
+    }
+  }
+  t.rho = 1.0 / t.v;
+  t.al = t.rho * t.sa;
+  t.be = t.rho * t.sb;
+  t.den = t.rho * t.be * t.cp - t.al * t.al * t.T;
+  t.a = sqrt(t.cp / t.den);
+}
+
+// reverse of thermo_fwd: adjoints of (rho, e, a, alpha, beta) -> (Y, P, T)
+template <int NS>
+__device__ __forceinline__ void thermo_rev(const KParams& P, const Thermo<NS>& t, double lrho, double le, double la,
+                                           double lal, double lbe, double* lY, double& lp, double& lT) {
+  // a = sqrt(cp / den)
+  double lcp = 0.0, lden = 0.0;
+  if (la != 0.0) {
+    const double g = la * 0.5 / t.a;
+    lcp += g / t.den;
+    lden -= g * t.cp / (t.den * t.den);
+  }
+  // den = rho be cp - al^2 T
+  lrho += lden * t.be * t.cp;
+  lbe += lden * t.rho * t.cp;
+  lcp += lden * t.rho * t.be;
+  lal -= lden * 2.0 * t.al * t.T;
+  lT -= lden * t.al * t.al;
+  // al = rho sa, be = rho sb
+  lrho += lal * t.sa + lbe * t.sb;
+  const double lsa = lal * t.rho, lsb = lbe * t.rho;
+  // rho = 1 / v
+  const double lv = -lrho * t.rho * t.rho;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    if (t.Y[k] == 0.0) continue;
+    const double r = t.r[k], RT = P.Rk[k] * t.T, pg = t.p + P.gam[k] * P.pinf[k];
+    const double vk = RT * r + P.b[k];
+    const double ek = P.cv[k] * t.T * pg * r + P.q[k];
+    lY[k] += lv * vk + le * ek + lcp * P.cp[k] + lsa * P.Rk[k] * r + lsb * RT * r * r;
+    const double y = t.Y[k];
+    // d/dT
+    lT += lv * y * P.Rk[k] * r + le * y * P.cv[k] * pg * r + lsb * y * P.Rk[k] * r * r;
+    // d/dP: through pg in ek and through r everywhere
+    lp += le * y * P.cv[k] * t.T * r;
+    const double lr = lv * y * RT + le * y * P.cv[k] * t.T * pg + lsa * y * P.Rk[k] + lsb * y * RT * 2.0 * r;
+    lp -= lr * r * r;
+  }
+}
+
+// Reverse of the p-T equilibrium (Y, e, v) -> (P, T) by the implicit-function
+// theorem of   G1 = T A(P,Y) - (v - b) = 0,   G2 = T B(P,Y) - (e - q) = 0,
+// A = sum Y_k R_k / (P + Pinf_k)  (NASG_T2),  B = sum Y_k cv_k (P + g Pinf)/(P + Pinf)  (NASG_T1).
+template <int NS>
+__device__ __forceinline__ void pt_rev(const KParams& P, const double* Y, double p, double T, double lp, double lT,
+                                       double* lY, double& le, double& lv) {
+  double A = 0.0, B = 0.0, AP = 0.0, BP = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    if (Y[k] == 0.0) continue;
+    const double r = 1.0 / (p + P.pinf[k]);
+    A += Y[k] * P.Rk[k] * r;
+    AP -= Y[k] * P.Rk[k] * r * r;
+    const double g = (p + P.gam[k] * P.pinf[k]) * r;
+    B += Y[k] * P.cv[k] * g;
+    // d/dP of (P + g Pinf)/(P + Pinf) = (Pinf - g Pinf) r^2
+    BP += Y[k] * P.cv[k] * (P.pinf[k] - P.gam[k] * P.pinf[k]) * r * r;
+  }
+  // J = [[T AP, A], [T BP, B]] (rows G1, G2; columns P, T); solve J^T mu = (lp, lT)
+  const double j11 = T * AP, j12 = A, j21 = T * BP, j22 = B;
+  const double det = j11 * j22 - j12 * j21;
+  // J^T = [[j11, j21], [j12, j22]]
+  const double mu1 = (lp * j22 - lT * j21) / det;
+  const double mu2 = (j11 * lT - j12 * lp) / det;
+  // lambda_x = -mu^T dG/dx
+  lv += mu1;   // dG1/dv = -1
+  le += mu2;   // dG2/de = -1
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    if (Y[k] == 0.0) continue;
+    const double r = 1.0 / (p + P.pinf[k]);
+    const double dG1 = T * P.Rk[k] * r + P.b[k];
+    const double dG2 = T * P.cv[k] * (p + P.gam[k] * P.pinf[k]) * r + P.q[k];
+    lY[k] -= mu1 * dG1 + mu2 * dG2;
+  }
+}
+
+// reverse of decode: U -> (rho, Y, u, e, v); adds into lU
+template <int NS, int D>
+__device__ __forceinline__ void decode_rev(const double* U, double rho, const double* Y, const double* u, double lrho,
+                                           const double* lY, const double* lu, double le, double lv, double* lU) {
+  // e = E/rho - |u|^2/2, v = 1/rho, u = m/rho, Y = U/rho, rho = sum U_k
+  double lu2[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) lu2[t] = (t < D ? lu[t] : 0.0) - le * u[t];
+  lU[NS + D] += le / rho;
+  lrho -= le * U[NS + D] / (rho * rho);
+  lrho -= lv / (rho * rho);
+#pragma unroll
+  for (int t = 0; t < D; ++t) {
+    lU[NS + t] += lu2[t] / rho;
+    lrho -= lu2[t] * u[t] / rho;
+  }
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    lU[k] += lY[k] / rho;
+    lrho -= lY[k] * Y[k] / rho;
+  }
+#pragma unroll
+  for (int k = 0; k < NS; ++k) lU[k] += lrho;
+}
+
+// ---------------------------------------------------------------------------
+// HLLC (Appendix B), forward with intermediates, and reverse
+template <int NS>
+struct St {
+  double rho, rhoY[NS], u[3], m[3], p, E, a;
+};
+
+template <int NS>
+struct StAdj {
+  double rho, rhoY[NS], u[3], m[3], p, E, a;
+  __device__ __forceinline__ void zero() {
+    rho = 0.0; p = 0.0; E = 0.0; a = 0.0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) rhoY[k] = 0.0;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) { u[t] = 0.0; m[t] = 0.0; }
+  }
+};
+
+template <int NS, int D>
+__device__ __forceinline__ void hllc_rev(int d, const St<NS>& L, const St<NS>& R, const double* lF, StAdj<NS>& gL,
+                                         StAdj<NS>& gR) {
+  const double ub = 0.5 * (L.u[d] + R.u[d]), ab = 0.5 * (L.a + R.a);
+  const bool bl = (ub - ab) <= (L.u[d] - L.a);   // fmin(ub - ab, uL - aL) picks ub - ab
+  const double sL = bl ? ub - ab : L.u[d] - L.a;
+  const bool br = (ub + ab) >= (R.u[d] + R.a);
+  const double sR = br ? ub + ab : R.u[d] + R.a;
+  const double sm = fmin(0.0, sL), sp = fmax(0.0, sR);
+  const double dL = sL - L.u[d], dR = sR - R.u[d];
+  const double num = R.p - L.p + L.rho * L.u[d] * dL - R.rho * R.u[d] * dR;
+  const double den = L.rho * dL - R.rho * dR;
+  const double ss = num / den;
+  const double wl = ss > 0.0 ? 1.0 : (ss < 0.0 ? 0.0 : 0.5);
+  const double wr = 1.0 - wl;
+  const double eL = sL - ss, eR = sR - ss;
+  const double fL = dL / eL, fR = dR / eR;
+  double lsm = 0.0, lsp = 0.0, lfL = 0.0, lfR = 0.0, lss = 0.0, ldL = 0.0, ldR = 0.0;
+  // species
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const double a = wl * lF[k], b = wr * lF[k];
+    gL.rhoY[k] += a * (L.u[d] + sm * (fL - 1.0));
+    gL.u[d] += a * L.rhoY[k];
+    lsm += a * (fL * L.rhoY[k] - L.rhoY[k]);
+    lfL += a * sm * L.rhoY[k];
+    gR.rhoY[k] += b * (R.u[d] + sp * (fR - 1.0));
+    gR.u[d] += b * R.rhoY[k];
+    lsp += b * (fR * R.rhoY[k] - R.rhoY[k]);
+    lfR += b * sp * R.rhoY[k];
+  }
+  // momentum
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const double a = wl * lF[NS + j], b = wr * lF[NS + j];
+    // FL = rhoL uLd uLj + (j==d) PL ; UsL = fL rhoL (j==d ? ss : uLj)
+    const double vjL = j == d ? ss : L.u[j], vjR = j == d ? ss : R.u[j];
+    const double UsL = fL * L.rho * vjL, UsR = fR * R.rho * vjR;
+    gL.rho += a * (L.u[d] * L.u[j] + sm * fL * vjL);
+    gL.u[d] += a * L.rho * L.u[j];
+    gL.u[j] += a * L.rho * L.u[d];
+    if (j == d) gL.p += a;
+    lsm += a * (UsL - L.m[j]);
+    lfL += a * sm * L.rho * vjL;
+    if (j == d) lss += a * sm * fL * L.rho;
+    else gL.u[j] += a * sm * fL * L.rho;
+    gL.m[j] -= a * sm;
+    gR.rho += b * (R.u[d] * R.u[j] + sp * fR * vjR);
+    gR.u[d] += b * R.rho * R.u[j];
+    gR.u[j] += b * R.rho * R.u[d];
+    if (j == d) gR.p += b;
+    lsp += b * (UsR - R.m[j]);
+    lfR += b * sp * R.rho * vjR;
+    if (j == d) lss += b * sp * fR * R.rho;
+    else gR.u[j] += b * sp * fR * R.rho;
+    gR.m[j] -= b * sp;
+  }
+  // energy: F = u (E + P) + s (f (E + (ss - u)(rho ss + P/dK)) - E)
+  {
+    const double a = wl * lF[NS + D], b = wr * lF[NS + D];
+    const double kL = L.rho * ss + L.p / dL, kR = R.rho * ss + R.p / dR;
+    const double inL = L.E + (ss - L.u[d]) * kL, inR = R.E + (ss - R.u[d]) * kR;
+    gL.u[d] += a * (L.E + L.p);
+    gL.E += a * (L.u[d] + sm * (fL - 1.0));
+    gL.p += a * L.u[d];
+    lsm += a * (fL * inL - L.E);
+    lfL += a * sm * inL;
+    {
+      const double g = a * sm * fL;   // adjoint of inL
+      lss += g * kL;
+      gL.u[d] -= g * kL;
+      const double gk = g * (ss - L.u[d]);
+      gL.rho += gk * ss;
+      lss += gk * L.rho;
+      gL.p += gk / dL;
+      ldL -= gk * L.p / (dL * dL);
+    }
+    gR.u[d] += b * (R.E + R.p);
+    gR.E += b * (R.u[d] + sp * (fR - 1.0));
+    gR.p += b * R.u[d];
+    lsp += b * (fR * inR - R.E);
+    lfR += b * sp * inR;
+    {
+      const double g = b * sp * fR;
+      lss += g * kR;
+      gR.u[d] -= g * kR;
+      const double gk = g * (ss - R.u[d]);
+      gR.rho += gk * ss;
+      lss += gk * R.rho;
+      gR.p += gk / dR;
+      ldR -= gk * R.p / (dR * dR);
+    }
+  }
+  // fK = dK / (sK - ss)
+  double lsL = 0.0, lsR = 0.0;
+  ldL += lfL / eL;
+  lsL -= lfL * dL / (eL * eL);
+  lss += lfL * dL / (eL * eL);
+  ldR += lfR / eR;
+  lsR -= lfR * dR / (eR * eR);
+  lss += lfR * dR / (eR * eR);
+  // ss = num / den
+  const double lnum = lss / den, lden = -lss * ss / den;
+  gR.p += lnum;
+  gL.p -= lnum;
+  gL.rho += lnum * L.u[d] * dL + lden * dL;
+  gL.u[d] += lnum * L.rho * dL;
+  ldL += lnum * L.rho * L.u[d] + lden * L.rho;
+  gR.rho -= lnum * R.u[d] * dR + lden * dR;
+  gR.u[d] -= lnum * R.rho * dR;
+  ldR -= lnum * R.rho * R.u[d] + lden * R.rho;
+  // dK = sK - uK
+  lsL += ldL;
+  gL.u[d] -= ldL;
+  lsR += ldR;
+  gR.u[d] -= ldR;
+  if (sL < 0.0) lsL += lsm;
+  if (sR > 0.0) lsR += lsp;
+  double lub = 0.0, lab = 0.0;
+  if (bl) { lub += lsL; lab -= lsL; } else { gL.u[d] += lsL; gL.a -= lsL; }
+  if (br) { lub += lsR; lab += lsR; } else { gR.u[d] += lsR; gR.a += lsR; }
+  gL.u[d] += 0.5 * lub;
+  gR.u[d] += 0.5 * lub;
+  gL.a += 0.5 * lab;
+  gR.a += 0.5 * lab;
+}
+
+// face-side state from (Y, u, P, T) and its reverse (adjoint of the state ->
+// adjoints of Y, u, P, T)
+template <int NS>
+__device__ __forceinline__ void face_state(const KParams& P, Thermo<NS>& t, const double* u, St<NS>& s) {
+  thermo_fwd<NS>(P, t);
+  double ke = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    s.u[d] = u[d];
+    s.m[d] = t.rho * u[d];
+    ke += u[d] * u[d];
+  }
+  s.rho = t.rho;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) s.rhoY[k] = t.rho * t.Y[k];
+  s.p = t.p;
+  s.E = t.rho * (t.e + 0.5 * ke);
+  s.a = t.a;
+}
+
+template <int NS>
+__device__ __forceinline__ void face_state_rev(const KParams& P, const Thermo<NS>& t, const St<NS>& s,
+                                               const StAdj<NS>& g, double* lY, double* lu, double& lp, double& lT) {
+  double ke = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) ke += s.u[d] * s.u[d];
+  double lrho = g.rho + g.E * (t.e + 0.5 * ke);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    lrho += g.rhoY[k] * t.Y[k];
+    lY[k] += g.rhoY[k] * t.rho;
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lrho += g.m[d] * s.u[d];
+    lu[d] += g.u[d] + g.m[d] * t.rho + g.E * t.rho * s.u[d];
+  }
+  lp += g.p;
+  thermo_rev<NS>(P, t, lrho, g.E * t.rho, g.a, 0.0, 0.0, lY, lp, lT);
+}
+
+}  // namespace adj
+}  // namespace mpmc

@@ -14,9 +14,12 @@
 
 using namespace mpmc;
 
+static constexpr int NFAM_MAX = 6;
+
 struct mpmc_ctx {
   KParams P;
   Ops ops;
+  AdjOps aops;
   int precision;
   cudaStream_t stream;
   cudaStream_t cap;  // internal stream used only to capture graphs
@@ -34,6 +37,15 @@ struct mpmc_ctx {
   int* status = nullptr;
   unsigned long long* stats = nullptr;
   int* counter = nullptr;
+  // adjoint scratch (allocated on first use): per-face slot buffer of one
+  // direction, cache adjoint, U adjoint, two stage adjoints, an internal
+  // tape of one step
+  double* Cslots = nullptr;
+  double* gW = nullptr;
+  double* gU = nullptr;
+  double* lamA = nullptr;
+  double* lamB = nullptr;
+  uint32_t* tape_int = nullptr;
   // graph of one SSP-RK3 step for step_n
   cudaGraphExec_t gexec = nullptr;
   const double* g_U = nullptr;
@@ -48,12 +60,12 @@ struct mpmc_ctx {
   };
   std::vector<Mark> marks;
   std::vector<cudaEvent_t> pool;
-  double prof_ms[4] = {0, 0, 0, 0};
-  unsigned long long prof_n[4] = {0, 0, 0, 0};
+  double prof_ms[NFAM_MAX] = {};
+  unsigned long long prof_n[NFAM_MAX] = {};
   char err[256];
 };
 
-enum { FAM_PRIM = 0, FAM_FACE = 1, FAM_UPDATE = 2, FAM_DT = 3 };
+enum { FAM_PRIM = 0, FAM_FACE = 1, FAM_UPDATE = 2, FAM_DT = 3, FAM_ADJ_FACE = 4, FAM_ADJ_PRIM = 5, NFAM = 6 };
 
 static cudaEvent_t take_event(mpmc_ctx* c) {
   if (!c->pool.empty()) {
@@ -123,8 +135,9 @@ static int check_launch(mpmc_ctx* c, const char* where) {
 
 static void free_all(mpmc_ctx* c) {
   // g_U and g_hist are caller-owned and never freed here
-  void* ptrs[] = {c->Wc, c->F[0], c->F[1], c->F[2], c->U1, c->U2, c->Ud, c->Uin, c->scal, c->red, c->status, c->stats,
-                  c->counter};
+  void* ptrs[] = {c->Wc,   c->F[0],  c->F[1],    c->F[2],   c->U1,   c->U2,   c->Ud,   c->Uin,
+                  c->scal, c->red,   c->status,  c->stats,  c->counter, c->gW, c->lamA, c->lamB,
+                  c->tape_int, c->Cslots, c->gU};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -249,7 +262,12 @@ extern "C" int mpmc_create(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_m
     case 2: c->ops = mixed ? ops_mixed_d2(ns) : ops_fp64_d2(ns); break;
     default: c->ops = mixed ? ops_mixed_d3(ns) : ops_fp64_d3(ns); break;
   }
-  if (!c->ops.face) {
+  switch (D) {
+    case 1: c->aops = adj_ops_d1(ns); break;
+    case 2: c->aops = adj_ops_d2(ns); break;
+    default: c->aops = adj_ops_d3(ns); break;
+  }
+  if (!c->ops.face || !c->aops.face) {
     delete c;
     return MPMC_INVALID_ARG;
   }
@@ -457,10 +475,172 @@ extern "C" int mpmc_dt_gamma(mpmc_ctx* c, const double* U, double* out_dev) {
   return check_launch(c, "dt_gamma");
 }
 
+// ---------------------------------------------------------------------------
+// discrete adjoint (FP64 contexts)
+static int ensure_adjoint(mpmc_ctx* c) {
+  if (c->precision != MPMC_FP64) return fail(c, MPMC_INVALID_ARG, "adjoint: needs an FP64 context");
+  const KParams& P = c->P;
+  int rc = MPMC_OK;
+  const size_t st_bytes = (size_t)P.nv * P.ncell * sizeof(double);
+  long long nfmax = 0;
+  for (int d = 0; d < P.dim; ++d) nfmax = c->nface[d] > nfmax ? c->nface[d] : nfmax;
+  if (!c->Cslots) rc = alloc(c, (void**)&c->Cslots, (size_t)c->aops.slots(P) * nfmax * sizeof(double));
+  if (!rc && !c->gW) rc = alloc(c, (void**)&c->gW, (size_t)P.nW * P.wstride * sizeof(double));
+  if (!rc && !c->gU) rc = alloc(c, (void**)&c->gU, st_bytes);
+  if (!rc && !c->lamA) rc = alloc(c, (void**)&c->lamA, st_bytes);
+  if (!rc && !c->lamB) rc = alloc(c, (void**)&c->lamB, st_bytes);
+  if (!rc && !c->tape_int) rc = alloc(c, (void**)&c->tape_int, 3 * (size_t)c->nface_total * sizeof(uint32_t));
+  return rc;
+}
+
+// face fluxes of one stage for their flags only (no divergence / update)
+static void faces_only(mpmc_ctx* c, cudaStream_t s, const double* Un, const double* Uk, double rk0, double rk1,
+                       double rk2, uint32_t* flags) {
+  long long off = 0;
+  for (int d = 0; d < c->P.dim; ++d) {
+    ProfScope ps(c, FAM_FACE, s);
+    c->ops.face(c->P, s, d, c->Wc, Un, Uk, c->Uin, c->scal, rk0, rk1, rk2, c->F[d], flags + off, nullptr);
+    off += c->nface[d];
+  }
+}
+
+// out = a x + b y + cz z + coef (dt) (dL/dU)^T lamL at U (whose primitive
+// cache is in Wc): per direction the faces' slots, their gather, then the
+// per-cell primitive-recovery reverse fused with the combination
+static void stage_vjp(mpmc_ctx* c, cudaStream_t s, const double* U, const uint32_t* tape, const double* lamL,
+                      double coef, int mul_dt, double* out, double a, const double* x, double b, const double* y,
+                      double cz, const double* z) {
+  const KParams& P = c->P;
+  long long off = 0;
+  for (int d = 0; d < P.dim; ++d) {
+    {
+      ProfScope ps(c, FAM_ADJ_FACE, s);
+      c->aops.face(P, s, d, c->Wc, U, c->Uin, c->scal, tape + off, lamL, coef, mul_dt, c->Cslots);
+    }
+    ProfScope ps(c, FAM_ADJ_PRIM, s);
+    c->aops.gather(P, s, d, c->Cslots, d == 0, c->gW, c->gU);
+    off += c->nface[d];
+  }
+  ProfScope ps(c, FAM_ADJ_PRIM, s);
+  c->aops.cell(P, s, U, c->gW, c->gU, out, a, x, b, y, cz, z);
+}
+
 extern "C" int mpmc_rhs_adjoint(mpmc_ctx* c, const double* U, const mpmc_stage* st, const uint32_t* tape,
                                 const double* lam_dUdt, double* lam_U) {
-  (void)U; (void)st; (void)tape; (void)lam_dUdt; (void)lam_U;
-  return fail(c, MPMC_INVALID_ARG, "rhs_adjoint: not available in this build");
+  if (!c || !U || !lam_dUdt || !lam_U) return fail(c, MPMC_INVALID_ARG, "rhs_adjoint: null argument");
+  int rc = ensure_adjoint(c);
+  if (rc) return rc;
+  const double* Un = st && st->U_n ? st->U_n : U;
+  const double rk0 = st ? st->rk0 : 1.0, rk1 = st ? st->rk1 : 0.0, rk2 = st ? st->rk2 : 1.0;
+  const double dt = st ? st->dt : 0.0, G = st ? st->Gamma : -1.0;
+  cudaStream_t s = c->stream;
+  // the same dt / Gamma and primitive cache as mpmc_rhs
+  dt_gamma(c, s, Un, dt, G, nullptr);
+  if (Un != U) prim(c, s, U, nullptr);
+  if (!tape) {
+    faces_only(c, s, Un, U, rk0, rk1, rk2, c->tape_int);
+    tape = c->tape_int;
+  }
+  stage_vjp(c, s, U, tape, lam_dUdt, 1.0, 0, lam_U, 1.0, lam_U, 0.0, nullptr, 0.0, nullptr);
+  return check_launch(c, "rhs_adjoint");
+}
+
+extern "C" int mpmc_rk_step_record(mpmc_ctx* c, double* U, double dt, uint32_t* tape, double* U_stages) {
+  if (!c || !U || !U_stages) return fail(c, MPMC_INVALID_ARG, "rk_step_record: null argument");
+  const KParams& P = c->P;
+  const long long n = (long long)P.nv * P.ncell, nf = c->nface_total;
+  double* U1 = U_stages;
+  double* U2 = U_stages + n;
+  cudaStream_t s = c->stream;
+  dt_gamma(c, s, U, dt, -1.0, nullptr);
+  stage(c, s, U, U, 1.0, 0.0, 1.0, U1, nullptr, tape);
+  prim(c, s, U1, nullptr);
+  stage(c, s, U, U1, 0.75, 0.25, 0.25, U2, nullptr, tape ? tape + nf : nullptr);
+  prim(c, s, U2, nullptr);
+  stage(c, s, U, U2, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, U, nullptr, tape ? tape + 2 * nf : nullptr);
+  c->faces_done += 3ull * c->nface_total;
+  return check_launch(c, "rk_step_record");
+}
+
+extern "C" int mpmc_rk_step_adjoint(mpmc_ctx* c, const double* U_n, const double* U_stages, double dt,
+                                    const uint32_t* tape, const double* lam_next, double* lam_n) {
+  if (!c || !U_n || !lam_next || !lam_n) return fail(c, MPMC_INVALID_ARG, "rk_step_adjoint: null argument");
+  int rc = ensure_adjoint(c);
+  if (rc) return rc;
+  const KParams& P = c->P;
+  const long long nf = c->nface_total, n = (long long)P.nv * P.ncell;
+  cudaStream_t s = c->stream;
+  dt_gamma(c, s, U_n, dt, -1.0, nullptr);
+  const double* U1 = U_stages ? U_stages : c->U1;
+  const double* U2 = U_stages ? U_stages + n : c->U2;
+  uint32_t* tp = tape ? nullptr : c->tape_int;
+  if (!U_stages) {
+    // forward recomputation of the stage states (and of the flags if no tape)
+    stage(c, s, U_n, U_n, 1.0, 0.0, 1.0, c->U1, nullptr, tp);
+    prim(c, s, c->U1, nullptr);
+    stage(c, s, U_n, c->U1, 0.75, 0.25, 0.25, c->U2, nullptr, tp ? tp + nf : nullptr);
+    prim(c, s, c->U2, nullptr);
+    if (tp) faces_only(c, s, U_n, c->U2, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, tp + 2 * nf);
+  } else if (tp) {
+    // stage states given, flags recomputed
+    faces_only(c, s, U_n, U_n, 1.0, 0.0, 1.0, tp);
+    prim(c, s, U1, nullptr);
+    faces_only(c, s, U_n, U1, 0.75, 0.25, 0.25, tp + nf);
+    prim(c, s, U2, nullptr);
+    faces_only(c, s, U_n, U2, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, tp + 2 * nf);
+  } else {
+    prim(c, s, U2, nullptr);
+  }
+  const uint32_t* T = tape ? tape : c->tape_int;
+  // Eq. SSPRK3 reversed:
+  //   lam2 = 2/3 lam3 + 2/3 dt L(U2)^T lam3
+  //   lam1 = 1/4 lam2 + 1/4 dt L(U1)^T lam2
+  //   lamn = 1/3 lam3 + 3/4 lam2 + lam1 + dt L(Un)^T lam1
+  double* l2 = c->lamB;
+  double* l1 = c->lamA;
+  stage_vjp(c, s, U2, T + 2 * nf, lam_next, 2.0 / 3.0, 1, l2, 2.0 / 3.0, lam_next, 0.0, nullptr, 0.0, nullptr);
+  prim(c, s, U1, nullptr);
+  stage_vjp(c, s, U1, T + nf, l2, 0.25, 1, l1, 0.25, l2, 0.0, nullptr, 0.0, nullptr);
+  prim(c, s, U_n, nullptr);
+  stage_vjp(c, s, U_n, T, l1, 1.0, 1, lam_n, 1.0 / 3.0, lam_next, 0.75, l2, 1.0, l1);
+  return check_launch(c, "rk_step_adjoint");
+}
+
+extern "C" int mpmc_init_state_adjoint(mpmc_ctx* c, const double* prim_in, const double* lam_U, double* lam_prim) {
+  if (!c || !prim_in || !lam_U || !lam_prim) return fail(c, MPMC_INVALID_ARG, "init_state_adjoint: null argument");
+  c->aops.init(c->P, c->stream, prim_in, lam_U, lam_prim, c->P.ncell);
+  return check_launch(c, "init_state_adjoint");
+}
+
+static int nprim_fields(const KParams& P) { return 4 + P.ns + P.dim; }
+
+extern "C" int mpmc_primitives(mpmc_ctx* c, const double* U, double* out) {
+  if (!c || !U || !out) return fail(c, MPMC_INVALID_ARG, "primitives: null argument");
+  if (c->precision != MPMC_FP64) return fail(c, MPMC_INVALID_ARG, "primitives: needs an FP64 context");
+  const KParams& P = c->P;
+  prim(c, c->stream, U, nullptr);
+  if (cudaMemcpy2DAsync(out, (size_t)P.ncell * sizeof(double), c->Wc, (size_t)P.wstride * sizeof(double),
+                        (size_t)P.ncell * sizeof(double), (size_t)nprim_fields(P), cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess)
+    return fail(c, MPMC_CUDA_ERROR, "primitives: copy");
+  return check_launch(c, "primitives");
+}
+
+extern "C" int mpmc_primitives_adjoint(mpmc_ctx* c, const double* U, const double* lam_W, double* lam_U) {
+  if (!c || !U || !lam_W || !lam_U) return fail(c, MPMC_INVALID_ARG, "primitives_adjoint: null argument");
+  int rc = ensure_adjoint(c);
+  if (rc) return rc;
+  const KParams& P = c->P;
+  cudaStream_t s = c->stream;
+  cudaMemsetAsync(c->gW, 0, (size_t)P.nW * P.wstride * sizeof(double), s);
+  cudaMemsetAsync(c->gU, 0, (size_t)P.nv * P.ncell * sizeof(double), s);
+  if (cudaMemcpy2DAsync(c->gW, (size_t)P.wstride * sizeof(double), lam_W, (size_t)P.ncell * sizeof(double),
+                        (size_t)P.ncell * sizeof(double), (size_t)nprim_fields(P), cudaMemcpyDeviceToDevice,
+                        s) != cudaSuccess)
+    return fail(c, MPMC_CUDA_ERROR, "primitives_adjoint: copy");
+  ProfScope ps(c, FAM_ADJ_PRIM, s);
+  c->aops.cell(P, s, U, c->gW, c->gU, lam_U, 1.0, lam_U, 0.0, nullptr, 0.0, nullptr);
+  return check_launch(c, "primitives_adjoint");
 }
 
 extern "C" int mpmc_get_status(mpmc_ctx* c, int reset) {
@@ -509,7 +689,7 @@ extern "C" int mpmc_get_profile(mpmc_ctx* c, double* ms, uint64_t* launches, int
     c->pool.push_back(m.b);
   }
   c->marks.clear();
-  for (int f = 0; f < 4; ++f) {
+  for (int f = 0; f < NFAM; ++f) {
     if (ms) ms[f] = c->prof_ms[f];
     if (launches) launches[f] = c->prof_n[f];
     if (reset) {

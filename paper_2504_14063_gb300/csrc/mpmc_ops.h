@@ -19,6 +19,19 @@ struct Ops {
                  const double* scal, double rk0, double rk1, double rk2, double* Uout, double* dUdt, int* status);
 };
 
+// discrete adjoint (FP64): per-face contributions of one direction into a
+// slot buffer, their per-cell gather, the per-cell primitive-recovery VJP
+// fused with the reverse RK combination, and the VJP of the initialisation
+struct AdjOps {
+  int (*slots)(const KParams&);
+  void (*face)(const KParams&, cudaStream_t, int d, const double* Wc, const double* Uk, const double* Uin,
+               const double* scal, const uint32_t* tape, const double* lamL, double coef, int mul_dt, double* C);
+  void (*gather)(const KParams&, cudaStream_t, int d, const double* C, int first, double* gW, double* gU);
+  void (*cell)(const KParams&, cudaStream_t, const double* U, const double* gW, const double* gU, double* out,
+               double a, const double* x, double b, const double* y, double cz, const double* z);
+  void (*init)(const KParams&, cudaStream_t, const double* prim, const double* lamU, double* lprim, long long n);
+};
+
 // per-dimension tables, defined in mpmc_kernels_d{1,2,3}.cu (FP64) and
 // mpmc_mixed_d{1,2,3}.cu (mixed precision; init is the FP64 one)
 Ops ops_fp64_d1(int ns);
@@ -27,5 +40,9 @@ Ops ops_fp64_d3(int ns);
 Ops ops_mixed_d1(int ns);
 Ops ops_mixed_d2(int ns);
 Ops ops_mixed_d3(int ns);
+// defined in mpmc_adjoint_d{1,2,3}.cu
+AdjOps adj_ops_d1(int ns);
+AdjOps adj_ops_d2(int ns);
+AdjOps adj_ops_d3(int ns);
 
 }  // namespace mpmc

@@ -270,15 +270,32 @@ def shock_interface_2d(n=512, seed=3, amps=None, nsteps=200):
     return p
 
 
+def interface_fractions(n, amps, phi_l, xp=np):
+    """Air and helium volume fractions of the n x n shock-interface case for
+    interface amplitudes `amps` (8 x 2, cells), with the liquid fraction
+    phi_l [n, n] given.  xp: numpy, or torch for a differentiable map from
+    the amplitudes (float64 tensors)."""
+    s = n / 512.0
+    R, cx, cy = 64.0 * s, 160.0 * s, n / 2.0
+    if xp is np:
+        i = np.arange(n) + 0.5
+        X, Y = np.meshgrid(i, i)
+    else:
+        i = xp.arange(n, dtype=amps.dtype, device=amps.device) + 0.5
+        Y, X = xp.meshgrid(i, i, indexing="ij")
+    th = xp.arctan2(Y - cy, X - cx) if xp is np else xp.atan2(Y - cy, X - cx)
+    r = R + 0.0 * th
+    for m in range(amps.shape[0]):
+        r = r + amps[m, 0] * xp.cos((m + 1) * th) + amps[m, 1] * xp.sin((m + 1) * th)
+    d = r - xp.hypot(X - cx, Y - cy)
+    phi_b = 0.5 * (1.0 + xp.tanh(d / 2.0))   # tanh_profile with dx = 1 cell
+    return (1.0 - phi_l) * (1.0 - phi_b), (1.0 - phi_l) * phi_b
+
+
 def _with_amplitudes(p, n, s, amps):
-    R, (cx, cy) = 64.0 * s, (160.0 * s, n / 2.0)
-    i = np.arange(n) + 0.5
-    X, Y = np.meshgrid(i, i)
-    th = np.arctan2(Y - cy, X - cx)
-    phi_b = tanh_profile(fourier_radius(th, R, amps) - np.hypot(X - cx, Y - cy), 1.0)
-    phi_l = p.prim[2, 0]
-    p.prim[0, 0] = (1.0 - phi_l) * (1.0 - phi_b)
-    p.prim[1, 0] = (1.0 - phi_l) * phi_b
+    a0, a1 = interface_fractions(n, amps, p.prim[2, 0])
+    p.prim[0, 0] = a0
+    p.prim[1, 0] = a1
     return p
 
 
