@@ -213,8 +213,8 @@ def adjoint_section(mp, torch, nsteps=200, every=20, n=512):
             "memory_mb": {"state": state_mb, "checkpoints": state_mb * len(range(0, nsteps, every)),
                           "segment_states": state_mb * (every + 1)},
             "J": float(J), "grad_norm": float(grad.norm()), "status": ctx.status(),
-            "note": "backward = per segment one forward replay step per step + per step the reverse of "
-                    "SSP-RK3 (stage states recomputed inside the reverse call)"}
+            "note": "backward = per segment one forward replay step per step (stage states and flags "
+                    "recorded) + per step the reverse of SSP-RK3"}
 
 
 def main():
