@@ -192,6 +192,34 @@ def adjoint_section(mp, torch, nsteps=200, every=20, n=512):
     _, J, _ = forward(a, 3)
     torch.autograd.grad(J, a)
     torch.cuda.synchronize()
+
+    # one reverse step with a dense random adjoint (every face active), from
+    # a developed state, stage states and flags recorded: the per-step cost
+    # once the adjoint covers the whole domain
+    Ud = ctx.init_state(torch.from_numpy(p.prim))
+    ctx.step_n(Ud, 20)
+    dt = float(ctx.dt_gamma(Ud)[0])
+    tape = torch.empty(3 * ctx.nfaces_total, dtype=torch.int32, device="cuda")
+    stages = ctx.rk_step_record(Ud.clone(), dt, tape)
+    lam = torch.randn(Ud.shape, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    lam_n = torch.empty_like(lam)
+    Uf = Ud.clone()
+    reps = 5
+    ef = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    ea = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for r in range(reps):
+        Uf.copy_(Ud)
+        ef[r][0].record()
+        ctx.rk_step(Uf, dt)
+        ef[r][1].record()
+    for r in range(reps):
+        ea[r][0].record()
+        ctx.rk_step_adjoint(Ud, lam, dt=dt, tape=tape, lam_n=lam_n, stages=stages)
+        ea[r][1].record()
+    torch.cuda.synchronize()
+    dense_f = float(np.median([x.elapsed_time(y) for x, y in ef]))
+    dense_a = float(np.median([x.elapsed_time(y) for x, y in ea]))
+    del Ud, Uf, stages, tape, lam, lam_n
     a = amps0.clone().requires_grad_(True)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     ctx.profile(reset=True)
@@ -209,6 +237,9 @@ def adjoint_section(mp, torch, nsteps=200, every=20, n=512):
     return {"workload": f"shock_interface_2d {n}x{n}, {nsteps} SSP-RK3 steps, checkpoint every {every} steps",
             "functional": f"sum_k dt_k mean_y P(x={col}, y, t_k); gradient w.r.t. 16 interface Fourier amplitudes",
             "forward_ms": fwd_ms, "backward_ms": bwd_ms, "ratio": bwd_ms / fwd_ms,
+            "dense_step": {"forward_ms": dense_f, "adjoint_ms": dense_a, "ratio": dense_a / dense_f,
+                           "note": "one SSP-RK3 step vs its reverse (stage states and flags recorded) "
+                                   "with a dense random adjoint, median of 5"},
             "backward_kernel_ms": {k: v[0] for k, v in prof.items() if v[1]},
             "memory_mb": {"state": state_mb, "checkpoints": state_mb * len(range(0, nsteps, every)),
                           "segment_states": state_mb * (every + 1)},
@@ -228,6 +259,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--compare-steps", type=int, default=100)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -342,7 +374,7 @@ def main():
 
     adjoint = None
     if not args.no_adjoint and rank == 0:
-        adjoint = adjoint_section(mp, torch)
+        adjoint = adjoint_section(mp, torch, nsteps=args.adjoint_steps)
 
     # ---- end to end through the host-buffer entry --------------------------
     H = U.cpu().pin_memory()

@@ -59,6 +59,60 @@ __device__ __forceinline__ double weno_fwd(Weno& w, double v0, double v1, double
   return w.out;
 }
 
+// WENO5-Z value and its gradient g[j] = d(out)/d(v_j) in one pass (the
+// same arithmetic as weno_fwd followed by weno_rev with a unit seed)
+__device__ __forceinline__ double weno_val_grad(double v0, double v1, double v2, double v3, double v4, double eps,
+                                                double* g) {
+  const double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
+  const double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) * (1.0 / 6.0);
+  const double q2 = (2.0 * v2 + 5.0 * v3 - v4) * (1.0 / 6.0);
+  const double t0 = v0 - 2.0 * v1 + v2, s0 = v0 - 4.0 * v1 + 3.0 * v2;
+  const double t1 = v1 - 2.0 * v2 + v3, s1 = v1 - v3;
+  const double t2 = v2 - 2.0 * v3 + v4, s2 = 3.0 * v2 - 4.0 * v3 + v4;
+  const double b0 = (13.0 / 12.0) * t0 * t0 + 0.25 * s0 * s0;
+  const double b1 = (13.0 / 12.0) * t1 * t1 + 0.25 * s1 * s1;
+  const double b2 = (13.0 / 12.0) * t2 * t2 + 0.25 * s2 * s2;
+  const double tau = fabs(b0 - b2);
+  const double c0 = b0 + eps, c1 = b1 + eps, c2 = b2 + eps;
+  const double A0 = 0.1 * (c0 + tau) * c1 * c2;
+  const double A1 = 0.6 * (c1 + tau) * c0 * c2;
+  const double A2 = 0.3 * (c2 + tau) * c0 * c1;
+  const double iS = 1.0 / (A0 + A1 + A2);
+  const double out = (A0 * q0 + A1 * q1 + A2 * q2) * iS;
+  double M = fmax(fmax(fabs(v0), fabs(v1)), fmax(fmax(fabs(v2), fabs(v3)), fabs(v4)));
+  const double tol = (WENO_FLAT * M) * (WENO_FLAT * M);
+  if (b0 <= tol && b1 <= tol && b2 <= tol) {
+    // ideal weights 1/10, 6/10, 3/10 on the three candidates
+    g[0] = 1.0 / 30.0;
+    g[1] = -13.0 / 60.0;
+    g[2] = 47.0 / 60.0;
+    g[3] = 9.0 / 20.0;
+    g[4] = -1.0 / 20.0;
+    return out;
+  }
+  // out = sum A_k q_k / S: dA_k -> (q_k - out)/S, dq_k -> A_k/S
+  const double lA0 = (q0 - out) * iS, lA1 = (q1 - out) * iS, lA2 = (q2 - out) * iS;
+  const double lq0 = A0 * iS, lq1 = A1 * iS, lq2 = A2 * iS;
+  double lc0 = 0.0, lc1 = 0.0, lc2 = 0.0, ltau = 0.0;
+  double a = lA0 * 0.1;
+  lc0 += a * c1 * c2; ltau += a * c1 * c2; lc1 += a * (c0 + tau) * c2; lc2 += a * (c0 + tau) * c1;
+  a = lA1 * 0.6;
+  lc1 += a * c0 * c2; ltau += a * c0 * c2; lc0 += a * (c1 + tau) * c2; lc2 += a * (c1 + tau) * c0;
+  a = lA2 * 0.3;
+  lc2 += a * c0 * c1; ltau += a * c0 * c1; lc0 += a * (c2 + tau) * c1; lc1 += a * (c2 + tau) * c0;
+  const double sg = (b0 - b2) >= 0.0 ? 1.0 : -1.0;
+  const double lb0 = lc0 + sg * ltau, lb1 = lc1, lb2 = lc2 - sg * ltau;
+  const double lt0 = lb0 * (13.0 / 6.0) * t0, ls0 = lb0 * 0.5 * s0;
+  const double lt1 = lb1 * (13.0 / 6.0) * t1, ls1 = lb1 * 0.5 * s1;
+  const double lt2 = lb2 * (13.0 / 6.0) * t2, ls2 = lb2 * 0.5 * s2;
+  g[0] = lt0 + ls0 + lq0 * (2.0 / 6.0);
+  g[1] = -2.0 * lt0 - 4.0 * ls0 + lt1 + ls1 - lq0 * (7.0 / 6.0) - lq1 * (1.0 / 6.0);
+  g[2] = lt0 + 3.0 * ls0 - 2.0 * lt1 + lt2 + 3.0 * ls2 + lq0 * (11.0 / 6.0) + lq1 * (5.0 / 6.0) + lq2 * (2.0 / 6.0);
+  g[3] = lt1 - ls1 - 2.0 * lt2 - 4.0 * ls2 + lq1 * (2.0 / 6.0) + lq2 * (5.0 / 6.0);
+  g[4] = lt2 + ls2 - lq2 * (1.0 / 6.0);
+  return out;
+}
+
 // adds d(out)/d(v) * lam to gv[0..4]
 __device__ __forceinline__ void weno_rev(const Weno& w, double lam, double* gv) {
   if (w.flat) {
@@ -141,9 +195,9 @@ __device__ __forceinline__ void thermo_rev(const KParams& P, const Thermo<NS>& t
   // a = sqrt(cp / den)
   double lcp = 0.0, lden = 0.0;
   if (la != 0.0) {
-    const double g = la * 0.5 / t.a;
-    lcp += g / t.den;
-    lden -= g * t.cp / (t.den * t.den);
+    const double g = la * 0.5 / t.a, iden = 1.0 / t.den;
+    lcp += g * iden;
+    lden -= g * t.cp * iden * iden;
   }
   // den = rho be cp - al^2 T
   lrho += lden * t.be * t.cp;
@@ -177,35 +231,34 @@ __device__ __forceinline__ void thermo_rev(const KParams& P, const Thermo<NS>& t
 // theorem of   G1 = T A(P,Y) - (v - b) = 0,   G2 = T B(P,Y) - (e - q) = 0,
 // A = sum Y_k R_k / (P + Pinf_k)  (NASG_T2),  B = sum Y_k cv_k (P + g Pinf)/(P + Pinf)  (NASG_T1).
 template <int NS>
-__device__ __forceinline__ void pt_rev(const KParams& P, const double* Y, double p, double T, double lp, double lT,
-                                       double* lY, double& le, double& lv) {
+__device__ __forceinline__ void pt_rev(const KParams& P, const double* Y, double p, double T, const double* r,
+                                       double lp, double lT, double* lY, double& le, double& lv) {
+  // r[k] = 1 / (P + Pinf_k)
   double A = 0.0, B = 0.0, AP = 0.0, BP = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     if (Y[k] == 0.0) continue;
-    const double r = 1.0 / (p + P.pinf[k]);
-    A += Y[k] * P.Rk[k] * r;
-    AP -= Y[k] * P.Rk[k] * r * r;
-    const double g = (p + P.gam[k] * P.pinf[k]) * r;
+    A += Y[k] * P.Rk[k] * r[k];
+    AP -= Y[k] * P.Rk[k] * r[k] * r[k];
+    const double g = (p + P.gam[k] * P.pinf[k]) * r[k];
     B += Y[k] * P.cv[k] * g;
     // d/dP of (P + g Pinf)/(P + Pinf) = (Pinf - g Pinf) r^2
-    BP += Y[k] * P.cv[k] * (P.pinf[k] - P.gam[k] * P.pinf[k]) * r * r;
+    BP += Y[k] * P.cv[k] * (P.pinf[k] - P.gam[k] * P.pinf[k]) * r[k] * r[k];
   }
   // J = [[T AP, A], [T BP, B]] (rows G1, G2; columns P, T); solve J^T mu = (lp, lT)
   const double j11 = T * AP, j12 = A, j21 = T * BP, j22 = B;
-  const double det = j11 * j22 - j12 * j21;
+  const double idet = 1.0 / (j11 * j22 - j12 * j21);
   // J^T = [[j11, j21], [j12, j22]]
-  const double mu1 = (lp * j22 - lT * j21) / det;
-  const double mu2 = (j11 * lT - j12 * lp) / det;
+  const double mu1 = (lp * j22 - lT * j21) * idet;
+  const double mu2 = (j11 * lT - j12 * lp) * idet;
   // lambda_x = -mu^T dG/dx
   lv += mu1;   // dG1/dv = -1
   le += mu2;   // dG2/de = -1
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     if (Y[k] == 0.0) continue;
-    const double r = 1.0 / (p + P.pinf[k]);
-    const double dG1 = T * P.Rk[k] * r + P.b[k];
-    const double dG2 = T * P.cv[k] * (p + P.gam[k] * P.pinf[k]) * r + P.q[k];
+    const double dG1 = T * P.Rk[k] * r[k] + P.b[k];
+    const double dG2 = T * P.cv[k] * (p + P.gam[k] * P.pinf[k]) * r[k] + P.q[k];
     lY[k] -= mu1 * dG1 + mu2 * dG2;
   }
 }
@@ -215,21 +268,21 @@ template <int NS, int D>
 __device__ __forceinline__ void decode_rev(const double* U, double rho, const double* Y, const double* u, double lrho,
                                            const double* lY, const double* lu, double le, double lv, double* lU) {
   // e = E/rho - |u|^2/2, v = 1/rho, u = m/rho, Y = U/rho, rho = sum U_k
+  const double ir = 1.0 / rho;
   double lu2[3];
 #pragma unroll
   for (int t = 0; t < 3; ++t) lu2[t] = (t < D ? lu[t] : 0.0) - le * u[t];
-  lU[NS + D] += le / rho;
-  lrho -= le * U[NS + D] / (rho * rho);
-  lrho -= lv / (rho * rho);
+  lU[NS + D] += le * ir;
+  lrho -= (le * U[NS + D] + lv) * ir * ir;
 #pragma unroll
   for (int t = 0; t < D; ++t) {
-    lU[NS + t] += lu2[t] / rho;
-    lrho -= lu2[t] * u[t] / rho;
+    lU[NS + t] += lu2[t] * ir;
+    lrho -= lu2[t] * u[t] * ir;
   }
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    lU[k] += lY[k] / rho;
-    lrho -= lY[k] * Y[k] / rho;
+    lU[k] += lY[k] * ir;
+    lrho -= lY[k] * Y[k] * ir;
   }
 #pragma unroll
   for (int k = 0; k < NS; ++k) lU[k] += lrho;
@@ -314,7 +367,8 @@ __device__ __forceinline__ void hllc_rev(int d, const St<NS>& L, const St<NS>& R
   // energy: F = u (E + P) + s (f (E + (ss - u)(rho ss + P/dK)) - E)
   {
     const double a = wl * lF[NS + D], b = wr * lF[NS + D];
-    const double kL = L.rho * ss + L.p / dL, kR = R.rho * ss + R.p / dR;
+    const double idL = 1.0 / dL, idR = 1.0 / dR;
+    const double kL = L.rho * ss + L.p * idL, kR = R.rho * ss + R.p * idR;
     const double inL = L.E + (ss - L.u[d]) * kL, inR = R.E + (ss - R.u[d]) * kR;
     gL.u[d] += a * (L.E + L.p);
     gL.E += a * (L.u[d] + sm * (fL - 1.0));
@@ -328,8 +382,8 @@ __device__ __forceinline__ void hllc_rev(int d, const St<NS>& L, const St<NS>& R
       const double gk = g * (ss - L.u[d]);
       gL.rho += gk * ss;
       lss += gk * L.rho;
-      gL.p += gk / dL;
-      ldL -= gk * L.p / (dL * dL);
+      gL.p += gk * idL;
+      ldL -= gk * L.p * idL * idL;
     }
     gR.u[d] += b * (R.E + R.p);
     gR.E += b * (R.u[d] + sp * (fR - 1.0));
@@ -343,20 +397,21 @@ __device__ __forceinline__ void hllc_rev(int d, const St<NS>& L, const St<NS>& R
       const double gk = g * (ss - R.u[d]);
       gR.rho += gk * ss;
       lss += gk * R.rho;
-      gR.p += gk / dR;
-      ldR -= gk * R.p / (dR * dR);
+      gR.p += gk * idR;
+      ldR -= gk * R.p * idR * idR;
     }
   }
   // fK = dK / (sK - ss)
   double lsL = 0.0, lsR = 0.0;
-  ldL += lfL / eL;
-  lsL -= lfL * dL / (eL * eL);
-  lss += lfL * dL / (eL * eL);
-  ldR += lfR / eR;
-  lsR -= lfR * dR / (eR * eR);
-  lss += lfR * dR / (eR * eR);
+  const double ieL = 1.0 / eL, ieR = 1.0 / eR, iden = 1.0 / den;
+  ldL += lfL * ieL;
+  lsL -= lfL * fL * ieL;
+  lss += lfL * fL * ieL;
+  ldR += lfR * ieR;
+  lsR -= lfR * fR * ieR;
+  lss += lfR * fR * ieR;
   // ss = num / den
-  const double lnum = lss / den, lden = -lss * ss / den;
+  const double lnum = lss * iden, lden = -lss * ss * iden;
   gR.p += lnum;
   gL.p -= lnum;
   gL.rho += lnum * L.u[d] * dL + lden * dL;

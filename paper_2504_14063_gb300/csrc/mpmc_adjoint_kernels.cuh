@@ -112,13 +112,64 @@ __device__ __forceinline__ void ylim_rev(const YLim<NS>& s, const double* lout, 
   for (int k = 0; k < NS; ++k) lY[k] += s.Yin[k] < 0.0 ? 0.0 : l1[k];
 }
 
+// Face-average scalars of the characteristic matrices (Appendix A):
+// X = (rho a^2 beta - 1) / (alpha a^2 rho) and c = rho a at the arithmetic
+// average of the two cells' conserved states, with what the reverse needs.
+template <int NS, int D>
+struct FaceAvg {
+  double Ub[NS + D + 1], rb, Yb[NS], ub[3], eb, vb, pb, Tb, XN, XD, X, c;
+  Thermo<NS> tb;
+};
+
+template <int NS, int D>
+__device__ __forceinline__ void face_avg_fwd(const KParams& P, const double* Uk, const double* Uin, CRef ri, CRef rj,
+                                             FaceAvg<NS, D>& f) {
+  constexpr int NV = NS + D + 1;
+  double Ui[NV], Uj[NV];
+  load_U<NS, D>(P, Uk, Uin, ri, Ui);
+  load_U<NS, D>(P, Uk, Uin, rj, Uj);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) f.Ub[v] = 0.5 * (Ui[v] + Uj[v]);
+  decode<NS, D>(f.Ub, f.rb, f.Yb, f.ub, f.eb, f.vb);
+  pt_equilibrium<NS>(P, f.Yb, f.eb, f.vb, f.pb, f.Tb);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) f.tb.Y[k] = f.Yb[k];
+  f.tb.p = f.pb;
+  f.tb.T = f.Tb;
+  thermo_fwd<NS>(P, f.tb);
+  const double a2 = f.tb.a * f.tb.a;
+  f.XN = f.rb * a2 * f.tb.be - 1.0;
+  f.XD = f.tb.al * a2 * f.rb;
+  f.X = f.XN / f.XD;
+  f.c = f.tb.a * f.rb;
+}
+
+// adjoints of X and c -> adjoint of the averaged conserved state Ub
+template <int NS, int D>
+__device__ __forceinline__ void face_avg_rev(const KParams& P, const FaceAvg<NS, D>& f, double lX, double lc,
+                                             double* lUb) {
+  const double a = f.tb.a, a2 = a * a;
+  double lrho = lc * a, la = lc * f.rb;
+  const double lXN = lX / f.XD, lXD = -lX * f.X / f.XD;
+  lrho += lXN * a2 * f.tb.be + lXD * f.tb.al * a2;
+  la += (lXN * f.rb * f.tb.be + lXD * f.tb.al * f.rb) * 2.0 * a;
+  const double lbe = lXN * f.rb * a2, lal = lXD * a2 * f.rb;
+  double lYb[NS], lpb = 0.0, lTb = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) lYb[k] = 0.0;
+  thermo_rev<NS>(P, f.tb, 0.0, 0.0, la, lal, lbe, lYb, lpb, lTb);
+  double leb = 0.0, lvb = 0.0;
+  pt_rev<NS>(P, f.Yb, f.pb, f.Tb, f.tb.r, lpb, lTb, lYb, leb, lvb);
+  const double lub[3] = {0.0, 0.0, 0.0};
+  decode_rev<NS, D>(f.Ub, f.rb, f.Yb, f.ub, lrho, lYb, lub, leb, lvb, lUb);
+}
+
 template <int NS, int D>
 __global__ void __launch_bounds__(VJP_THREADS)
     k_face_adj(const KParams P, const int d, const double* __restrict__ Wc, const double* __restrict__ Uk,
                const double* __restrict__ Uin, const double* __restrict__ scal, const uint32_t* __restrict__ tape,
                const double* __restrict__ lamL, const double coef, const int mul_dt, double* __restrict__ C) {
   constexpr int NV = NS + D + 1;
-  constexpr int NL = Lay<NS, D>::NL;
   const int f0 = P.n[0] + (d == 0), f1 = P.n[1] + (d == 1), f2 = P.n[2] + (d == 2);
   const long long nf = (long long)f0 * f1 * f2;
   const long long fid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -161,77 +212,75 @@ __global__ void __launch_bounds__(VJP_THREADS)
     return;
   }
   const uint32_t fl = tape[fid];
-
-  // ---------------- forward recomputation ----------------
-  double Ui[NV], Uj[NV], Ub[NV];
-  load_U<NS, D>(P, Uk, Uin, ri, Ui);
-  load_U<NS, D>(P, Uk, Uin, rj, Uj);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Ub[v] = 0.5 * (Ui[v] + Uj[v]);
-  double rb, Yb[NS], ubv[3], eb, vb, pb, Tb;
-  decode<NS, D>(Ub, rb, Yb, ubv, eb, vb);
-  pt_equilibrium<NS>(P, Yb, eb, vb, pb, Tb);
-  Thermo<NS> tb;
-#pragma unroll
-  for (int k = 0; k < NS; ++k) tb.Y[k] = Yb[k];
-  tb.p = pb;
-  tb.T = Tb;
-  thermo_fwd<NS>(P, tb);
-  const double a2 = tb.a * tb.a;
-  const double XN = rb * a2 * tb.be - 1.0, XD = tb.al * a2 * rb;
-  const double X = XN / XD, c = tb.a * rb, ic = 1.0 / c;
-
-  double Ts[6], Ps[6], us[6], w1[6], w5[6], w6[6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    Ts[j] = wget(P, Wc, P.wT, cr[j]);
-    Ps[j] = wget(P, Wc, P.wP, cr[j]);
-    us[j] = wget(P, Wc, P.wU + d, cr[j]) * sgn_flip(cr[j].flip, d);
-    w1[j] = Ts[j] - X * Ps[j];
-    w5[j] = (0.5 * c) * us[j] + 0.5 * Ps[j];
-    w6[j] = (-0.5 * c) * us[j] + 0.5 * Ps[j];
-  }
-  const double w1L = weno5z(w1[0], w1[1], w1[2], w1[3], w1[4], eps);
-  const double w1R = weno5z(w1[5], w1[4], w1[3], w1[2], w1[1], eps);
-  const double w5L = weno5z(w5[0], w5[1], w5[2], w5[3], w5[4], eps);
-  const double w5R = weno5z(w5[5], w5[4], w5[3], w5[2], w5[1], eps);
-  const double w6L = weno5z(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-  const double w6R = weno5z(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
-  double TL = w1L + X * w5L + X * w6L, TR = w1R + X * w5R + X * w6R;
-  double uL[3] = {0.0, 0.0, 0.0}, uR[3] = {0.0, 0.0, 0.0};
-  uL[d] = ic * w5L + (-ic) * w6L;
-  uR[d] = ic * w5R + (-ic) * w6R;
-  double PL = w5L + w6L, PR = w5R + w6R;
   // six-cell stencil of a cache field (velocity components with the wall sign)
   auto stencil = [&](int f, int t, double* y) {
 #pragma unroll
     for (int j = 0; j < 6; ++j) y[j] = wget(P, Wc, f, cr[j]) * (t >= 0 ? sgn_flip(cr[j].flip, t) : 1.0);
   };
-  double YL[NS], YR[NS];
+
+  // ================= forward recomputation (values only) =================
+  FaceAvg<NS, D> fa;
+  face_avg_fwd<NS, D>(P, Uk, Uin, ri, rj, fa);
+  const double X = fa.X, c = fa.c, ic = 1.0 / c;
+  // reconstruction values with their gradients w.r.t. the stencil values
+  double TL, TR, PL, PR, uL[3] = {0.0, 0.0, 0.0}, uR[3] = {0.0, 0.0, 0.0};
+  double g1L[5], g1R[5], g5L[5], g5R[5], g6L[5], g6R[5], w5L, w5R, w6L, w6R;
+  double gYL[NS][5], gYR[NS][5], gtL[2][5], gtR[2][5];
+  {
+    double w1[6], w5[6], w6[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const double Tj_ = wget(P, Wc, P.wT, cr[j]), Pj_ = wget(P, Wc, P.wP, cr[j]);
+      const double un = wget(P, Wc, P.wU + d, cr[j]) * sgn_flip(cr[j].flip, d);
+      w1[j] = Tj_ - X * Pj_;
+      w5[j] = (0.5 * c) * un + 0.5 * Pj_;
+      w6[j] = (-0.5 * c) * un + 0.5 * Pj_;
+    }
+    const double w1L = weno_val_grad(w1[0], w1[1], w1[2], w1[3], w1[4], eps, g1L);
+    const double w1R = weno_val_grad(w1[5], w1[4], w1[3], w1[2], w1[1], eps, g1R);
+    w5L = weno_val_grad(w5[0], w5[1], w5[2], w5[3], w5[4], eps, g5L);
+    w5R = weno_val_grad(w5[5], w5[4], w5[3], w5[2], w5[1], eps, g5R);
+    w6L = weno_val_grad(w6[0], w6[1], w6[2], w6[3], w6[4], eps, g6L);
+    w6R = weno_val_grad(w6[5], w6[4], w6[3], w6[2], w6[1], eps, g6R);
+    TL = w1L + X * w5L + X * w6L;
+    TR = w1R + X * w5R + X * w6R;
+    uL[d] = ic * w5L + (-ic) * w6L;
+    uR[d] = ic * w5R + (-ic) * w6R;
+    PL = w5L + w6L;
+    PR = w5R + w6R;
+  }
+  double YLp[NS], YRp[NS];   // before the Y limiter
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     double y[6];
     stencil(P.wY + k, -1, y);
-    YL[k] = weno5z(y[0], y[1], y[2], y[3], y[4], eps);
-    YR[k] = weno5z(y[5], y[4], y[3], y[2], y[1], eps);
+    YLp[k] = weno_val_grad(y[0], y[1], y[2], y[3], y[4], eps, gYL[k]);
+    YRp[k] = weno_val_grad(y[5], y[4], y[3], y[2], y[1], eps, gYR[k]);
   }
+  {
+    int tt = 0;
 #pragma unroll
-  for (int t = 0; t < D; ++t) {
-    if (t == d) continue;
-    double y[6];
-    stencil(P.wU + t, t, y);
-    uL[t] = weno5z(y[0], y[1], y[2], y[3], y[4], eps);
-    uR[t] = weno5z(y[5], y[4], y[3], y[2], y[1], eps);
+    for (int t = 0; t < D; ++t) {
+      if (t == d) continue;
+      double y[6];
+      stencil(P.wU + t, t, y);
+      uL[t] = weno_val_grad(y[0], y[1], y[2], y[3], y[4], eps, gtL[tt]);
+      uR[t] = weno_val_grad(y[5], y[4], y[3], y[2], y[1], eps, gtR[tt]);
+      ++tt;
+    }
   }
-  double Yi[NS], Yj[NS];
+  double Yi[NS], Yj[NS], YL[NS], YR[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     Yi[k] = wget(P, Wc, P.wY + k, ri);
     Yj[k] = wget(P, Wc, P.wY + k, rj);
+    YL[k] = YLp[k];
+    YR[k] = YRp[k];
   }
-  const double Ti = Ts[2], Tj = Ts[3], Pi = Ps[2], Pj = Ps[3];
-  YLim<NS> yl, yr;
+  const double Ti = wget(P, Wc, P.wT, ri), Tj = wget(P, Wc, P.wT, rj);
+  const double Pi = wget(P, Wc, P.wP, ri), Pj = wget(P, Wc, P.wP, rj);
   if (P.pos_limiter) {
+    YLim<NS> yl, yr;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       yl.Yc[k] = Yi[k];
@@ -245,91 +294,61 @@ __global__ void __launch_bounds__(VJP_THREADS)
     if (fl & F_THETA_P_R) PR = Pj;
   }
   const bool fallback = (fl & F_HLLC_FALLBACK) != 0;
-  Thermo<NS> tL, tR;
-  St<NS> sL, sR;
-  if (!fallback) {
+
+  // ================= reverse sweep =================
+  // adjoints gathered on the two neighbour cells (slots 2 and 3) before the
+  // reconstruction's reverse; index 0 = cell i, 1 = cell i+1
+  double aT[2] = {0.0, 0.0}, aP[2] = {0.0, 0.0}, aY[2][NS], aU3[2][3], aRho[2] = {0.0, 0.0}, aA[2] = {0.0, 0.0};
+  double aU[2][NV];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      tL.Y[k] = YL[k];
-      tR.Y[k] = YR[k];
-    }
-    tL.p = PL; tL.T = TL; tR.p = PR; tR.T = TR;
-    face_state<NS>(P, tL, uL, sL);
-    face_state<NS>(P, tR, uR, sR);
-  } else {
-    sL.rho = wget(P, Wc, P.wRho, ri);
-    sR.rho = wget(P, Wc, P.wRho, rj);
+  for (int s2 = 0; s2 < 2; ++s2) {
 #pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      sL.rhoY[k] = Ui[k];
-      sR.rhoY[k] = Uj[k];
-    }
+    for (int k = 0; k < NS; ++k) aY[s2][k] = 0.0;
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      sL.u[t] = t < D ? wget(P, Wc, P.wU + t, ri) * sgn_flip(ri.flip, t) : 0.0;
-      sR.u[t] = t < D ? wget(P, Wc, P.wU + t, rj) * sgn_flip(rj.flip, t) : 0.0;
-      sL.m[t] = t < D ? Ui[NS + t] : 0.0;
-      sR.m[t] = t < D ? Uj[NS + t] : 0.0;
-    }
-    sL.p = Pi; sR.p = Pj;
-    sL.E = Ui[NS + D]; sR.E = Uj[NS + D];
-    sL.a = wget(P, Wc, P.wA, ri);
-    sR.a = wget(P, Wc, P.wA, rj);
+    for (int t = 0; t < 3; ++t) aU3[s2][t] = 0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) aU[s2][v] = 0.0;
   }
 
-  // ---------------- reverse sweep ----------------
-  // adjoints of cache fields of the six stencil cells and of the neighbours
-  double gT[6], gP[6], gu[6], gY[NS][6], gut[3][6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    gT[j] = 0.0; gP[j] = 0.0; gu[j] = 0.0;
-#pragma unroll
-    for (int k = 0; k < NS; ++k) gY[k][j] = 0.0;
-#pragma unroll
-    for (int t = 0; t < 3; ++t) gut[t][j] = 0.0;
-  }
-  double gUi[NV], gUj[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) { gUi[v] = 0.0; gUj[v] = 0.0; }
-  double grho_i = 0.0, grho_j = 0.0, ga_i = 0.0, ga_j = 0.0;
-  double gu_i[3] = {0.0, 0.0, 0.0}, gu_j[3] = {0.0, 0.0, 0.0};
-
-  // species diffusion
+  // ---- species diffusion (Eq. SpeciesMassDiffusion), stores its cache slots
   if (P.diffusion) {
     const double rbar = 0.5 * (wget(P, Wc, P.wRho, ri) + wget(P, Wc, P.wRho, rj));
     double lrb = 0.0;
 #pragma unroll
     for (int ph = 0; ph < 2; ++ph) {
-      double Yp = 0.0, S = 0.0, Bf[NS], G[NS], Bi[NS], Bj[NS], xi[NS], xj[NS];
+      double Yp = 0.0, S = 0.0, Bf[NS], G[NS];
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        Bf[k] = 0.0; G[k] = 0.0;
+        Bf[k] = 0.0;
+        G[k] = 0.0;
         if (P.phase[k] != ph) continue;
         Yp += 0.5 * (Yi[k] + Yj[k]);
-        Bi[k] = wget(P, Wc, P.wB + k, ri); Bj[k] = wget(P, Wc, P.wB + k, rj);
-        xi[k] = wget(P, Wc, P.wXr + k, ri); xj[k] = wget(P, Wc, P.wXr + k, rj);
-        Bf[k] = 0.5 * (Bi[k] + Bj[k]);
-        G[k] = (xj[k] - xi[k]) * P.inv_dx;
+        Bf[k] = 0.5 * (wget(P, Wc, P.wB + k, ri) + wget(P, Wc, P.wB + k, rj));
+        G[k] = (wget(P, Wc, P.wXr + k, rj) - wget(P, Wc, P.wXr + k, ri)) * P.inv_dx;
         S += Bf[k] * G[k];
       }
       double lYp = 0.0, lS = 0.0, lBf[NS], lG[NS];
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        lBf[k] = 0.0; lG[k] = 0.0;
+        lBf[k] = 0.0;
+        lG[k] = 0.0;
         if (P.phase[k] != ph) continue;
         const double Ybk = 0.5 * (Yi[k] + Yj[k]);
         const double J = -rbar * (Yp * Bf[k] * G[k] - Ybk * S);
         const double hi = h_k(P, k, Pi, Ti), hj = h_k(P, k, Pj, Tj);
         const double lJ = nu[k] + nu[NS + D] * 0.5 * (hi + hj);
         const double lh = nu[NS + D] * J * 0.5;
-        gT[2] += lh * P.cp[k]; gP[2] += lh * P.b[k];
-        gT[3] += lh * P.cp[k]; gP[3] += lh * P.b[k];
+        aT[0] += lh * P.cp[k];
+        aP[0] += lh * P.b[k];
+        aT[1] += lh * P.cp[k];
+        aP[1] += lh * P.b[k];
         lrb -= lJ * (Yp * Bf[k] * G[k] - Ybk * S);
         lYp -= rbar * lJ * Bf[k] * G[k];
         lBf[k] -= rbar * lJ * Yp * G[k];
         lG[k] -= rbar * lJ * Yp * Bf[k];
         const double lYb = rbar * lJ * S;
-        gY[k][2] += 0.5 * lYb; gY[k][3] += 0.5 * lYb;
+        aY[0][k] += 0.5 * lYb;
+        aY[1][k] += 0.5 * lYb;
         lS += rbar * lJ * Ybk;
       }
 #pragma unroll
@@ -337,57 +356,62 @@ __global__ void __launch_bounds__(VJP_THREADS)
         if (P.phase[k] != ph) continue;
         lBf[k] += lS * G[k];
         lG[k] += lS * Bf[k];
-        gY[k][2] += 0.5 * lYp; gY[k][3] += 0.5 * lYp;
+        aY[0][k] += 0.5 * lYp;
+        aY[1][k] += 0.5 * lYp;
         put(L.nbq(0, L.qB + k), 0.5 * lBf[k]);
         put(L.nbq(1, L.qB + k), 0.5 * lBf[k]);
         put(L.nbq(1, L.qXr + k), lG[k] * P.inv_dx);
         put(L.nbq(0, L.qXr + k), -lG[k] * P.inv_dx);
       }
     }
-    grho_i += 0.5 * lrb; grho_j += 0.5 * lrb;
+    aRho[0] += 0.5 * lrb;
+    aRho[1] += 0.5 * lrb;
   }
 
-  // interface regularization (if the forward added it); its cache-field
-  // adjoints are gathered here and stored below
-  double cYr[2][NS], cHr[2][2], cPhi[2] = {0.0, 0.0}, cPsi[2] = {0.0, 0.0}, cPsiT[2][4];
+  // ---- interface regularization (if the forward added it), stores its slots
+  if (P.cdi) {
+    double cYr[2][NS], cHr[2][2] = {{0.0, 0.0}, {0.0, 0.0}}, cPhi[2] = {0.0, 0.0}, cPsi[2] = {0.0, 0.0};
+    double cPsiT[2][4];
 #pragma unroll
-  for (int s2 = 0; s2 < 2; ++s2) {
+    for (int s2 = 0; s2 < 2; ++s2) {
 #pragma unroll
-    for (int k = 0; k < NS; ++k) cYr[s2][k] = 0.0;
-    cHr[s2][0] = 0.0;
-    cHr[s2][1] = 0.0;
+      for (int k = 0; k < NS; ++k) cYr[s2][k] = 0.0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) cPsiT[s2][q] = 0.0;
-  }
-  if (P.cdi && P.two_phase && !(fl & F_CDI_DROPPED)) {
+      for (int q = 0; q < 4; ++q) cPsiT[s2][q] = 0.0;
+    }
     bool pres_i[2], pres_j[2];
     {
       double ypi[2] = {0.0, 0.0}, ypj[2] = {0.0, 0.0};
 #pragma unroll
-      for (int k = 0; k < NS; ++k) { ypi[P.phase[k]] += Yi[k]; ypj[P.phase[k]] += Yj[k]; }
+      for (int k = 0; k < NS; ++k) {
+        ypi[P.phase[k]] += Yi[k];
+        ypj[P.phase[k]] += Yj[k];
+      }
 #pragma unroll
-      for (int ph = 0; ph < 2; ++ph) { pres_i[ph] = ypi[ph] >= ABSENT; pres_j[ph] = ypj[ph] >= ABSENT; }
+      for (int ph = 0; ph < 2; ++ph) {
+        pres_i[ph] = ypi[ph] >= ABSENT;
+        pres_j[ph] = ypj[ph] >= ABSENT;
+      }
     }
-    if ((pres_i[0] || pres_j[0]) && (pres_i[1] || pres_j[1])) {
+    if (P.two_phase && !(fl & F_CDI_DROPPED) && (pres_i[0] || pres_j[0]) && (pres_i[1] || pres_j[1])) {
       const double ceps = P.cdi_eps;
       const double psi_i = wget(P, Wc, P.wPsi, ri), psi_j = wget(P, Wc, P.wPsi, rj);
       const double dphi = (wget(P, Wc, P.wPhi0, rj) - wget(P, Wc, P.wPhi0, ri)) * P.inv_dx;
       double g[3] = {0.0, 0.0, 0.0};
-      CRef nb[3][4];
       g[d] = (psi_j - psi_i) * P.inv_dx;
 #pragma unroll
       for (int t = 0; t < D; ++t) {
         if (t == d) continue;
         int a0[3] = {ci[0], ci[1], ci[2]}, a1[3] = {ci[0], ci[1], ci[2]};
-        a0[t] += 1; a1[t] -= 1;
+        a0[t] += 1;
+        a1[t] -= 1;
         int b0[3] = {a0[0], a0[1], a0[2]}, b1[3] = {a1[0], a1[1], a1[2]};
-        b0[d] += 1; b1[d] += 1;
-        nb[t][0] = map_cell(P, a0[0], a0[1], a0[2]);
-        nb[t][1] = map_cell(P, a1[0], a1[1], a1[2]);
-        nb[t][2] = map_cell(P, b0[0], b0[1], b0[2]);
-        nb[t][3] = map_cell(P, b1[0], b1[1], b1[2]);
-        g[t] = 0.5 * ((wget(P, Wc, P.wPsi, nb[t][0]) - wget(P, Wc, P.wPsi, nb[t][1])) * (0.5 * P.inv_dx) +
-                      (wget(P, Wc, P.wPsi, nb[t][2]) - wget(P, Wc, P.wPsi, nb[t][3])) * (0.5 * P.inv_dx));
+        b0[d] += 1;
+        b1[d] += 1;
+        g[t] = 0.5 * ((wget(P, Wc, P.wPsi, map_cell(P, a0[0], a0[1], a0[2])) -
+                       wget(P, Wc, P.wPsi, map_cell(P, a1[0], a1[1], a1[2]))) * (0.5 * P.inv_dx) +
+                      (wget(P, Wc, P.wPsi, map_cell(P, b0[0], b0[1], b0[2])) -
+                       wget(P, Wc, P.wPsi, map_cell(P, b1[0], b1[1], b1[2]))) * (0.5 * P.inv_dx));
       }
       const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
       const bool nact = gn >= GTOL;
@@ -396,21 +420,13 @@ __global__ void __launch_bounds__(VJP_THREADS)
       const double ch = cosh(xarg);
       const double sech2 = 1.0 / (ch * ch);
       const double ahat0 = Gamma * (ceps * dphi - 0.25 * (sech2 - P.sharp0) * nd);
-      // forward pieces
-      double Rtot = 0.0, kb = 0.0, yr_i[NS], yr_j[NS], hr_i[2], hr_j[2];
-#pragma unroll
-      for (int ph = 0; ph < 2; ++ph) {
-        hr_i[ph] = wget(P, Wc, P.wHrho + ph, ri);
-        hr_j[ph] = wget(P, Wc, P.wHrho + ph, rj);
-      }
+      double Rtot = 0.0, kb = 0.0;
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        yr_i[k] = wget(P, Wc, P.wYrho + k, ri);
-        yr_j[k] = wget(P, Wc, P.wYrho + k, rj);
         const bool pi = pres_i[P.phase[k]], pj = pres_j[P.phase[k]];
-        const double kp = pi && pj ? 0.5 * (yr_i[k] + yr_j[k]) : (pi ? yr_i[k] : (pj ? yr_j[k] : 0.0));
-        const double ah = P.phase[k] == 0 ? ahat0 : -ahat0;
-        Rtot += -kp * ah;
+        const double yi = wget(P, Wc, P.wYrho + k, ri), yj = wget(P, Wc, P.wYrho + k, rj);
+        const double kp = pi && pj ? 0.5 * (yi + yj) : (pi ? yi : (pj ? yj : 0.0));
+        Rtot += -kp * (P.phase[k] == 0 ? ahat0 : -ahat0);
       }
       double ui[3] = {0.0, 0.0, 0.0}, uj[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -419,14 +435,13 @@ __global__ void __launch_bounds__(VJP_THREADS)
         uj[t] = wget(P, Wc, P.wU + t, rj) * sgn_flip(rj.flip, t);
         kb += ui[t] * uj[t];
       }
-      // reverse
       double lRtot = nu[NS + D] * 0.5 * kb;
       const double lkb = nu[NS + D] * 0.5 * Rtot;
 #pragma unroll
       for (int t = 0; t < D; ++t) {
         lRtot += nu[NS + t] * 0.5 * (ui[t] + uj[t]);
-        gu_i[t] += nu[NS + t] * 0.5 * Rtot + lkb * uj[t];
-        gu_j[t] += nu[NS + t] * 0.5 * Rtot + lkb * ui[t];
+        aU3[0][t] += nu[NS + t] * 0.5 * Rtot + lkb * uj[t];
+        aU3[1][t] += nu[NS + t] * 0.5 * Rtot + lkb * ui[t];
       }
       const double lhR = nu[NS + D];
       double lahat0 = 0.0;
@@ -434,9 +449,10 @@ __global__ void __launch_bounds__(VJP_THREADS)
       for (int k = 0; k < NS; ++k) {
         const int ph = P.phase[k];
         const bool pi = pres_i[ph], pj = pres_j[ph];
-        const double kp = pi && pj ? 0.5 * (yr_i[k] + yr_j[k]) : (pi ? yr_i[k] : (pj ? yr_j[k] : 0.0));
+        const double yi = wget(P, Wc, P.wYrho + k, ri), yj = wget(P, Wc, P.wYrho + k, rj);
+        const double kp = pi && pj ? 0.5 * (yi + yj) : (pi ? yi : (pj ? yj : 0.0));
         const double sgn = ph == 0 ? 1.0 : -1.0;
-        const double lR = nu[k] + lRtot;            // R_k = -kp * sgn * ahat0
+        const double lR = nu[k] + lRtot;   // R_k = -kp sgn ahat0
         const double lkp = -lR * sgn * ahat0;
         lahat0 += -lR * kp * sgn;
         if (pi && pj) {
@@ -451,8 +467,9 @@ __global__ void __launch_bounds__(VJP_THREADS)
 #pragma unroll
       for (int ph = 0; ph < 2; ++ph) {
         const bool pi = pres_i[ph], pj = pres_j[ph];
-        const double kh = pi && pj ? 0.5 * (hr_i[ph] + hr_j[ph]) : (pi ? hr_i[ph] : (pj ? hr_j[ph] : 0.0));
-        const double sgn = ph == 0 ? 1.0 : -1.0;   // hR -= kh * sgn * ahat0
+        const double hi = wget(P, Wc, P.wHrho + ph, ri), hj = wget(P, Wc, P.wHrho + ph, rj);
+        const double kh = pi && pj ? 0.5 * (hi + hj) : (pi ? hi : (pj ? hj : 0.0));
+        const double sgn = ph == 0 ? 1.0 : -1.0;   // hR -= kh sgn ahat0
         const double lkh = -lhR * sgn * ahat0;
         lahat0 += -lhR * kh * sgn;
         if (pi && pj) {
@@ -496,182 +513,6 @@ __global__ void __launch_bounds__(VJP_THREADS)
       cPsi[0] = lpsi_i;
       cPsi[1] = lpsi_j;
     }
-  }
-
-  // HLLC
-  StAdj<NS> gL, gR;
-  gL.zero();
-  gR.zero();
-  hllc_rev<NS, D>(d, sL, sR, nu, gL, gR);
-  double lTL = 0.0, lTR = 0.0, lPL = 0.0, lPR = 0.0, lYL[NS], lYR[NS], luL[3] = {0.0, 0.0, 0.0},
-         luR[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-  for (int k = 0; k < NS; ++k) { lYL[k] = 0.0; lYR[k] = 0.0; }
-  if (fallback) {
-    grho_i += gL.rho; grho_j += gR.rho;
-#pragma unroll
-    for (int k = 0; k < NS; ++k) { gUi[k] += gL.rhoY[k]; gUj[k] += gR.rhoY[k]; }
-#pragma unroll
-    for (int t = 0; t < D; ++t) {
-      gu_i[t] += gL.u[t]; gu_j[t] += gR.u[t];
-      gUi[NS + t] += gL.m[t]; gUj[NS + t] += gR.m[t];
-    }
-    gP[2] += gL.p; gP[3] += gR.p;
-    gUi[NS + D] += gL.E; gUj[NS + D] += gR.E;
-    ga_i += gL.a; ga_j += gR.a;
-  } else {
-    face_state_rev<NS>(P, tL, sL, gL, lYL, luL, lPL, lTL);
-    face_state_rev<NS>(P, tR, sR, gR, lYR, luR, lPR, lTR);
-  }
-
-  // interpolation limiters (replayed)
-  if (P.pos_limiter) {
-    if (fl & F_THETA_T_L) { gT[2] += lTL; lTL = 0.0; }
-    if (fl & F_THETA_T_R) { gT[3] += lTR; lTR = 0.0; }
-    if (fl & F_THETA_P_L) { gP[2] += lPL; lPL = 0.0; }
-    if (fl & F_THETA_P_R) { gP[3] += lPR; lPR = 0.0; }
-    double lYLi[NS], lYRi[NS], lYci[NS], lYcj[NS];
-#pragma unroll
-    for (int k = 0; k < NS; ++k) { lYLi[k] = 0.0; lYRi[k] = 0.0; lYci[k] = 0.0; lYcj[k] = 0.0; }
-    ylim_rev<NS>(yl, lYL, lYLi, lYci);
-    ylim_rev<NS>(yr, lYR, lYRi, lYcj);
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      lYL[k] = lYLi[k]; lYR[k] = lYRi[k];
-      gY[k][2] += lYci[k]; gY[k][3] += lYcj[k];
-    }
-  }
-
-  // WENO of mass fractions and tangential velocities (recomputed, reversed)
-#pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    double y[6];
-    stencil(P.wY + k, -1, y);
-    Weno W;
-    double gv[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    weno_fwd(W, y[0], y[1], y[2], y[3], y[4], eps);
-    weno_rev(W, lYL[k], gv);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) gY[k][j] += gv[j];
-    double hv[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    weno_fwd(W, y[5], y[4], y[3], y[2], y[1], eps);
-    weno_rev(W, lYR[k], hv);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) gY[k][5 - j] += hv[j];
-  }
-#pragma unroll
-  for (int t = 0; t < D; ++t) {
-    if (t == d) continue;
-    double y[6];
-    stencil(P.wU + t, t, y);
-    Weno W;
-    double gv[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    weno_fwd(W, y[0], y[1], y[2], y[3], y[4], eps);
-    weno_rev(W, luL[t], gv);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) gut[t][j] += gv[j];
-    double hv[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    weno_fwd(W, y[5], y[4], y[3], y[2], y[1], eps);
-    weno_rev(W, luR[t], hv);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) gut[t][5 - j] += hv[j];
-  }
-
-  // back-projection: T = w1 + X (w5 + w6), u = ic (w5 - w6), P = w5 + w6
-  double lX = 0.0, lic = 0.0, lw1[6], lw5[6], lw6[6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) { lw1[j] = 0.0; lw5[j] = 0.0; lw6[j] = 0.0; }
-  {
-    const double l1 = lTL, l5 = X * lTL + ic * luL[d] + lPL, l6 = X * lTL - ic * luL[d] + lPL;
-    lX += lTL * (w5L + w6L);
-    lic += luL[d] * (w5L - w6L);
-    double g1[5] = {0, 0, 0, 0, 0}, g5[5] = {0, 0, 0, 0, 0}, g6[5] = {0, 0, 0, 0, 0};
-    Weno W;
-    weno_fwd(W, w1[0], w1[1], w1[2], w1[3], w1[4], eps);
-    weno_rev(W, l1, g1);
-    weno_fwd(W, w5[0], w5[1], w5[2], w5[3], w5[4], eps);
-    weno_rev(W, l5, g5);
-    weno_fwd(W, w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-    weno_rev(W, l6, g6);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) { lw1[j] += g1[j]; lw5[j] += g5[j]; lw6[j] += g6[j]; }
-  }
-  {
-    const double l1 = lTR, l5 = X * lTR + ic * luR[d] + lPR, l6 = X * lTR - ic * luR[d] + lPR;
-    lX += lTR * (w5R + w6R);
-    lic += luR[d] * (w5R - w6R);
-    double g1[5] = {0, 0, 0, 0, 0}, g5[5] = {0, 0, 0, 0, 0}, g6[5] = {0, 0, 0, 0, 0};
-    Weno W;
-    weno_fwd(W, w1[5], w1[4], w1[3], w1[2], w1[1], eps);
-    weno_rev(W, l1, g1);
-    weno_fwd(W, w5[5], w5[4], w5[3], w5[2], w5[1], eps);
-    weno_rev(W, l5, g5);
-    weno_fwd(W, w6[5], w6[4], w6[3], w6[2], w6[1], eps);
-    weno_rev(W, l6, g6);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) { lw1[5 - j] += g1[j]; lw5[5 - j] += g5[j]; lw6[5 - j] += g6[j]; }
-  }
-  // projection: w1 = T - X P, w5 = c/2 u + P/2, w6 = -c/2 u + P/2
-  double lc = -lic * ic * ic;
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    gT[j] += lw1[j];
-    gP[j] += -X * lw1[j] + 0.5 * (lw5[j] + lw6[j]);
-    lX -= Ps[j] * lw1[j];
-    gu[j] += 0.5 * c * (lw5[j] - lw6[j]);
-    lc += 0.5 * us[j] * (lw5[j] - lw6[j]);
-  }
-  // characteristic scalars at the averaged state: X = XN / XD, c = a rho
-  {
-    const double a = tb.a;
-    double lrho = lc * a, la = lc * rb;
-    const double lXN = lX / XD, lXD = -lX * X / XD;
-    lrho += lXN * a2 * tb.be + lXD * tb.al * a2;
-    la += (lXN * rb * tb.be + lXD * tb.al * rb) * 2.0 * a;
-    const double lbe = lXN * rb * a2, lal = lXD * a2 * rb;
-    double lYb[NS], lpb = 0.0, lTb = 0.0;
-#pragma unroll
-    for (int k = 0; k < NS; ++k) lYb[k] = 0.0;
-    thermo_rev<NS>(P, tb, 0.0, 0.0, la, lal, lbe, lYb, lpb, lTb);
-    double leb = 0.0, lvb = 0.0;
-    pt_rev<NS>(P, Yb, pb, Tb, lpb, lTb, lYb, leb, lvb);
-    double lUb[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) lUb[v] = 0.0;
-    const double lub[3] = {0.0, 0.0, 0.0};
-    decode_rev<NS, D>(Ub, rb, Yb, ubv, lrho, lYb, lub, leb, lvb, lUb);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { gUi[v] += 0.5 * lUb[v]; gUj[v] += 0.5 * lUb[v]; }
-  }
-
-  // ---------------- store (the face's frame; the gather applies mirror signs)
-#pragma unroll
-  for (int t = 0; t < D; ++t) {
-    if (t == d) {
-      gu[2] += gu_i[t];
-      gu[3] += gu_j[t];
-    } else {
-      gut[t][2] += gu_i[t];
-      gut[t][3] += gu_j[t];
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    put(L.line(j, 0), gT[j]);
-    put(L.line(j, 1), gP[j]);
-    put(L.line(j, 2), gu[j]);
-#pragma unroll
-    for (int k = 0; k < NS; ++k) put(L.line(j, 3 + k), gY[k][j]);
-    int q = 3 + NS;
-#pragma unroll
-    for (int t = 0; t < D; ++t)
-      if (t != d) put(L.line(j, q++), gut[t][j]);
-  }
-  put(L.nbq(0, 0), grho_i);
-  put(L.nbq(1, 0), grho_j);
-  put(L.nbq(0, 1), ga_i);
-  put(L.nbq(1, 1), ga_j);
-  if (P.cdi) {
 #pragma unroll
     for (int s2 = 0; s2 < 2; ++s2) {
 #pragma unroll
@@ -686,12 +527,199 @@ __global__ void __launch_bounds__(VJP_THREADS)
 #pragma unroll
       for (int q = 0; q < 4; ++q) put(L.psi0 + 4 * tt + q, cPsiT[tt][q]);
   }
+
+  // ---- face states and HLLC (Appendix B), built here and reversed at once
+  double lTL = 0.0, lTR = 0.0, lPL = 0.0, lPR = 0.0, lYL[NS], lYR[NS], luL[3] = {0.0, 0.0, 0.0},
+         luR[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    put(L.nbq(0, L.qU + v), gUi[v]);
-    put(L.nbq(1, L.qU + v), gUj[v]);
+  for (int k = 0; k < NS; ++k) {
+    lYL[k] = 0.0;
+    lYR[k] = 0.0;
   }
-  (void)NL;
+  if (!fallback) {
+    Thermo<NS> tL, tR;
+    St<NS> sL, sR;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      tL.Y[k] = YL[k];
+      tR.Y[k] = YR[k];
+    }
+    tL.p = PL;
+    tL.T = TL;
+    tR.p = PR;
+    tR.T = TR;
+    face_state<NS>(P, tL, uL, sL);
+    face_state<NS>(P, tR, uR, sR);
+    StAdj<NS> gL, gR;
+    gL.zero();
+    gR.zero();
+    hllc_rev<NS, D>(d, sL, sR, nu, gL, gR);
+    face_state_rev<NS>(P, tL, sL, gL, lYL, luL, lPL, lTL);
+    face_state_rev<NS>(P, tR, sR, gR, lYR, luR, lPR, lTR);
+  } else {
+    // first-order fallback: HLLC of the two cells' own states
+    St<NS> sL, sR;
+    double Ui[NV], Uj[NV];
+    load_U<NS, D>(P, Uk, Uin, ri, Ui);
+    load_U<NS, D>(P, Uk, Uin, rj, Uj);
+    sL.rho = wget(P, Wc, P.wRho, ri);
+    sR.rho = wget(P, Wc, P.wRho, rj);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      sL.rhoY[k] = Ui[k];
+      sR.rhoY[k] = Uj[k];
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      sL.u[t] = t < D ? wget(P, Wc, P.wU + t, ri) * sgn_flip(ri.flip, t) : 0.0;
+      sR.u[t] = t < D ? wget(P, Wc, P.wU + t, rj) * sgn_flip(rj.flip, t) : 0.0;
+      sL.m[t] = t < D ? Ui[NS + t] : 0.0;
+      sR.m[t] = t < D ? Uj[NS + t] : 0.0;
+    }
+    sL.p = Pi;
+    sR.p = Pj;
+    sL.E = Ui[NS + D];
+    sR.E = Uj[NS + D];
+    sL.a = wget(P, Wc, P.wA, ri);
+    sR.a = wget(P, Wc, P.wA, rj);
+    StAdj<NS> gL, gR;
+    gL.zero();
+    gR.zero();
+    hllc_rev<NS, D>(d, sL, sR, nu, gL, gR);
+    aRho[0] += gL.rho;
+    aRho[1] += gR.rho;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      aU[0][k] += gL.rhoY[k];
+      aU[1][k] += gR.rhoY[k];
+    }
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      aU3[0][t] += gL.u[t];
+      aU3[1][t] += gR.u[t];
+      aU[0][NS + t] += gL.m[t];
+      aU[1][NS + t] += gR.m[t];
+    }
+    aP[0] += gL.p;
+    aP[1] += gR.p;
+    aU[0][NS + D] += gL.E;
+    aU[1][NS + D] += gR.E;
+    aA[0] += gL.a;
+    aA[1] += gR.a;
+  }
+
+  // ---- interpolation limiters (replayed; the Y limiter recomputed)
+  if (P.pos_limiter) {
+    if (fl & F_THETA_T_L) { aT[0] += lTL; lTL = 0.0; }
+    if (fl & F_THETA_T_R) { aT[1] += lTR; lTR = 0.0; }
+    if (fl & F_THETA_P_L) { aP[0] += lPL; lPL = 0.0; }
+    if (fl & F_THETA_P_R) { aP[1] += lPR; lPR = 0.0; }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      YLim<NS> ylm;
+      double tmp[NS], lin[NS], lc_[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        ylm.Yc[k] = side ? Yj[k] : Yi[k];
+        tmp[k] = side ? YRp[k] : YLp[k];
+        lin[k] = 0.0;
+        lc_[k] = 0.0;
+      }
+      ylim_fwd<NS>(ylm, tmp);
+      ylim_rev<NS>(ylm, side ? lYR : lYL, lin, lc_);
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        if (side) lYR[k] = lin[k];
+        else lYL[k] = lin[k];
+        aY[side][k] += lc_[k];
+      }
+    }
+  }
+
+  // ---- WENO of mass fractions and tangential velocities, reversed; slots stored
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    double gj[6];
+    gj[0] = lYL[k] * gYL[k][0];
+    gj[5] = lYR[k] * gYR[k][0];
+#pragma unroll
+    for (int j = 1; j < 5; ++j) gj[j] = lYL[k] * gYL[k][j] + lYR[k] * gYR[k][5 - j];
+    gj[2] += aY[0][k];
+    gj[3] += aY[1][k];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) put(L.line(j, 3 + k), gj[j]);
+  }
+  {
+    int tt = 0;
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      if (t == d) continue;
+      double gj[6];
+      gj[0] = luL[t] * gtL[tt][0];
+      gj[5] = luR[t] * gtR[tt][0];
+#pragma unroll
+      for (int j = 1; j < 5; ++j) gj[j] = luL[t] * gtL[tt][j] + luR[t] * gtR[tt][5 - j];
+      gj[2] += aU3[0][t];
+      gj[3] += aU3[1][t];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) put(L.line(j, 3 + NS + tt), gj[j]);
+      ++tt;
+    }
+  }
+
+  // ---- characteristic reconstruction, reversed: T = w1 + X (w5 + w6),
+  // u = ic (w5 - w6), P = w5 + w6 back-projection; w1 = T - X P,
+  // w5/6 = +-c/2 u + P/2 projection (Appendix A); slots stored
+  double lX = 0.0, lc;
+  {
+    const double l1L = lTL, l5L = X * lTL + ic * luL[d] + lPL, l6L = X * lTL - ic * luL[d] + lPL;
+    const double l1R = lTR, l5R = X * lTR + ic * luR[d] + lPR, l6R = X * lTR - ic * luR[d] + lPR;
+    lX += lTL * (w5L + w6L) + lTR * (w5R + w6R);
+    const double lic = luL[d] * (w5L - w6L) + luR[d] * (w5R - w6R);
+    lc = -lic * ic * ic;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      // left stencil v = w[0..4], right stencil v = w[5..1]
+      const double lw1 = (j < 5 ? l1L * g1L[j] : 0.0) + (j > 0 ? l1R * g1R[5 - j] : 0.0);
+      const double lw5 = (j < 5 ? l5L * g5L[j] : 0.0) + (j > 0 ? l5R * g5R[5 - j] : 0.0);
+      const double lw6 = (j < 5 ? l6L * g6L[j] : 0.0) + (j > 0 ? l6R * g6R[5 - j] : 0.0);
+      const double Pj_ = wget(P, Wc, P.wP, cr[j]);
+      const double un = wget(P, Wc, P.wU + d, cr[j]) * sgn_flip(cr[j].flip, d);
+      double gT_ = lw1;
+      double gP_ = -X * lw1 + 0.5 * (lw5 + lw6);
+      double gu_ = 0.5 * c * (lw5 - lw6);
+      lX -= Pj_ * lw1;
+      lc += 0.5 * un * (lw5 - lw6);
+      if (j == 2 || j == 3) {
+        gT_ += aT[j - 2];
+        gP_ += aP[j - 2];
+        gu_ += aU3[j - 2][d];
+      }
+      put(L.line(j, 0), gT_);
+      put(L.line(j, 1), gP_);
+      put(L.line(j, 2), gu_);
+    }
+  }
+
+  // ---- face-average scalars, reversed
+  {
+    double lUb[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) lUb[v] = 0.0;
+    face_avg_rev<NS, D>(P, fa, lX, lc, lUb);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      aU[0][v] += 0.5 * lUb[v];
+      aU[1][v] += 0.5 * lUb[v];
+    }
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < 2; ++s2) {
+    put(L.nbq(s2, 0), aRho[s2]);
+    put(L.nbq(s2, 1), aA[s2]);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) put(L.nbq(s2, L.qU + v), aU[s2][v]);
+  }
 }
 
 // preimages of real index c along one axis (length n, boundary codes lo/hi)
@@ -890,6 +918,22 @@ __global__ void __launch_bounds__(CELL_THREADS)
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= P.ncell) return;
   const long long ws = P.wstride;
+  {
+    // a cell whose cache adjoint is zero needs no primitive-recovery reverse
+    bool any = false;
+    for (int f = 0; f < P.nW; ++f) any = any || gW[(long long)f * ws + c] != 0.0;
+    if (!any) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const long long i = (long long)v * P.ncell + c;
+        double r = a * x[i] + gU[i];
+        if (y) r += b * y[i];
+        if (z) r += cz * z[i];
+        out[i] = r;
+      }
+      return;
+    }
+  }
   double Uc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) Uc[v] = U[(long long)v * P.ncell + c];
@@ -919,7 +963,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
       const int ph = P.phase[k];
       Yp[ph] += Y[k];
       if (Uc[k] != 0.0) {
-        phi[ph] += Uc[k] * v_k(P, k, p, T);
+        phi[ph] += Uc[k] * (P.Rk[k] * T * th.r[k] + P.b[k]);
         hr[ph] += Uc[k] * h_k(P, k, p, T);
       }
     }
@@ -932,16 +976,18 @@ __global__ void __launch_bounds__(CELL_THREADS)
 #pragma unroll
       for (int ph = 0; ph < 2; ++ph) {
         if (!(Yp[ph] >= ABSENT)) continue;
+        const double iphi = 1.0 / phi[ph];
         const double lh = gW[(P.wHrho + ph) * ws + c];
-        lhr[ph] += lh / phi[ph];
-        lphi[ph] -= lh * hr[ph] / (phi[ph] * phi[ph]);
+        lhr[ph] += lh * iphi;
+        double lq = lh * hr[ph];
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
           if (P.phase[k] != ph) continue;
           const double ly = gW[(P.wYrho + k) * ws + c];
-          lU[k] += ly / phi[ph];
-          lphi[ph] -= ly * Uc[k] / (phi[ph] * phi[ph]);
+          lU[k] += ly * iphi;
+          lq += ly * Uc[k];
         }
+        lphi[ph] -= lq * iphi * iphi;
       }
     }
     if (P.diffusion) {
@@ -1015,7 +1061,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
     for (int k = 0; k < NS; ++k) {
       if (Uc[k] == 0.0) continue;
       const int ph = P.phase[k];
-      const double r = 1.0 / (p + P.pinf[k]);
+      const double r = th.r[k];
       const double vk = P.Rk[k] * T * r + P.b[k];
       lU[k] += lphi[ph] * vk + lhr[ph] * h_k(P, k, p, T);
       lT += lphi[ph] * Uc[k] * P.Rk[k] * r + lhr[ph] * Uc[k] * P.cp[k];
@@ -1026,7 +1072,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
   thermo_rev<NS>(P, th, 0.0, 0.0, la, 0.0, 0.0, lY, lp, lT);
   // p-T equilibrium
   double le = 0.0, lv = 0.0;
-  pt_rev<NS>(P, Y, p, T, lp, lT, lY, le, lv);
+  pt_rev<NS>(P, Y, p, T, th.r, lp, lT, lY, le, lv);
   decode_rev<NS, D>(Uc, rho, Y, u, lrho, lY, lu, le, lv, lU);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
