@@ -46,6 +46,7 @@ struct mpmc_ctx {
   double* lamA = nullptr;
   double* lamB = nullptr;
   uint32_t* tape_int = nullptr;
+  float* unf = nullptr;   // mixed precision: FP32 copy of U^n
   // graph of one SSP-RK3 step for step_n
   cudaGraphExec_t gexec = nullptr;
   const double* g_U = nullptr;
@@ -137,7 +138,7 @@ static void free_all(mpmc_ctx* c) {
   // g_U and g_hist are caller-owned and never freed here
   void* ptrs[] = {c->Wc,   c->F[0],  c->F[1],    c->F[2],   c->U1,   c->U2,   c->Ud,   c->Uin,
                   c->scal, c->red,   c->status,  c->stats,  c->counter, c->gW, c->lamA, c->lamB,
-                  c->tape_int, c->Cslots, c->gU};
+                  c->tape_int, c->Cslots, c->gU, c->unf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -282,6 +283,11 @@ extern "C" int mpmc_create(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_m
     c->nface[d] = nf;
     c->nface_total += nf;
     rc = alloc(c, (void**)&c->F[d], (size_t)P.nv * nf * sizeof(double));
+  }
+  if (!rc && mixed) {
+    // FP32 copy of U^n for the mixed path's limiter (read by its face kernel)
+    rc = alloc(c, (void**)&c->unf, (size_t)P.nv * P.wstride * sizeof(float));
+    P.unf = c->unf;
   }
   rc = rc ? rc : alloc(c, (void**)&c->U1, st_bytes);
   rc = rc ? rc : alloc(c, (void**)&c->U2, st_bytes);

@@ -43,6 +43,10 @@ struct KParams {
   // holds the inflow state
   int wT, wP, wRho, wA, wY, wU, wPhi0, wPsi, wYrho, wHrho, wXr, wB, nW;
   long long wstride;
+  // mixed precision only: FP32 copy of U^n ([nv][wstride]) written by the
+  // primitive pass that computes the step's dt and Gamma; FP32 copies of
+  // U^(k) live in the FP32 cache at fields nW .. nW + nv - 1
+  float* unf;
 };
 
 // ---------------------------------------------------------------------------

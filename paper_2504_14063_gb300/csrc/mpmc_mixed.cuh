@@ -302,6 +302,13 @@ __global__ void __launch_bounds__(CELL_THREADS)
     for (int k = 0; k < NS; ++k) Wc[(P.wY + k) * ws + c] = Yf[k];
 #pragma unroll
     for (int d = 0; d < D; ++d) Wc[(P.wU + d) * ws + c] = (float)u[d];
+    // FP32 copies of U for the limiter's first (FP32) admissibility test;
+    // the pass that computes dt and Gamma (red != null) runs on U^n
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Wc[(P.nW + v) * ws + c] = (float)Uc[v];
+      if (red) P.unf[v * ws + c] = (float)Uc[v];
+    }
     float mu = 0.f;
     const float rhof = (float)rho;
     if (P.cdi || P.diffusion) {
@@ -387,7 +394,61 @@ __global__ void __launch_bounds__(CELL_THREADS)
   if (red) block_max2f(smax, gmax, red);
 }
 
-// per face: FP32 pipeline, FP64 pseudo-updates for the limiter decisions
+// Admissibility (Eqs. PositivityReqs1/2, as in admissible()) of the
+// pseudo-update T = rk0 Un + rk1 Uk + s lam F from FP32 copies.  Each test is
+// decided only when its value clears RMARGIN times the magnitudes of its
+// terms, far above FP32 rounding (~13 ulp of those magnitudes), so a
+// decision equals the exact one: returns 1 (admissible), 0 (not), -1 (too
+// close to call: the caller decides in FP64).
+constexpr float RMARGIN = 1e-4f;
+
+template <int NS, int D>
+__device__ __forceinline__ int admissible_f(const KParams& P, const float* Unf, const float* Ukf, const float* F,
+                                            float rk0, float rk1, float slam) {
+  constexpr int NV = NS + D + 1;
+  float T[NV], M[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float a = rk0 * Unf[v], b = rk1 * Ukf[v], f = slam * F[v];
+    T[v] = a + b + f;
+    M[v] = fabsf(a) + fabsf(b) + fabsf(f);
+  }
+  bool undecided = false;
+  auto test = [&](float val, float mag) {
+    if (val > RMARGIN * mag) return true;
+    if (!(val < -RMARGIN * mag)) undecided = true;
+    return false;
+  };
+  float rho = 0.f, Mrho = 0.f, sb = 0.f, Msb = 0.f, sq = 0.f, Msq = 0.f;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    rho += T[k];
+    Mrho += M[k];
+    const float b = (float)P.b[k], q = (float)P.q[k];
+    sb += T[k] * b;
+    Msb += M[k] * fabsf(b);
+    sq += T[k] * q;
+    Msq += M[k] * fabsf(q);
+  }
+  bool ok = test(rho, Mrho);
+  ok = test(1.f - sb, 1.f + Msb) && ok;
+  const float ytol = (float)YTOL;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) ok = test(T[k] + ytol * rho, M[k] + ytol * Mrho) && ok;
+  float mm = 0.f, Mmm = 0.f;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    mm += T[NS + d] * T[NS + d];
+    Mmm += M[NS + d] * M[NS + d];
+  }
+  ok = test(rho * T[NS + D] - 0.5f * mm - rho * sq, Mrho * M[NS + D] + 0.5f * Mmm + Mrho * Msq) && ok;
+  if (ok) return 1;
+  // a test decided "no" makes the state inadmissible whatever the others say
+  return undecided ? -1 : 0;
+}
+
+// per face: FP32 pipeline; the limiter's decisions from FP32 copies of the
+// states with a margin, in FP64 when a state is too close to call
 template <int NS, int D>
 __global__ void __launch_bounds__(FACE_THREADS)
     k_face(const KParams P, const int d, const float* __restrict__ Wc, const double* __restrict__ Un,
@@ -421,13 +482,14 @@ __global__ void __launch_bounds__(FACE_THREADS)
   const CRef ri = cr[2], rj = cr[3];
   uint32_t fl = 0u;
 
-  // FP64 conserved states of the two neighbours (face average, limiter)
-  double Uni[NV], Unj[NV], Uki[NV], Ukj[NV];
-  load_U<NS, D>(P, Uk, Uin, ri, Uki);
-  load_U<NS, D>(P, Uk, Uin, rj, Ukj);
-  if (P.pos_limiter) {
-    load_U<NS, D>(P, Un, Uin, ri, Uni);
-    load_U<NS, D>(P, Un, Uin, rj, Unj);
+  // FP32 copies of the two neighbours' conserved states (wall mirror applied)
+  float Uki[NV], Ukj[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float si = v >= NS && v < NS + D ? sgnf(ri.flip, v - NS) : 1.f;
+    const float sj = v >= NS && v < NS + D ? sgnf(rj.flip, v - NS) : 1.f;
+    Uki[v] = wgetf(P, Wc, P.nW + v, ri) * si;
+    Ukj[v] = wgetf(P, Wc, P.nW + v, rj) * sj;
   }
 
   // characteristic scalars at the averaged state (FP32 EOS)
@@ -435,7 +497,7 @@ __global__ void __launch_bounds__(FACE_THREADS)
   {
     float Ub[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Ub[v] = (float)(0.5 * (Uki[v] + Ukj[v]));
+    for (int v = 0; v < NV; ++v) Ub[v] = 0.5f * (Uki[v] + Ukj[v]);
     float rho = 0.f, Y[NS], ke = 0.f;
 #pragma unroll
     for (int k = 0; k < NS; ++k) rho += Ub[k];
@@ -541,15 +603,36 @@ __global__ void __launch_bounds__(FACE_THREADS)
     hllc_f<NS, D>(d, sL, sR, Fx);
   }
 
-  // positivity decisions on FP64 pseudo-updates
+  // positivity decisions on the pseudo-updates: FP32 with a margin, FP64
+  // (exact as in the FP64 path) when too close to call
   const double lam = 2.0 * D * rk2 * dt * P.inv_dx;
+  float Uni[NV], Unj[NV];
+  if (P.pos_limiter) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float si = v >= NS && v < NS + D ? sgnf(ri.flip, v - NS) : 1.f;
+      const float sj = v >= NS && v < NS + D ? sgnf(rj.flip, v - NS) : 1.f;
+      Uni[v] = P.unf[(long long)v * P.wstride + ri.idx] * si;
+      Unj[v] = P.unf[(long long)v * P.wstride + rj.idx] * sj;
+    }
+  }
   auto passes = [&](const float* Ft) {
-    double Ti_[NV], Tj_[NV];
+    const float r0 = (float)rk0, r1 = (float)rk1, lf = (float)lam;
+    const int a = admissible_f<NS, D>(P, Uni, Uki, Ft, r0, r1, -lf);
+    if (a == 0) return false;
+    const int b = admissible_f<NS, D>(P, Unj, Ukj, Ft, r0, r1, lf);
+    if (b == 0) return false;
+    if (a == 1 && b == 1) return true;
+    double Uni_[NV], Unj_[NV], Uki_[NV], Ukj_[NV], Ti_[NV], Tj_[NV];
+    load_U<NS, D>(P, Un, Uin, ri, Uni_);
+    load_U<NS, D>(P, Un, Uin, rj, Unj_);
+    load_U<NS, D>(P, Uk, Uin, ri, Uki_);
+    load_U<NS, D>(P, Uk, Uin, rj, Ukj_);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const double f = (double)Ft[v];
-      Ti_[v] = rk0 * Uni[v] + rk1 * Uki[v] - lam * f;
-      Tj_[v] = rk0 * Unj[v] + rk1 * Ukj[v] + lam * f;
+      Ti_[v] = rk0 * Uni_[v] + rk1 * Uki_[v] - lam * f;
+      Tj_[v] = rk0 * Unj_[v] + rk1 * Ukj_[v] + lam * f;
     }
     return admissible<NS, D>(P, Ti_) && admissible<NS, D>(P, Tj_);
   };
@@ -559,20 +642,20 @@ __global__ void __launch_bounds__(FACE_THREADS)
     sj.rho = wgetf(P, Wc, P.wRho, rj);
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      si.rhoY[k] = (float)Uki[k];
-      sj.rhoY[k] = (float)Ukj[k];
+      si.rhoY[k] = Uki[k];
+      sj.rhoY[k] = Ukj[k];
     }
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
       si.u[t] = t < D ? wgetf(P, Wc, P.wU + t, ri) * sgnf(ri.flip, t) : 0.f;
       sj.u[t] = t < D ? wgetf(P, Wc, P.wU + t, rj) * sgnf(rj.flip, t) : 0.f;
-      si.m[t] = t < D ? (float)Uki[NS + t] : 0.f;
-      sj.m[t] = t < D ? (float)Ukj[NS + t] : 0.f;
+      si.m[t] = t < D ? Uki[NS + t] : 0.f;
+      sj.m[t] = t < D ? Ukj[NS + t] : 0.f;
     }
     si.p = Pi;
     sj.p = Pj;
-    si.E = (float)Uki[NS + D];
-    sj.E = (float)Ukj[NS + D];
+    si.E = Uki[NS + D];
+    sj.E = Ukj[NS + D];
     si.a = wgetf(P, Wc, P.wA, ri);
     sj.a = wgetf(P, Wc, P.wA, rj);
     hllc_f<NS, D>(d, si, sj, Fx);
