@@ -16,6 +16,7 @@ built for one GPU; the whole-job value sums the replicas).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -32,6 +33,22 @@ METRIC = "cell-updates/s (FP64 vs mixed at stated L1 error); adjoint/forward tim
 UNIT = "cell-updates/s"
 FP64_PEAK_NOMINAL = 1.25e12   # GB300 FP64, nominal (no FP64 figure is measured in MEASURED_PEAKS)
 L2_BYTES = 129 * 2 ** 20
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_face launch of this
+# workload from an ncu capture (profiles/k_face_shock_bubble_2d_1024x512_fp64.md),
+# reported while the kernel's sources hash to the captured version
+K_FACE_TRAFFIC_BYTES = 125.43e6
+K_FACE_SOURCES = ("paper_2504_14063_gb300/csrc/mpmc_kernels.cuh", "paper_2504_14063_gb300/csrc/mpmc_device.cuh",
+                  "paper_2504_14063_gb300/csrc/mpmc_kernels_d2.cu")
+K_FACE_SOURCES_SHA256 = "17c10c211d2fb0a5fbe352badc430bec9adc56a07d2076cdfcad0e990d4eca43"
+
+
+def k_face_traffic():
+    h = hashlib.sha256()
+    for f in K_FACE_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return K_FACE_TRAFFIC_BYTES if h.hexdigest() == K_FACE_SOURCES_SHA256 else None
 
 
 def flops_per_face(ns, D, cdi, diffusion, pos_limiter=True):
@@ -396,7 +413,8 @@ def main():
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL / 1e12,
-                         "unit": "TFLOP/s", "frac": achieved * 1e12 / FP64_PEAK_NOMINAL, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved * 1e12 / FP64_PEAK_NOMINAL, "traffic": k_face_traffic(),
+                         "traffic_unit": "bytes per launch (ncu dram read + write)",
                          "kernel": "k_face (FP64 face flux)", "flops_per_face": fpf,
                          "faces_per_launch": faces_per_launch, "avg_launch_ms": face_ms / face_n,
                          "peak_source": "nominal GB300 FP64 rate (recipe table); FP64 pipe, not HBM, binds"},
