@@ -130,8 +130,8 @@ __device__ __forceinline__ void face_avg_fwd(const KParams& P, const double* Uk,
   load_U<NS, D>(P, Uk, Uin, rj, Uj);
 #pragma unroll
   for (int v = 0; v < NV; ++v) f.Ub[v] = 0.5 * (Ui[v] + Uj[v]);
-  decode<NS, D>(f.Ub, f.rb, f.Yb, f.ub, f.eb, f.vb);
-  pt_equilibrium<NS>(P, f.Yb, f.eb, f.vb, f.pb, f.Tb);
+  decode<NS, D, false>(f.Ub, f.rb, f.Yb, f.ub, f.eb, f.vb);
+  pt_equilibrium<NS, false>(P, f.Yb, f.eb, f.vb, f.pb, f.Tb);
 #pragma unroll
   for (int k = 0; k < NS; ++k) f.tb.Y[k] = f.Yb[k];
   f.tb.p = f.pb;

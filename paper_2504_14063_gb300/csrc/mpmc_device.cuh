@@ -153,26 +153,45 @@ __device__ __forceinline__ void pt_residual(const KParams& P, const double* Y, d
 // a stiff liquid (P << Pinf) is the small difference of terms ~ gamma Pinf,
 // so it inherits the rounding of every operation before it; evaluating in
 // a fixed order without fused multiply-adds makes it reproducible.
-__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+// EX = false: ordinary (contractible) arithmetic, for the uses that need no
+// bit-for-bit reproduction (face-average scalars, the mixed path)
+template <bool EX = true>
+__device__ __forceinline__ double mul_(double a, double b) { return EX ? __dmul_rn(a, b) : a * b; }
+template <bool EX = true>
+__device__ __forceinline__ double add_(double a, double b) { return EX ? __dadd_rn(a, b) : a + b; }
+template <bool EX = true>
+__device__ __forceinline__ double sub_(double a, double b) { return EX ? __dsub_rn(a, b) : a - b; }
 
 // mixture decode of a conserved vector: rho, Y, |u|^2, specific e, v
-template <int NS, int D>
+template <int NS, int D, bool EX = true>
 __device__ __forceinline__ void decode(const double* U, double& rho, double* Y, double* u, double& e, double& v) {
   rho = 0.0;
 #pragma unroll
-  for (int k = 0; k < NS; ++k) rho = add_(rho, U[k]);
+  for (int k = 0; k < NS; ++k) rho = add_<EX>(rho, U[k]);
+  if (EX) {
 #pragma unroll
-  for (int k = 0; k < NS; ++k) Y[k] = U[k] / rho;
-  double ke = 0.0;
+    for (int k = 0; k < NS; ++k) Y[k] = U[k] / rho;
+    double ke = 0.0;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    u[d] = d < D ? U[NS + d] / rho : 0.0;
-    ke = add_(ke, mul_(u[d], u[d]));
+    for (int d = 0; d < 3; ++d) {
+      u[d] = d < D ? U[NS + d] / rho : 0.0;
+      ke = add_(ke, mul_(u[d], u[d]));
+    }
+    e = sub_(U[NS + D] / rho, mul_(0.5, ke));
+    v = 1.0 / rho;
+  } else {
+    const double ir = 1.0 / rho;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) Y[k] = U[k] * ir;
+    double ke = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      u[d] = d < D ? U[NS + d] * ir : 0.0;
+      ke += u[d] * u[d];
+    }
+    e = U[NS + D] * ir - 0.5 * ke;
+    v = ir;
   }
-  e = sub_(U[NS + D] / rho, mul_(0.5, ke));
-  v = 1.0 / rho;
 }
 
 // p-T equilibrium from mass fractions, specific internal energy and volume
@@ -181,16 +200,16 @@ __device__ __forceinline__ void decode(const double* U, double& rho, double* Y, 
 // form, linear root without gas.  Several distinct Pinf: safeguarded Newton
 // on the common-pressure residual, started from the quadratic with a
 // Y-weighted Pinf, at most 100 iterations.
-template <int NS>
+template <int NS, bool EX = true>
 __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, double v, double& p, double& T) {
   double Cv = 0.0, q = 0.0, b = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    Cv = add_(Cv, mul_(Y[k], P.cv[k]));
-    q = add_(q, mul_(Y[k], P.q[k]));
-    b = add_(b, mul_(Y[k], P.b[k]));
+    Cv = add_<EX>(Cv, mul_<EX>(Y[k], P.cv[k]));
+    q = add_<EX>(q, mul_<EX>(Y[k], P.q[k]));
+    b = add_<EX>(b, mul_<EX>(Y[k], P.b[k]));
   }
-  const double em = sub_(e, q), vm = sub_(v, b);
+  const double em = sub_<EX>(e, q), vm = sub_<EX>(v, b);
   int st = ST_OK;
   if (!(em > 0.0) || !(vm > 0.0)) st = ST_INADMISSIBLE;
   const double Ep = em / vm;
@@ -203,25 +222,25 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
       if (P.pinf[k] > 0.0) {
         if (pl < 0.0) pl = P.pinf[k];
         else if (P.pinf[k] != pl) multi = true;
-        Rl = add_(Rl, mul_(Y[k], P.Rk[k]));
+        Rl = add_<EX>(Rl, mul_<EX>(Y[k], P.Rk[k]));
         wpl += Y[k] * P.Rk[k] * P.pinf[k];
       } else {
         gas = true;
-        Rg = add_(Rg, mul_(Y[k], P.Rk[k]));
+        Rg = add_<EX>(Rg, mul_<EX>(Y[k], P.Rk[k]));
       }
     }
   }
   if (!multi) {
     if (pl < 0.0) {
-      p = mul_(Ep, Rg) / Cv;
+      p = mul_<EX>(Ep, Rg) / Cv;
     } else if (!gas) {
-      p = sub_(sub_(mul_(Ep, Rl), mul_(pl, Cv)), mul_(pl, Rl)) / Cv;
+      p = sub_<EX>(sub_<EX>(mul_<EX>(Ep, Rl), mul_<EX>(pl, Cv)), mul_<EX>(pl, Rl)) / Cv;
     } else {
       const double a1 = Cv;
-      const double a2 = sub_(sub_(mul_(Ep, add_(Rg, Rl)), mul_(pl, Cv)), mul_(pl, Rl));
-      const double a3 = mul_(mul_(Ep, pl), Rg);
-      const double sq = sqrt(add_(mul_(a2, a2), mul_(mul_(4.0, a1), a3)));
-      p = a2 >= 0.0 ? add_(a2, sq) / mul_(2.0, a1) : mul_(2.0, a3) / sub_(sq, a2);
+      const double a2 = sub_<EX>(sub_<EX>(mul_<EX>(Ep, add_<EX>(Rg, Rl)), mul_<EX>(pl, Cv)), mul_<EX>(pl, Rl));
+      const double a3 = mul_<EX>(mul_<EX>(Ep, pl), Rg);
+      const double sq = sqrt(add_<EX>(mul_<EX>(a2, a2), mul_<EX>(mul_<EX>(4.0, a1), a3)));
+      p = a2 >= 0.0 ? add_<EX>(a2, sq) / mul_<EX>(2.0, a1) : mul_<EX>(2.0, a3) / sub_<EX>(sq, a2);
     }
   } else {
     const double lo = -pmin;
@@ -268,8 +287,13 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
   double den = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k)
-    if (Y[k] != 0.0)
-      den = add_(den, mul_(mul_(Y[k], P.cv[k]), add_(p, mul_(P.gam[k], P.pinf[k]))) / add_(p, P.pinf[k]));
+    if (Y[k] != 0.0) {
+      if (!EX && P.pinf[k] == 0.0)
+        den += Y[k] * P.cv[k];   // (P + gamma Pinf) / (P + Pinf) = 1
+      else
+        den = add_<EX>(den, mul_<EX>(mul_<EX>(Y[k], P.cv[k]), add_<EX>(p, mul_<EX>(P.gam[k], P.pinf[k]))) /
+                                add_<EX>(p, P.pinf[k]));
+    }
   T = em / den;
   return st;
 }
@@ -279,13 +303,23 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
 template <int NS>
 __device__ __forceinline__ void eos_forward(const KParams& P, const double* Y, double p, double T, double& rho,
                                             double& e, double& a, double& alpha, double& beta) {
-  double v = 0.0, cp = 0.0, sa = 0.0, sb = 0.0;
+  double v = 0.0, cp = 0.0, sa = 0.0, sb = 0.0, rg = 0.0;
+  bool have_rg = false;
   e = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     if (Y[k] != 0.0) {
-      const double pp = p + P.pinf[k];
-      const double r = 1.0 / pp;
+      // ideal-gas species share 1/(P + 0) = 1/P (the same value bit for bit)
+      double r;
+      if (P.pinf[k] == 0.0) {
+        if (!have_rg) {
+          rg = 1.0 / p;
+          have_rg = true;
+        }
+        r = rg;
+      } else {
+        r = 1.0 / (p + P.pinf[k]);
+      }
       const double RT = P.Rk[k] * T;
       v += Y[k] * (RT * r + P.b[k]);
       e += Y[k] * (P.cv[k] * T * (p + P.gam[k] * P.pinf[k]) * r + P.q[k]);

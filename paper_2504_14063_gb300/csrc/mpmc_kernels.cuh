@@ -241,11 +241,12 @@ __global__ void __launch_bounds__(FACE_THREADS)
     load_U<NS, D>(P, Uk, Uin, ri, Ui);
     load_U<NS, D>(P, Uk, Uin, rj, Uj);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Ui[v] = mul_(0.5, add_(Ui[v], Uj[v]));
+    for (int v = 0; v < NV; ++v) Ui[v] = 0.5 * (Ui[v] + Uj[v]);
+    // these scalars only shape the projection: ordinary (contracted) arithmetic
     double rho, Y[NS], uu[3], e, vol;
-    decode<NS, D>(Ui, rho, Y, uu, e, vol);
+    decode<NS, D, false>(Ui, rho, Y, uu, e, vol);
     double p, T, r2, e2, a, al, be;
-    pt_equilibrium<NS>(P, Y, e, vol, p, T);
+    pt_equilibrium<NS, false>(P, Y, e, vol, p, T);
     eos_forward<NS>(P, Y, p, T, r2, e2, a, al, be);
     X = (rho * a * a * be - 1.0) / (al * a * a * rho);
     c = a * rho;

@@ -278,13 +278,13 @@ __global__ void __launch_bounds__(CELL_THREADS)
     }
     const long long ws = P.wstride;
     double rho, Y[NS], u[3], e, vol;
-    decode<NS, D>(Uc, rho, Y, u, e, vol);
+    decode<NS, D, false>(Uc, rho, Y, u, e, vol);
     int st = rho > 0.0 ? ST_OK : ST_INADMISSIBLE;
 #pragma unroll
     for (int k = 0; k < NS; ++k)
       if (Uc[k] < -YTOL * rho) st = ST_INADMISSIBLE;
     double pd, Td;
-    const int st2 = pt_equilibrium<NS>(P, Y, e, vol, pd, Td);
+    const int st2 = pt_equilibrium<NS, false>(P, Y, e, vol, pd, Td);
     if (st == ST_OK) st = st2;
     SpeciesF sp[NS];
     load_species<NS>(P, sp);
