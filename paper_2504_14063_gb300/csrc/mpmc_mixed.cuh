@@ -127,11 +127,16 @@ __device__ __forceinline__ float weno5z_f(float v0, float v1, float v2, float v3
   // tau / (beta + eps) clamped at 1e30: with eps = 1e-30 the ratio of a
   // stencil that is flat next to a jump would overflow FP32 (in FP64 it
   // reaches 1e50 harmlessly); at 1e30 that stencil already carries all the
-  // weight, so the clamp changes the weights by 1 part in 1e30
-  const float a0 = 0.1f * (1.f + fminf(tau / (b0 + WENO_EPS32), 1e30f));
-  const float a1 = 0.6f * (1.f + fminf(tau / (b1 + WENO_EPS32), 1e30f));
-  const float a2 = 0.3f * (1.f + fminf(tau / (b2 + WENO_EPS32), 1e30f));
-  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+  // weight, so the clamp changes the weights by 1 part in 1e30.
+  // The divisions are the fast reciprocal-multiply form: every denominator
+  // stays far below 2^126 (smoothness indicators of these variables are
+  // < 1e20, the weights' sum < 1e31), an overflowing ratio is clamped, and
+  // a 2-ulp weight error moves only the deviation from the left cell, which
+  // is zero where the field is uniform.
+  const float a0 = 0.1f * (1.f + fminf(__fdividef(tau, b0 + WENO_EPS32), 1e30f));
+  const float a1 = 0.6f * (1.f + fminf(__fdividef(tau, b1 + WENO_EPS32), 1e30f));
+  const float a2 = 0.3f * (1.f + fminf(__fdividef(tau, b2 + WENO_EPS32), 1e30f));
+  return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
 }
 
 template <int NS>
