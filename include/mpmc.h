@@ -161,9 +161,12 @@ int mpmc_rhs(mpmc_ctx* ctx, const double* U, double* dUdt, const mpmc_stage* sta
 int mpmc_rk_step(mpmc_ctx* ctx, double* U, double dt, uint32_t* tape);
 
 /* n SSP-RK3 steps in place (replayed as a CUDA graph); each step takes its
- * CFL step from its own U^n on the device.  dt_dev_out (nullable, device):
- * receives n step sizes. */
-int mpmc_step_n(mpmc_ctx* ctx, double* U, int n, double* dt_dev_out);
+ * CFL step (Sec. 3.4) from its own U^n on the device.  t_end > 0: the run
+ * stops at physical time t_end — the step that would pass it is clipped to
+ * it and any later step has zero length (U unchanged), all decided on the
+ * device; t_end <= 0: no end time.  dt_dev_out (nullable, device): receives
+ * the n step sizes (their sum is the time advanced). */
+int mpmc_step_n(mpmc_ctx* ctx, double* U, int n, double t_end, double* dt_dev_out);
 
 /* Host-buffer entry: copies U_host (nv x ncells FP64, pinned or pageable)
  * to the device, runs n steps, copies the state back; synchronizes.  The

@@ -9,6 +9,8 @@ pass are replayed and each step's dt and Gamma are frozen (Sec. 3.3, 3.4).
   init_state(ctx, prim)             U = conserved state of primitive fields
   rk_step(ctx, U, dt=0.0)           one SSP-RK3 step (out of place)
   primitives(ctx, U)                [T, P, rho, a, Y_k, u_d] per cell
+  RKStep.apply(ctx, U, dt)          the same step as an autograd Function
+  step_n_checkpointed(ctx, U0, n, every=20)   U_n of a checkpointed rollout
   rollout(ctx, U0, n, every=20, probe=None)
         n steps with a checkpoint every `every` steps; returns (U_n, J, dts)
         with J = sum_{k=1..n} dt_k sum_c probe_c P_c(U^k) (zero without a
@@ -140,3 +142,13 @@ def rollout(ctx, U0, n, every=20, probe=None):
     if ctx.precision != _b.FP64:
         raise ValueError("the discrete adjoint needs an FP64 context")
     return _Rollout.apply(ctx, U0, int(n), int(every), probe)
+
+
+# the autograd Function of one step, for callers that chain steps themselves
+RKStep = _RKStep
+
+
+def step_n_checkpointed(ctx, U0, n, every=20):
+    """n CFL steps from U0 with a checkpoint every `every` steps; returns U_n
+    (differentiable with respect to U0)."""
+    return rollout(ctx, U0, n, every)[0]

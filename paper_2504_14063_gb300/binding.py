@@ -71,7 +71,7 @@ def _load():
         "mpmc_init_state": (i, [vp, vp, vp]),
         "mpmc_rhs": (i, [vp, vp, vp, ctypes.POINTER(StageC), vp]),
         "mpmc_rk_step": (i, [vp, vp, d, vp]),
-        "mpmc_step_n": (i, [vp, vp, i, vp]),
+        "mpmc_step_n": (i, [vp, vp, i, d, vp]),
         "mpmc_step_n_host": (i, [vp, vp, i]),
         "mpmc_dt_gamma": (i, [vp, vp, vp]),
         "mpmc_rhs_adjoint": (i, [vp, vp, ctypes.POINTER(StageC), vp, vp, vp]),
@@ -207,8 +207,11 @@ class Context:
         self._check(lib.mpmc_rk_step(self.h, _dev(U), float(dt), _ptr(tape)))
         return U
 
-    def step_n(self, U, n, dt_out=None):
-        self._check(lib.mpmc_step_n(self.h, _dev(U), int(n), _ptr(dt_out)))
+    def step_n(self, U, n, dt_out=None, t_end=0.0):
+        """n SSP-RK3 steps in place; t_end > 0 stops at that physical time
+        (later steps have zero length); dt_out (n doubles, device) receives
+        the step sizes."""
+        self._check(lib.mpmc_step_n(self.h, _dev(U), int(n), float(t_end), _ptr(dt_out)))
         return U
 
     def step_n_host(self, U_host, n):
@@ -321,8 +324,8 @@ def rk_step(ctx, U, dt=0.0, tape=None):
     return ctx.rk_step(U, dt, tape)
 
 
-def step_n(ctx, U, n, dt_out=None):
-    return ctx.step_n(U, n, dt_out)
+def step_n(ctx, U, n, dt_out=None, t_end=0.0):
+    return ctx.step_n(U, n, dt_out, t_end)
 
 
 def rhs_adjoint(ctx, U, stage, tape, lam_dUdt, lam_U=None):

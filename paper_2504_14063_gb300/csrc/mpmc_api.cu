@@ -105,8 +105,12 @@ __global__ void k_dt(const KParams P, unsigned long long* red, double* scal, dou
                      double* dt_hist, int* counter) {
   const double smax = __longlong_as_double((long long)red[0]);
   const double gmax = __longlong_as_double((long long)red[1]);
-  const double dt = dt_fixed > 0.0 ? dt_fixed : P.cfl / smax;
+  double dt = dt_fixed > 0.0 ? dt_fixed : P.cfl / smax;
   const double G = gamma_fixed >= 0.0 ? gamma_fixed : (P.cdi_gamma > 0.0 ? P.cdi_gamma : gmax);
+  // scal[2]: elapsed time of the run; scal[3] > 0: its end time, the last
+  // step clipped to it and any later step of zero length
+  if (scal[3] > 0.0) dt = fmin(dt, fmax(scal[3] - scal[2], 0.0));
+  scal[2] += dt;
   scal[0] = dt;
   scal[1] = G;
   red[0] = 0ull;
@@ -419,10 +423,16 @@ extern "C" int mpmc_rk_step(mpmc_ctx* c, double* U, double dt, uint32_t* tape) {
   return check_launch(c, "rk_step");
 }
 
-extern "C" int mpmc_step_n(mpmc_ctx* c, double* U, int n, double* dt_out) {
+extern "C" int mpmc_step_n(mpmc_ctx* c, double* U, int n, double t_end, double* dt_out) {
   if (!c || !U || n < 0) return fail(c, MPMC_INVALID_ARG, "step_n: bad argument");
   if (n == 0) return MPMC_OK;
   cudaStream_t s = c->stream;
+  {
+    // run clock and end time (scal[2], scal[3]) for the steps of this call
+    const double tt[2] = {0.0, t_end > 0.0 ? t_end : 0.0};
+    if (cudaMemcpyAsync(c->scal + 2, tt, sizeof(tt), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return fail(c, MPMC_CUDA_ERROR, "step_n: set end time");
+  }
   if (!c->gexec || c->g_U != U || c->g_hist != dt_out) {
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);
@@ -453,6 +463,12 @@ extern "C" int mpmc_step_n(mpmc_ctx* c, double* U, int n, double* dt_out) {
     if (e != cudaSuccess) return fail(c, MPMC_CUDA_ERROR, "step_n: graph launch: %s", cudaGetErrorString(e));
   }
   c->faces_done += 3ull * c->nface_total * (unsigned long long)n;
+  {
+    // later single steps are not clipped
+    const double tt[2] = {0.0, 0.0};
+    if (cudaMemcpyAsync(c->scal + 2, tt, sizeof(tt), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return fail(c, MPMC_CUDA_ERROR, "step_n: reset end time");
+  }
   return check_launch(c, "step_n");
 }
 
@@ -466,7 +482,7 @@ extern "C" int mpmc_step_n_host(mpmc_ctx* c, double* U_host, int n) {
   cudaStream_t s = c->stream;
   if (cudaMemcpyAsync(c->Ud, U_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return fail(c, MPMC_CUDA_ERROR, "step_n_host: copy in");
-  int rc = mpmc_step_n(c, c->Ud, n, nullptr);
+  int rc = mpmc_step_n(c, c->Ud, n, 0.0, nullptr);
   if (rc) return rc;
   if (cudaMemcpyAsync(U_host, c->Ud, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return fail(c, MPMC_CUDA_ERROR, "step_n_host: copy out");

@@ -531,7 +531,9 @@ __global__ void __launch_bounds__(CELL_THREADS)
 #pragma unroll
     for (int d = 0; d < D; ++d) L -= (Fd[d][(long long)v * nf[d] + fp[d]] - Fd[d][(long long)v * nf[d] + fm[d]]) * P.inv_dx;
     if (dUdt) dUdt[(long long)v * P.ncell + c] = L;
-    Uo[v] = rk0 * Un[(long long)v * P.ncell + c] + rk1 * Uk[(long long)v * P.ncell + c] + (rk2 * dt) * L;
+    // a zero-length step (a run past its end time) leaves the state as it is
+    Uo[v] = dt == 0.0 ? Uk[(long long)v * P.ncell + c]
+                      : rk0 * Un[(long long)v * P.ncell + c] + rk1 * Uk[(long long)v * P.ncell + c] + (rk2 * dt) * L;
   }
   if (Uout) {
 #pragma unroll

@@ -819,7 +819,9 @@ __global__ void __launch_bounds__(CELL_THREADS)
       L -= (double)Fd[d][(long long)v * nf[d] + fp[d]] - (double)Fd[d][(long long)v * nf[d] + fm[d]];
     L *= P.inv_dx;
     if (dUdt) dUdt[(long long)v * P.ncell + c] = L;
-    Uo[v] = rk0 * Un[(long long)v * P.ncell + c] + rk1 * Uk[(long long)v * P.ncell + c] + s * L;
+    // a zero-length step (a run past its end time) leaves the state as it is
+    Uo[v] = s == 0.0 ? Uk[(long long)v * P.ncell + c]
+                     : rk0 * Un[(long long)v * P.ncell + c] + rk1 * Uk[(long long)v * P.ncell + c] + s * L;
   }
   if (Uout) {
 #pragma unroll

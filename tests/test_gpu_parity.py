@@ -346,3 +346,46 @@ def test_full_size_shock_bubble_step(mp):
     err = scaled_l1(Ug.cpu().numpy(), Uo, p.ns, p.dim)
     print(f"full-size shock_bubble_2d one step: scaled L1 err {np.array2string(err, precision=2)}")
     assert err.max() <= L1_TOL, err
+
+
+def test_paper_droplet_advection_golden_on_gpu(mp):
+    """Table DropAdvectionIECResults (WENO5Z row): the FP64 GPU path run to
+    one flow-through time, the end time enforced on the device (t_end of
+    mpmc_step_n), keeps P, T and u uniform within a small factor of the
+    paper's printed maximum errors; steps requested beyond t_end have zero
+    length and leave the state unchanged."""
+    import json
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                    "drop_advection_iec.json")))
+    p = W.paper_droplet_advection(n=100, cdi=1)
+    ctx = mp.Context(p)
+    U = ctx.init_state(torch.from_numpy(p.prim))
+    nmax = 120000
+    hist = torch.zeros(nmax, dtype=torch.float64, device="cuda")
+    ctx.step_n(U, nmax, dt_out=hist, t_end=p.t_end)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    h = hist.cpu().numpy()
+    nsteps = int((h > 0).sum())
+    assert nsteps < nmax and np.all(h[nsteps:] == 0.0)
+    assert h.sum() == pytest.approx(p.t_end, rel=1e-12)
+    o = Oracle(p)
+    Uh = U.cpu().numpy()
+    pr = o.primitives(Uh)
+    u = Uh[p.ns] / Uh[:p.ns].sum(0)
+    errs = {"P": np.abs(pr["P"] / 101325.0 - 1).max(), "T": np.abs(pr["T"] / 297.0 - 1).max(),
+            "u": np.abs(u / 5.0 - 1).max()}
+    ref = g["max_rel_err"]
+    print(f"GPU droplet advection, {nsteps} steps to t_end: P {errs['P']:.2e} (paper {ref['P']:.2e}) "
+          f"T {errs['T']:.2e} (paper {ref['T']:.2e}) u {errs['u']:.2e} (paper {ref['u']:.2e})")
+    for k in ("P", "T", "u"):
+        assert errs[k] <= 5 * ref[k]
+    # a run whose end time is reached by its first step: the first step is
+    # clipped to it, the others have zero length and change nothing
+    W1, W2 = U.clone(), U.clone()
+    hist2 = torch.zeros(4, dtype=torch.float64, device="cuda")
+    tend = 0.5 * float(h[0])
+    ctx.step_n(W2, 4, dt_out=hist2, t_end=tend)
+    ctx.rk_step(W1, tend)
+    assert float(hist2[0]) == tend and float(hist2[1:].abs().sum()) == 0.0
+    assert torch.equal(W1, W2)
