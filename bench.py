@@ -148,9 +148,16 @@ def cpu_baseline(p, seconds=12.0):
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
+    # one thread: one step of the same workload
+    o1 = Oracle(p, nthreads=1)
+    t1 = time.perf_counter()
+    o1.rk_step(o1.init_state())
+    el1 = time.perf_counter() - t1
     return {"value": p.ncells * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} SSP-RK3 steps of the full {p.n[0]}x{p.n[1]} workload from its initial state "
-                      f"({el:.1f} s, OpenMP threads = {cores})"}
+                      f"({el:.1f} s, OpenMP threads = {cores})",
+            "single_thread": {"value": p.ncells / el1, "unit": UNIT, "cores": 1,
+                              "sample": f"1 SSP-RK3 step of the same workload ({el1:.1f} s)"}}
 
 
 def run_reference(args, rank, world):
@@ -198,11 +205,14 @@ def adjoint_section(mp, torch, nsteps=200, every=20, n=512):
     rest = torch.from_numpy(p.prim[2:]).cuda()
     amps0 = torch.from_numpy(W.seeded_fourier_amplitudes(3, 8, 1.0)).cuda()
 
+    # fixed step: the CFL step of the initial state
+    dt_ic = float(ctx.dt_gamma(ctx.init_state(torch.from_numpy(p.prim)))[0])
+
     def forward(amps, steps):
         a0, a1 = W.interface_fractions(n, amps, phi_l, xp=torch)
         prim = torch.cat([a0[None, None], a1[None, None], rest], 0)
         U0 = ag.init_state(ctx, prim)
-        return ag.rollout(ctx, U0, steps, every=every, probe=probe)
+        return ag.rollout(ctx, U0, steps, every=every, probe=probe, dt=dt_ic)
 
     # warm-up (graph capture, adjoint scratch)
     a = amps0.clone().requires_grad_(True)
@@ -251,7 +261,8 @@ def adjoint_section(mp, torch, nsteps=200, every=20, n=512):
     prof = ctx.profile(reset=True)
     fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
     state_mb = ctx.nv * ctx.ncells * 8 / 2 ** 20
-    return {"workload": f"shock_interface_2d {n}x{n}, {nsteps} SSP-RK3 steps, checkpoint every {every} steps",
+    return {"workload": f"shock_interface_2d {n}x{n}, {nsteps} SSP-RK3 steps of fixed length (the initial CFL "
+                        f"step, {dt_ic:.4e} s), checkpoint every {every} steps",
             "functional": f"sum_k dt_k mean_y P(x={col}, y, t_k); gradient w.r.t. 16 interface Fourier amplitudes",
             "forward_ms": fwd_ms, "backward_ms": bwd_ms, "ratio": bwd_ms / fwd_ms,
             "dense_step": {"forward_ms": dense_f, "adjoint_ms": dense_a, "ratio": dense_a / dense_f,
@@ -411,6 +422,7 @@ def main():
             "clocks": clk,
             "e2e": {"value": world * p.ncells * args.steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "rhs_cell_evaluations_per_s": 3 * value,
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL / 1e12,
                          "unit": "TFLOP/s", "frac": achieved * 1e12 / FP64_PEAK_NOMINAL, "traffic": k_face_traffic(),

@@ -11,8 +11,9 @@ pass are replayed and each step's dt and Gamma are frozen (Sec. 3.3, 3.4).
   primitives(ctx, U)                [T, P, rho, a, Y_k, u_d] per cell
   RKStep.apply(ctx, U, dt)          the same step as an autograd Function
   step_n_checkpointed(ctx, U0, n, every=20)   U_n of a checkpointed rollout
-  rollout(ctx, U0, n, every=20, probe=None)
-        n steps with a checkpoint every `every` steps; returns (U_n, J, dts)
+  rollout(ctx, U0, n, every=20, probe=None, dt=0.0)
+        n steps (of fixed length dt > 0, or each the CFL step of its own
+        state) with a checkpoint every `every` steps; returns (U_n, J, dts)
         with J = sum_{k=1..n} dt_k sum_c probe_c P_c(U^k) (zero without a
         probe).  The backward pass replays each segment from its checkpoint
         (one forward step per step, keeping each step's input, stage states
@@ -76,7 +77,7 @@ def _probe_term(ctx, U, probe):
 
 class _Rollout(torch.autograd.Function):
     @staticmethod
-    def forward(fctx, ctx, U0, n, every, probe):
+    def forward(fctx, ctx, U0, n, every, probe, dt):
         U = U0.detach().contiguous().clone()
         ckpts = []
         dts = torch.empty(n, dtype=torch.float64, device=U.device)
@@ -85,8 +86,12 @@ class _Rollout(torch.autograd.Function):
         for k in range(n):
             if k % every == 0:
                 ckpts.append(U.clone())
-            ctx.step_n(U, 1, slot)          # CFL step of U^k, recorded
-            dts[k] = slot[0]
+            if dt > 0.0:
+                ctx.rk_step(U, dt)              # fixed step
+                dts[k] = dt
+            else:
+                ctx.step_n(U, 1, slot)          # CFL step of U^k, recorded
+                dts[k] = slot[0]
             if probe is not None:
                 J += dts[k] * _probe_term(ctx, U, probe)
         fctx.ctx, fctx.n, fctx.every, fctx.probe = ctx, n, every, probe
@@ -123,7 +128,7 @@ class _Rollout(torch.autograd.Function):
                     lamW[1] = (gJ * dt_host[k]) * probe
                     ctx.primitives_adjoint(states[q + 1], lamW, lam)
                 ctx.rk_step_adjoint(states[q], lam, dt=dt_host[k], tape=tapes[q], lam_n=lam, stages=stages[q])
-        return None, lam, None, None, None
+        return None, lam, None, None, None, None
 
 
 def init_state(ctx, prim):
@@ -138,10 +143,12 @@ def primitives(ctx, U):
     return _Primitives.apply(ctx, U)
 
 
-def rollout(ctx, U0, n, every=20, probe=None):
+def rollout(ctx, U0, n, every=20, probe=None, dt=0.0):
+    """dt > 0: every step has that length; otherwise each step takes the CFL
+    step of its own U^k (recorded, and frozen in the backward pass)."""
     if ctx.precision != _b.FP64:
         raise ValueError("the discrete adjoint needs an FP64 context")
-    return _Rollout.apply(ctx, U0, int(n), int(every), probe)
+    return _Rollout.apply(ctx, U0, int(n), int(every), probe, float(dt))
 
 
 # the autograd Function of one step, for callers that chain steps themselves
