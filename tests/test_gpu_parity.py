@@ -389,3 +389,45 @@ def test_paper_droplet_advection_golden_on_gpu(mp):
     ctx.rk_step(W1, tend)
     assert float(hist2[0]) == tend and float(hist2[1:].abs().sum()) == 0.0
     assert torch.equal(W1, W2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("fault", ["negative_partial_density", "internal_energy_at_q", "nan_energy"])
+def test_host_injected_faults_set_status(mp, precision, fault):
+    """Faults made on the host (Eqs. PositivityReqs1/2 violated, a NaN) are
+    reported as MPMC_INADMISSIBLE through the status word, with no device
+    trap; the context stays usable."""
+    p = W.shock_bubble_2d(nx=32, ny=16, seed=0)
+    ctx = mp.Context(p, precision=mp.FP64 if precision == "fp64" else mp.MIXED)
+    U = ctx.init_state(torch.from_numpy(p.prim))
+    V = U.clone()
+    ns, D = p.ns, p.dim
+    if fault == "negative_partial_density":
+        V[0, 0, 5, 5] = -1.0
+    elif fault == "internal_energy_at_q":
+        # every species has q = 0: E = kinetic energy leaves e - q = 0
+        rho = V[:ns, 0, 5, 5].sum()
+        V[ns + D, 0, 5, 5] = 0.5 * (V[ns:ns + D, 0, 5, 5] ** 2).sum() / rho
+    else:
+        V[ns + D, 0, 5, 5] = float("nan")
+    ctx.rk_step(V)
+    assert ctx.status(reset=True) == mp.INADMISSIBLE
+    ctx.rk_step(U)
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_forward_steps_are_bitwise_reproducible(mp, precision):
+    """No floating-point atomics in the forward path: the same steps from
+    the same state give bit-identical states (graph replay and single
+    steps alike)."""
+    p = W.shock_bubble_2d(nx=96, ny=48, seed=3)
+    ctx = mp.Context(p, precision=mp.FP64 if precision == "fp64" else mp.MIXED)
+    U = ctx.init_state(torch.from_numpy(p.prim))
+    ctx.step_n(U, 20)
+    A, B, C = U.clone(), U.clone(), U.clone()
+    ctx.step_n(A, 5)
+    ctx.step_n(B, 5)
+    for _ in range(5):
+        ctx.rk_step(C)
+    assert torch.equal(A, B) and torch.equal(A, C)
