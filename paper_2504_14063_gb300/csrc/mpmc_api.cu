@@ -212,6 +212,8 @@ extern "C" int mpmc_create(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_m
     P.mu[k] = eos->mu[k];
     P.Sc[k] = eos->Sc[k];
     P.Rk[k] = (eos->gamma[k] - 1.0) * eos->cv[k];
+    if (eos->b[k] != 0.0) P.has_b = 1;
+    if (eos->q[k] != 0.0) P.has_q = 1;
     P.cp[k] = eos->gamma[k] * eos->cv[k];
   }
   for (int i = 0; i < ns; ++i)

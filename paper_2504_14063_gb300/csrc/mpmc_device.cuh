@@ -38,6 +38,7 @@ struct KParams {
   double wilke[MAXS][MAXS];  // (W_i / W_j) Phi_ij of Wilke's rule (gas species)
   double weno_eps;
   int cdi, diffusion, pos_limiter, two_phase, has_inflow;
+  int has_b, has_q;  // some species has a nonzero NASG covolume b / reference energy q
   double cdi_eps, cdi_gamma, phi_min, psi_delta, cfl, mu_liquid, sharp0;
   // primitive cache: field f of cell c at Wc[f * wstride + c]; slot ncell
   // holds the inflow state
@@ -334,6 +335,37 @@ __device__ __forceinline__ void eos_forward(const KParams& P, const double* Y, d
   a = sqrt(cp / (rho * beta * cp - alpha * alpha * T));
 }
 
+// the sound speed, alpha and beta of eos_forward at a state whose density
+// rho is already known (the face average: its (P, T) come from inverting
+// that density, so v(P, T, Y) = 1/rho up to rounding)
+template <int NS>
+__device__ __forceinline__ void eos_char(const KParams& P, const double* Y, double p, double T, double rho,
+                                         double& a, double& alpha, double& beta) {
+  double cp = 0.0, sa = 0.0, sb = 0.0, rg = 0.0;
+  bool have_rg = false;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    if (Y[k] != 0.0) {
+      double r;
+      if (P.pinf[k] == 0.0) {
+        if (!have_rg) {
+          rg = 1.0 / p;
+          have_rg = true;
+        }
+        r = rg;
+      } else {
+        r = 1.0 / (p + P.pinf[k]);
+      }
+      cp += Y[k] * P.cp[k];
+      sa += Y[k] * P.Rk[k] * r;
+      sb += Y[k] * P.Rk[k] * T * r * r;
+    }
+  }
+  alpha = rho * sa;
+  beta = rho * sb;
+  a = sqrt(cp / (rho * beta * cp - alpha * alpha * T));
+}
+
 // ---------------------------------------------------------------------------
 // WENO5-Z (Borges et al. 2008), exponent 1: value at the right face of v2
 __device__ __forceinline__ double weno5z(double v0, double v1, double v2, double v3, double v4, double eps) {
@@ -425,8 +457,8 @@ __device__ __forceinline__ bool admissible(const KParams& P, const double* U) {
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     rho += U[k];
-    sb += U[k] * P.b[k];
-    sq += U[k] * P.q[k];
+    if (P.has_b) sb += U[k] * P.b[k];
+    if (P.has_q) sq += U[k] * P.q[k];
   }
   bool ok = rho > 0.0 && (1.0 - sb) > 0.0;
 #pragma unroll

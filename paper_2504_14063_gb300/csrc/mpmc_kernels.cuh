@@ -245,9 +245,9 @@ __global__ void __launch_bounds__(FACE_THREADS)
     // these scalars only shape the projection: ordinary (contracted) arithmetic
     double rho, Y[NS], uu[3], e, vol;
     decode<NS, D, false>(Ui, rho, Y, uu, e, vol);
-    double p, T, r2, e2, a, al, be;
+    double p, T, a, al, be;
     pt_equilibrium<NS, false>(P, Y, e, vol, p, T);
-    eos_forward<NS>(P, Y, p, T, r2, e2, a, al, be);
+    eos_char<NS>(P, Y, p, T, rho, a, al, be);
     X = (rho * a * a * be - 1.0) / (al * a * a * rho);
     c = a * rho;
     ic = 1.0 / c;
