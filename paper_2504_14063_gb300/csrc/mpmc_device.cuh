@@ -128,11 +128,13 @@ __device__ __forceinline__ double h_k(const KParams& P, int k, double p, double 
 }
 
 // common-pressure residual of NASG_T1 = NASG_T2 and its derivative
+// (mag: the sum of the magnitudes of its terms, the scale of its rounding)
 template <int NS>
 __device__ __forceinline__ void pt_residual(const KParams& P, const double* Y, double Ep, double Cv, double x,
-                                            double& f, double& df) {
+                                            double& f, double& df, double& mag) {
   f = -Cv;
   df = 0.0;
+  mag = Cv;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     if (Y[k] != 0.0) {
@@ -140,6 +142,7 @@ __device__ __forceinline__ void pt_residual(const KParams& P, const double* Y, d
       const double r = 1.0 / (x + P.pinf[k]);
       f += w * r;
       df -= w * r * r;
+      mag += fabs(w * r);
     }
   }
 }
@@ -246,12 +249,12 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
   } else {
     const double lo = -pmin;
     double hi = fmax(fabs(Ep), 1.0) + fabs(lo);
-    double f, df;
+    double f, df, mag;
     int it = 0;
-    pt_residual<NS>(P, Y, Ep, Cv, hi, f, df);
+    pt_residual<NS>(P, Y, Ep, Cv, hi, f, df, mag);
     while (f >= 0.0 && it < 200) {
       hi *= 2.0;
-      pt_residual<NS>(P, Y, Ep, Cv, hi, f, df);
+      pt_residual<NS>(P, Y, Ep, Cv, hi, f, df, mag);
       ++it;
     }
     double a = lo, bb = hi;
@@ -264,10 +267,13 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
     if (!(x > a && x < bb)) x = 0.5 * (a + bb);
     bool conv = false;
     for (it = 0; it < 100; ++it) {
-      pt_residual<NS>(P, Y, Ep, Cv, x, f, df);
+      pt_residual<NS>(P, Y, Ep, Cv, x, f, df, mag);
       if (f > 0.0) a = x;
       else bb = x;
-      if (f == 0.0) { conv = true; break; }
+      // the residual is a difference of terms of size mag: once it is at its
+      // own rounding level, x is the root as far as the data determine it
+      // (a stiff liquid with trace gas: Newton would wander in that band)
+      if (fabs(f) <= 16.0 * 2.220446049250313e-16 * mag) { conv = true; break; }
       double xn = x - f / df;
       if (!(xn > a && xn < bb)) {
         const double da = a - lo, db = bb - lo;
@@ -276,7 +282,7 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
       const double dxn = fabs(xn - x);
       x = xn;
       if (dxn <= 4.5e-16 * fabs(x) || !(bb > a)) {
-        pt_residual<NS>(P, Y, Ep, Cv, x, f, df);
+        pt_residual<NS>(P, Y, Ep, Cv, x, f, df, mag);
         x = x - f / df;   // one more Newton step at full accuracy
         conv = true;
         break;

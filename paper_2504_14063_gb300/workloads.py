@@ -408,23 +408,36 @@ def shock_droplet_3d(n=512, seed=4, mach=2.0, nsteps=200, cdi=1, diffusion=1, ph
     s = n / 512.0
     dx = 1e-5 * (512.0 / n)
     g = np.arange(n) + 0.5
-    Z, Yg, X = np.meshgrid(g, g, g, indexing="ij")
+    X, Yg, Z = g[None, None, :], g[None, :, None], g[:, None, None]   # broadcast [z, y, x]
     c = np.array([160.0, 256.0, 256.0]) * s
-    rel = np.stack([X - c[0], Yg - c[1], Z - c[2]])
-    r = np.sqrt((rel ** 2).sum(axis=0)) + 1e-30
-    nrm = rel / r
+    r = np.sqrt((X - c[0]) ** 2 + (Yg - c[1]) ** 2 + (Z - c[2]) ** 2) + 1e-30
     # all monomials of the direction cosines up to degree 4 span Y_lm, l <= 4
     mons = [(a, b, cc) for a in range(5) for b in range(5) for cc in range(5) if 0 < a + b + cc <= 4]
     coef = rng.standard_normal(len(mons))
-    pert = sum(cf * nrm[0] ** a * nrm[1] ** b * nrm[2] ** cc for cf, (a, b, cc) in zip(coef, mons))
-    pert = pert / np.abs(pert).max()
-    phi_l = floored(tanh_profile(48.0 * s + pert - r, 1.0), phase_floor)
+    R0 = 48.0 * s
+    # the perturbation (peak one cell) matters only near the surface: beyond
+    # 21 cells the floored profile is phase_floor or 1 - phase_floor whatever
+    # its value.  Its normalization uses the unit sphere of directions, which
+    # the shell covers.
+    shell = np.abs(r - R0) < 21.0
+    idx = np.nonzero(shell)
+    rs = r[idx]
+    nx_ = (X[0, 0, idx[2]] - c[0]) / rs
+    ny_ = (Yg[0, idx[1], 0] - c[1]) / rs
+    nz_ = (Z[idx[0], 0, 0] - c[2]) / rs
+    pert_s = sum(cf * nx_ ** a * ny_ ** b * nz_ ** cc for cf, (a, b, cc) in zip(coef, mons))
+    pert_s = pert_s / np.abs(pert_s).max()
+    d = R0 - r
+    d[idx] += pert_s
+    phi_l = floored(tanh_profile(d, 1.0), phase_floor)
+    del d, r
     cg = np.array([320.0, 256.0, 256.0]) * s
     rg = np.sqrt((X - cg[0]) ** 2 + (Yg - cg[1]) ** 2 + (Z - cg[2]) ** 2)
     he = 0.5 * tanh_profile(32.0 * s - rg, 1.0)
+    del rg
     P1, T1 = 1e5, 300.0
     P2, T2, u2 = normal_shock(mach, AIR.gamma, AIR.W, P1, T1)
-    post = X < 64.0 * s
+    post = np.broadcast_to(X < 64.0 * s, (n, n, n))
     pr = _prim(3, 3, (n, n, n))
     pr[0] = (1.0 - phi_l) * (1.0 - he)
     pr[1] = (1.0 - phi_l) * he
