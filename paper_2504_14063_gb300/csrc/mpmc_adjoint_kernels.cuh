@@ -164,12 +164,15 @@ __device__ __forceinline__ void face_avg_rev(const KParams& P, const FaceAvg<NS,
   decode_rev<NS, D>(f.Ub, f.rb, f.Yb, f.ub, lrho, lYb, lub, leb, lvb, lUb);
 }
 
-template <int NS, int D>
+// DIR: the face direction, a template parameter so that every array indexed
+// by it is indexed by a constant
+template <int NS, int D, int DIR>
 __global__ void __launch_bounds__(VJP_THREADS)
-    k_face_adj(const KParams P, const int d, const double* __restrict__ Wc, const double* __restrict__ Uk,
+    k_face_adj(const KParams P, const double* __restrict__ Wc, const double* __restrict__ Uk,
                const double* __restrict__ Uin, const double* __restrict__ scal, const uint32_t* __restrict__ tape,
                const double* __restrict__ lamL, const double coef, const int mul_dt, double* __restrict__ C) {
   constexpr int NV = NS + D + 1;
+  constexpr int d = DIR;
   const int f0 = P.n[0] + (d == 0), f1 = P.n[1] + (d == 1), f2 = P.n[2] + (d == 2);
   const long long nf = (long long)f0 * f1 * f2;
   const long long fid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -384,8 +387,13 @@ __global__ void __launch_bounds__(VJP_THREADS)
       double ypi[2] = {0.0, 0.0}, ypj[2] = {0.0, 0.0};
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        ypi[P.phase[k]] += Yi[k];
-        ypj[P.phase[k]] += Yj[k];
+        if (P.phase[k]) {
+          ypi[1] += Yi[k];
+          ypj[1] += Yj[k];
+        } else {
+          ypi[0] += Yi[k];
+          ypj[0] += Yj[k];
+        }
       }
 #pragma unroll
       for (int ph = 0; ph < 2; ++ph) {
@@ -423,7 +431,7 @@ __global__ void __launch_bounds__(VJP_THREADS)
       double Rtot = 0.0, kb = 0.0;
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        const bool pi = pres_i[P.phase[k]], pj = pres_j[P.phase[k]];
+        const bool pi = P.phase[k] ? pres_i[1] : pres_i[0], pj = P.phase[k] ? pres_j[1] : pres_j[0];
         const double yi = wget(P, Wc, P.wYrho + k, ri), yj = wget(P, Wc, P.wYrho + k, rj);
         const double kp = pi && pj ? 0.5 * (yi + yj) : (pi ? yi : (pj ? yj : 0.0));
         Rtot += -kp * (P.phase[k] == 0 ? ahat0 : -ahat0);
@@ -763,11 +771,12 @@ __device__ __forceinline__ Pre preimages(int c, int n, int lo, int hi) {
 // Per cell: sums, in a fixed order, the contributions of the faces of
 // direction d whose stencils reach the cell; first != 0 writes, otherwise
 // adds.  gW: cache adjoint [nW][wstride]; gU: U adjoint [NV][ncell].
-template <int NS, int D>
+template <int NS, int D, int DIR>
 __global__ void __launch_bounds__(CELL_THREADS)
-    k_gather(const KParams P, const int d, const double* __restrict__ C, const int first, double* __restrict__ gW,
+    k_gather(const KParams P, const double* __restrict__ C, const int first, double* __restrict__ gW,
              double* __restrict__ gU) {
   constexpr int NV = NS + D + 1;
+  constexpr int d = DIR;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= P.ncell) return;
   const Lay<NS, D> L(P.cdi, P.diffusion);
@@ -1148,11 +1157,22 @@ struct AdjImpl {
                    double* C) {
     long long nf = 1;
     for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
-    k_face_adj<NS, D><<<nblocks(nf, VJP_THREADS), VJP_THREADS, 0, s>>>(P, d, Wc, Uk, Uin, scal, tape, lamL, coef,
-                                                                         mul_dt, C);
+    const unsigned nb = nblocks(nf, VJP_THREADS);
+    if (d == 0)
+      k_face_adj<NS, D, 0><<<nb, VJP_THREADS, 0, s>>>(P, Wc, Uk, Uin, scal, tape, lamL, coef, mul_dt, C);
+    else if (d == 1)
+      k_face_adj<NS, D, (D > 1 ? 1 : 0)><<<nb, VJP_THREADS, 0, s>>>(P, Wc, Uk, Uin, scal, tape, lamL, coef, mul_dt, C);
+    else
+      k_face_adj<NS, D, (D > 2 ? 2 : 0)><<<nb, VJP_THREADS, 0, s>>>(P, Wc, Uk, Uin, scal, tape, lamL, coef, mul_dt, C);
   }
   static void gather(const KParams& P, cudaStream_t s, int d, const double* C, int first, double* gW, double* gU) {
-    k_gather<NS, D><<<nblocks(P.ncell, CELL_THREADS), CELL_THREADS, 0, s>>>(P, d, C, first, gW, gU);
+    const unsigned nb = nblocks(P.ncell, CELL_THREADS);
+    if (d == 0)
+      k_gather<NS, D, 0><<<nb, CELL_THREADS, 0, s>>>(P, C, first, gW, gU);
+    else if (d == 1)
+      k_gather<NS, D, (D > 1 ? 1 : 0)><<<nb, CELL_THREADS, 0, s>>>(P, C, first, gW, gU);
+    else
+      k_gather<NS, D, (D > 2 ? 2 : 0)><<<nb, CELL_THREADS, 0, s>>>(P, C, first, gW, gU);
   }
   static void cell(const KParams& P, cudaStream_t s, const double* U, const double* gW, const double* gU,
                    double* out, double a, const double* x, double b, const double* y, double cz, const double* z) {

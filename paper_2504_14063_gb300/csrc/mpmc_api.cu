@@ -10,6 +10,7 @@
 
 #include "../../include/mpmc.h"
 #include "mpmc_device.cuh"
+#include "mpmc_params.h"
 #include "mpmc_ops.h"
 
 using namespace mpmc;
@@ -169,98 +170,15 @@ extern "C" int mpmc_create(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_m
                            mpmc_ctx** out) {
   if (!out) return MPMC_INVALID_ARG;
   *out = nullptr;
-  if (!g || !eos || !m) return MPMC_INVALID_ARG;
-  if (g->dim < 1 || g->dim > 3 || eos->n_species < 1 || eos->n_species > MPMC_MAXS || !(g->dx > 0.0))
-    return MPMC_INVALID_ARG;
-  if (m->precision != MPMC_FP64 && m->precision != MPMC_MIXED) return MPMC_INVALID_ARG;
-  for (int d = 0; d < 3; ++d) {
-    if (d < g->dim && g->n[d] < 3) return MPMC_INVALID_ARG;
-    if (d >= g->dim && g->n[d] != 1) return MPMC_INVALID_ARG;
-    if (d < g->dim && (g->bc_lo[d] < 0 || g->bc_lo[d] > 3 || g->bc_hi[d] < 0 || g->bc_hi[d] > 3))
-      return MPMC_INVALID_ARG;
-    if (d < g->dim && ((g->bc_lo[d] == MPMC_BC_PERIODIC) != (g->bc_hi[d] == MPMC_BC_PERIODIC)))
-      return MPMC_INVALID_ARG;
-  }
+  KParams P0;
+  const int prc = build_params(g, eos, m, P0);
+  if (prc) return prc;
   mpmc_ctx* c = new (std::nothrow) mpmc_ctx();
   if (!c) return MPMC_OUT_OF_MEMORY;
   c->err[0] = 0;
+  c->P = P0;
   KParams& P = c->P;
-  memset(&P, 0, sizeof(P));
-  const int ns = eos->n_species, D = g->dim;
-  P.dim = D;
-  P.ns = ns;
-  P.nv = ns + D + 1;
-  for (int d = 0; d < 3; ++d) {
-    P.n[d] = g->n[d];
-    P.bc_lo[d] = d < D ? g->bc_lo[d] : 0;
-    P.bc_hi[d] = d < D ? g->bc_hi[d] : 0;
-    if (d < D && (P.bc_lo[d] == MPMC_BC_INFLOW || P.bc_hi[d] == MPMC_BC_INFLOW)) P.has_inflow = 1;
-  }
-  P.ncell = (long long)g->n[0] * g->n[1] * g->n[2];
-  P.dx = g->dx;
-  P.inv_dx = 1.0 / g->dx;
-  bool has0 = false, has1 = false;
-  for (int k = 0; k < ns; ++k) {
-    P.phase[k] = eos->phase[k] ? 1 : 0;
-    (P.phase[k] ? has1 : has0) = true;
-    P.cv[k] = eos->cv[k];
-    P.gam[k] = eos->gamma[k];
-    P.q[k] = eos->q[k];
-    P.b[k] = eos->b[k];
-    P.pinf[k] = eos->pinf[k];
-    P.W[k] = eos->W[k];
-    P.mu[k] = eos->mu[k];
-    P.Sc[k] = eos->Sc[k];
-    P.Rk[k] = (eos->gamma[k] - 1.0) * eos->cv[k];
-    if (eos->b[k] != 0.0) P.has_b = 1;
-    if (eos->q[k] != 0.0) P.has_q = 1;
-    P.cp[k] = eos->gamma[k] * eos->cv[k];
-  }
-  for (int i = 0; i < ns; ++i)
-    for (int j = 0; j < ns; ++j) {
-      const double Wij = P.W[i] / P.W[j];
-      const double t = 1.0 + std::sqrt(P.mu[i] / P.mu[j]) * std::pow(P.W[j] / P.W[i], 0.25);
-      const double Phi = t * t / (std::sqrt(8.0) * std::sqrt(1.0 + Wij));
-      P.wilke[i][j] = Wij * Phi;
-    }
-  P.two_phase = has0 && has1;
-  P.weno_eps = m->weno_eps;
-  P.cdi = m->cdi ? 1 : 0;
-  P.diffusion = m->diffusion ? 1 : 0;
-  P.pos_limiter = m->pos_limiter ? 1 : 0;
-  P.cdi_eps = m->cdi_eps > 0.0 ? m->cdi_eps : g->dx;
-  P.cdi_gamma = m->cdi_gamma;
-  P.phi_min = m->phi_min;
-  P.psi_delta = m->psi_delta;
-  P.cfl = m->cfl;
-  P.mu_liquid = m->mu_liquid;
-  P.sharp0 = 4.0 * m->phi_min * (1.0 - m->phi_min);
-  // primitive cache layout
-  int f = 0;
-  P.wT = f++;
-  P.wP = f++;
-  P.wRho = f++;
-  P.wA = f++;
-  P.wY = f;
-  f += ns;
-  P.wU = f;
-  f += D;
-  if (P.cdi) {
-    P.wPhi0 = f++;
-    P.wPsi = f++;
-    P.wYrho = f;
-    f += ns;
-    P.wHrho = f;
-    f += 2;
-  }
-  if (P.diffusion) {
-    P.wXr = f;
-    f += ns;
-    P.wB = f;
-    f += ns;
-  }
-  P.nW = f;
-  P.wstride = P.ncell + 1;
+  const int ns = P.ns, D = P.dim;
   c->precision = m->precision;
 
   const bool mixed = m->precision == MPMC_MIXED;

@@ -48,7 +48,36 @@ struct KParams {
   // primitive pass that computes the step's dt and Gamma; FP32 copies of
   // U^(k) live in the FP32 cache at fields nW .. nW + nv - 1
   float* unf;
+  // FP32 roundings of the constants above, made once on the host: the
+  // mixed-precision kernels read these instead of converting per thread (a
+  // double -> float conversion issues on the FP64 pipe)
+  struct Consts32 {
+    float cv[MAXS], gam[MAXS], q[MAXS], b[MAXS], pinf[MAXS], Rk[MAXS], cp[MAXS];
+    float W[MAXS], mu[MAXS], Sc[MAXS], wilke[MAXS][MAXS];
+    float inv_dx, cdi_eps, sharp0, mu_liquid;
+  } f32;
 };
+
+// fills P.f32 from the FP64 fields (host)
+inline void round_consts32(KParams& P) {
+  for (int k = 0; k < MAXS; ++k) {
+    P.f32.cv[k] = (float)P.cv[k];
+    P.f32.gam[k] = (float)P.gam[k];
+    P.f32.q[k] = (float)P.q[k];
+    P.f32.b[k] = (float)P.b[k];
+    P.f32.pinf[k] = (float)P.pinf[k];
+    P.f32.Rk[k] = (float)P.Rk[k];
+    P.f32.cp[k] = (float)P.cp[k];
+    P.f32.W[k] = (float)P.W[k];
+    P.f32.mu[k] = (float)P.mu[k];
+    P.f32.Sc[k] = (float)P.Sc[k];
+    for (int j = 0; j < MAXS; ++j) P.f32.wilke[k][j] = (float)P.wilke[k][j];
+  }
+  P.f32.inv_dx = (float)P.inv_dx;
+  P.f32.cdi_eps = (float)P.cdi_eps;
+  P.f32.sharp0 = (float)P.sharp0;
+  P.f32.mu_liquid = (float)P.mu_liquid;
+}
 
 // ---------------------------------------------------------------------------
 // boundary ghosts by index mapping.  Directions are resolved in order x, y,

@@ -202,13 +202,16 @@ __global__ void __launch_bounds__(CELL_THREADS)
 
 
 // ---------------------------------------------------------------------------
-template <int NS, int D>
+// DIR: the face direction, a template parameter so that every array indexed
+// by it is indexed by a constant (registers, not the stack)
+template <int NS, int D, int DIR>
 __global__ void __launch_bounds__(FACE_THREADS)
-    k_face(const KParams P, const int d, const double* __restrict__ Wc, const double* __restrict__ Un,
+    k_face(const KParams P, const double* __restrict__ Wc, const double* __restrict__ Un,
            const double* __restrict__ Uk, const double* __restrict__ Uin, const double* __restrict__ scal,
            const double rk0, const double rk1, const double rk2, double* __restrict__ F,
            uint32_t* __restrict__ flags, unsigned long long* __restrict__ stats) {
   constexpr int NV = NS + D + 1;
+  constexpr int d = DIR;
   const int f0 = P.n[0] + (d == 0), f1 = P.n[1] + (d == 1), f2 = P.n[2] + (d == 2);
   const long long nf = (long long)f0 * f1 * f2;
   const long long fid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -383,11 +386,18 @@ __global__ void __launch_bounds__(FACE_THREADS)
   if (P.cdi && P.two_phase) {
     bool pres_i[2] = {false, false}, pres_j[2] = {false, false};
     {
+      // (branches on the phase rather than ypi[P.phase[k]]: an array indexed
+      // at run time would live on the stack)
       double ypi[2] = {0.0, 0.0}, ypj[2] = {0.0, 0.0};
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        ypi[P.phase[k]] += Yi[k];
-        ypj[P.phase[k]] += Yj[k];
+        if (P.phase[k]) {
+          ypi[1] += Yi[k];
+          ypj[1] += Yj[k];
+        } else {
+          ypi[0] += Yi[k];
+          ypj[0] += Yj[k];
+        }
       }
 #pragma unroll
       for (int ph = 0; ph < 2; ++ph) {
@@ -524,16 +534,26 @@ __global__ void __launch_bounds__(CELL_THREADS)
     fp[d] = fm[d] + (d == 0 ? 1 : (d == 1 ? f0 : (long long)f0 * f1));
   }
   const double dt = scal[0];
+  // U = rk0 U^n + rk1 U^(k) + rk2 dt L, L = sum_d (F_{-1/2} - F_{+1/2}) / dx:
+  // the flux differences are summed first and scaled once (the FP64 pipe
+  // binds this kernel on GB300); a zero coefficient skips its state's load
+  const double sdx = (rk2 * dt) * P.inv_dx;
   double Uo[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    double L = 0.0;
+    double fs = Fd[0][(long long)v * nf[0] + fm[0]] - Fd[0][(long long)v * nf[0] + fp[0]];
 #pragma unroll
-    for (int d = 0; d < D; ++d) L -= (Fd[d][(long long)v * nf[d] + fp[d]] - Fd[d][(long long)v * nf[d] + fm[d]]) * P.inv_dx;
-    if (dUdt) dUdt[(long long)v * P.ncell + c] = L;
+    for (int d = 1; d < D; ++d) fs += Fd[d][(long long)v * nf[d] + fm[d]] - Fd[d][(long long)v * nf[d] + fp[d]];
+    if (dUdt) dUdt[(long long)v * P.ncell + c] = fs * P.inv_dx;
     // a zero-length step (a run past its end time) leaves the state as it is
-    Uo[v] = dt == 0.0 ? Uk[(long long)v * P.ncell + c]
-                      : rk0 * Un[(long long)v * P.ncell + c] + rk1 * Uk[(long long)v * P.ncell + c] + (rk2 * dt) * L;
+    if (dt == 0.0) {
+      Uo[v] = Uk[(long long)v * P.ncell + c];
+    } else {
+      double t = sdx * fs;
+      if (rk1 != 0.0) t = fma(rk1, Uk[(long long)v * P.ncell + c], t);
+      if (rk0 != 0.0) t = fma(rk0, Un[(long long)v * P.ncell + c], t);
+      Uo[v] = t;
+    }
   }
   if (Uout) {
 #pragma unroll
@@ -560,8 +580,15 @@ struct Impl {
                    uint32_t* flags, unsigned long long* stats) {
     long long nf = 1;
     for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
-    k_face<NS, D><<<nblocks(nf, FACE_THREADS), FACE_THREADS, 0, s>>>(P, d, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F,
-                                                                       flags, stats);
+    const unsigned nb = nblocks(nf, FACE_THREADS);
+    if (d == 0)
+      k_face<NS, D, 0><<<nb, FACE_THREADS, 0, s>>>(P, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags, stats);
+    else if (d == 1)
+      k_face<NS, D, (D > 1 ? 1 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags,
+                                                                 stats);
+    else
+      k_face<NS, D, (D > 2 ? 2 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags,
+                                                                 stats);
   }
   static void update(const KParams& P, cudaStream_t s, const double* Un, const double* Uk, double* const* F,
                      const double* scal, double rk0, double rk1, double rk2, double* Uout, double* dUdt,

@@ -10,6 +10,7 @@
 #pragma once
 #include "mpmc_device.cuh"
 #include "mpmc_ops.h"
+#include "mpmc_widen.h"
 
 namespace mpmc {
 namespace mx {
@@ -30,13 +31,13 @@ template <int NS>
 __device__ __forceinline__ void load_species(const KParams& P, SpeciesF* s) {
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    s[k].cv = (float)P.cv[k];
-    s[k].gam = (float)P.gam[k];
-    s[k].q = (float)P.q[k];
-    s[k].b = (float)P.b[k];
-    s[k].pinf = (float)P.pinf[k];
-    s[k].Rk = (float)P.Rk[k];
-    s[k].cp = (float)P.cp[k];
+    s[k].cv = P.f32.cv[k];
+    s[k].gam = P.f32.gam[k];
+    s[k].q = P.f32.q[k];
+    s[k].b = P.f32.b[k];
+    s[k].pinf = P.f32.pinf[k];
+    s[k].Rk = P.f32.Rk[k];
+    s[k].cp = P.f32.cp[k];
   }
 }
 
@@ -344,11 +345,11 @@ __global__ void __launch_bounds__(CELL_THREADS)
       }
       if (P.cdi) {
         Wc[P.wPhi0 * ws + c] = phi[0];
-        Wc[P.wPsi * ws + c] = (float)P.cdi_eps * __logf((phi[0] + DELTA32) / (phi[1] + DELTA32));
+        Wc[P.wPsi * ws + c] = P.f32.cdi_eps * __logf((phi[0] + DELTA32) / (phi[1] + DELTA32));
       }
       if (P.diffusion) {
         float mup[2];
-        mup[0] = (float)P.mu_liquid;
+        mup[0] = P.f32.mu_liquid;
         float num = 0.f;
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -356,8 +357,8 @@ __global__ void __launch_bounds__(CELL_THREADS)
           float den = 0.f;
 #pragma unroll
           for (int j = 0; j < NS; ++j)
-            if (P.phase[j] == 1) den += Yf[j] * (float)P.wilke[i][j];
-          if (den > 0.f) num += Yf[i] * (float)P.mu[i] / den;
+            if (P.phase[j] == 1) den += Yf[j] * P.f32.wilke[i][j];
+          if (den > 0.f) num += Yf[i] * P.f32.mu[i] / den;
         }
         mup[1] = Yp[1] > 0.f ? num : 0.f;
         mu = phi[0] * mup[0] + phi[1] * mup[1];
@@ -366,17 +367,17 @@ __global__ void __launch_bounds__(CELL_THREADS)
           float sY = 0.f;
 #pragma unroll
           for (int j = 0; j < NS; ++j)
-            if (P.phase[j] == ph) sY += Yf[j] / (float)P.W[j];
+            if (P.phase[j] == ph) sY += Yf[j] / P.f32.W[j];
           const bool present = Yp[ph] > 0.f && sY > 0.f && phi[ph] > 0.f;
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
             if (P.phase[k] != ph) continue;
             float xr = 0.f, B = 0.f;
             if (present) {
-              xr = (Yf[k] / (float)P.W[k]) / sY;
-              const float WcWp = (float)P.W[k] * sY / Yp[ph];
+              xr = (Yf[k] / P.f32.W[k]) / sY;
+              const float WcWp = P.f32.W[k] * sY / Yp[ph];
               const float rho_p = rhof * Yp[ph] / phi[ph];
-              B = WcWp * (mup[ph] / (rho_p * (float)P.Sc[k]));
+              B = WcWp * (mup[ph] / (rho_p * P.f32.Sc[k]));
             }
             Wc[(P.wXr + k) * ws + c] = xr;
             Wc[(P.wB + k) * ws + c] = B;
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
     }
     if (st != ST_OK) atomicMax(status, st);
     if (c < P.ncell) {
-      const float idx = (float)P.inv_dx;
+      const float idx = P.f32.inv_dx;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const float ud = fabsf((float)u[d]);
@@ -429,7 +430,7 @@ __device__ __forceinline__ int admissible_f(const KParams& P, const float* Unf, 
   for (int k = 0; k < NS; ++k) {
     rho += T[k];
     Mrho += M[k];
-    const float b = (float)P.b[k], q = (float)P.q[k];
+    const float b = P.f32.b[k], q = P.f32.q[k];
     sb += T[k] * b;
     Msb += M[k] * fabsf(b);
     sq += T[k] * q;
@@ -454,13 +455,16 @@ __device__ __forceinline__ int admissible_f(const KParams& P, const float* Unf, 
 
 // per face: FP32 pipeline; the limiter's decisions from FP32 copies of the
 // states with a margin, in FP64 when a state is too close to call
-template <int NS, int D>
+// DIR: the face direction, a template parameter so that every array indexed
+// by it is indexed by a constant (registers, not the stack)
+template <int NS, int D, int DIR>
 __global__ void __launch_bounds__(FACE_THREADS)
-    k_face(const KParams P, const int d, const float* __restrict__ Wc, const double* __restrict__ Un,
+    k_face(const KParams P, const float* __restrict__ Wc, const double* __restrict__ Un,
            const double* __restrict__ Uk, const double* __restrict__ Uin, const double* __restrict__ scal,
            const double rk0, const double rk1, const double rk2, float* __restrict__ F,
            uint32_t* __restrict__ flags, unsigned long long* __restrict__ stats) {
   constexpr int NV = NS + D + 1;
+  constexpr int d = DIR;
   const int f0 = P.n[0] + (d == 0), f1 = P.n[1] + (d == 1), f2 = P.n[2] + (d == 2);
   const long long nf = (long long)f0 * f1 * f2;
   const long long fid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -670,11 +674,18 @@ __global__ void __launch_bounds__(FACE_THREADS)
   if (P.cdi && P.two_phase) {
     bool pres_i[2] = {false, false}, pres_j[2] = {false, false};
     {
+      // (branches on the phase rather than ypi[P.phase[k]]: an array indexed
+      // at run time would live on the stack)
       float ypi[2] = {0.f, 0.f}, ypj[2] = {0.f, 0.f};
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        ypi[P.phase[k]] += Yi[k];
-        ypj[P.phase[k]] += Yj[k];
+        if (P.phase[k]) {
+          ypi[1] += Yi[k];
+          ypj[1] += Yj[k];
+        } else {
+          ypi[0] += Yi[k];
+          ypj[0] += Yj[k];
+        }
       }
 #pragma unroll
       for (int ph = 0; ph < 2; ++ph) {
@@ -683,7 +694,7 @@ __global__ void __launch_bounds__(FACE_THREADS)
       }
     }
     if ((pres_i[0] || pres_j[0]) && (pres_i[1] || pres_j[1])) {
-      const float ceps = (float)P.cdi_eps, idx = (float)P.inv_dx;
+      const float ceps = P.f32.cdi_eps, idx = P.f32.inv_dx;
       const float psi_i = wgetf(P, Wc, P.wPsi, ri), psi_j = wgetf(P, Wc, P.wPsi, rj);
       const float dphi = (wgetf(P, Wc, P.wPhi0, rj) - wgetf(P, Wc, P.wPhi0, ri)) * idx;
       float g[3] = {0.f, 0.f, 0.f};
@@ -707,7 +718,7 @@ __global__ void __launch_bounds__(FACE_THREADS)
       const float nd = gn >= GTOL32 ? g[d] / gn : 0.f;
       const float ch = coshf((0.5f * (psi_i + psi_j)) / (2.f * ceps));
       const float sech2 = __frcp_rn(ch * ch);
-      const float ahat0 = Gamma * (ceps * dphi - 0.25f * (sech2 - (float)P.sharp0) * nd);
+      const float ahat0 = Gamma * (ceps * dphi - 0.25f * (sech2 - P.f32.sharp0) * nd);
       float Fdi[NV], Rtot = 0.f, hR = 0.f;
 #pragma unroll
       for (int ph = 0; ph < 2; ++ph) {
@@ -745,7 +756,7 @@ __global__ void __launch_bounds__(FACE_THREADS)
   }
 
   if (P.diffusion) {
-    const float idx = (float)P.inv_dx;
+    const float idx = P.f32.inv_dx;
     const float rb = 0.5f * (wgetf(P, Wc, P.wRho, ri) + wgetf(P, Wc, P.wRho, rj));
     float Jh = 0.f;
 #pragma unroll
@@ -809,19 +820,28 @@ __global__ void __launch_bounds__(CELL_THREADS)
     fm[d] = ((long long)k * f1 + j) * f0 + i;
     fp[d] = fm[d] + (d == 0 ? 1 : (d == 1 ? f0 : (long long)f0 * f1));
   }
-  const double s = rk2 * scal[0];
+  const double dt = scal[0];
+  // as the FP64 update, on the FP32 fluxes widened exactly (on the integer
+  // pipes): each flux enters its two cells with opposite signs and the same
+  // FP64 value, so the sum over cells telescopes to FP64 rounding
+  const double sdx = (rk2 * dt) * P.inv_dx;
   double Uo[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    double L = 0.0;
+    double fs = widen(Fd[0][(long long)v * nf[0] + fm[0]]) - widen(Fd[0][(long long)v * nf[0] + fp[0]]);
 #pragma unroll
-    for (int d = 0; d < D; ++d)
-      L -= (double)Fd[d][(long long)v * nf[d] + fp[d]] - (double)Fd[d][(long long)v * nf[d] + fm[d]];
-    L *= P.inv_dx;
-    if (dUdt) dUdt[(long long)v * P.ncell + c] = L;
+    for (int d = 1; d < D; ++d)
+      fs += widen(Fd[d][(long long)v * nf[d] + fm[d]]) - widen(Fd[d][(long long)v * nf[d] + fp[d]]);
+    if (dUdt) dUdt[(long long)v * P.ncell + c] = fs * P.inv_dx;
     // a zero-length step (a run past its end time) leaves the state as it is
-    Uo[v] = s == 0.0 ? Uk[(long long)v * P.ncell + c]
-                     : rk0 * Un[(long long)v * P.ncell + c] + rk1 * Uk[(long long)v * P.ncell + c] + s * L;
+    if (dt == 0.0) {
+      Uo[v] = Uk[(long long)v * P.ncell + c];
+    } else {
+      double t = sdx * fs;
+      if (rk1 != 0.0) t = fma(rk1, Uk[(long long)v * P.ncell + c], t);
+      if (rk0 != 0.0) t = fma(rk0, Un[(long long)v * P.ncell + c], t);
+      Uo[v] = t;
+    }
   }
   if (Uout) {
 #pragma unroll
@@ -844,9 +864,17 @@ struct Impl {
                    uint32_t* flags, unsigned long long* stats) {
     long long nf = 1;
     for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
-    k_face<NS, D><<<nblocks(nf, FACE_THREADS), FACE_THREADS, 0, s>>>(
-        P, d, reinterpret_cast<const float*>(Wc), Un, Uk, Uin, scal, rk0, rk1, rk2, reinterpret_cast<float*>(F),
-        flags, stats);
+    const unsigned nb = nblocks(nf, FACE_THREADS);
+    const float* W = reinterpret_cast<const float*>(Wc);
+    float* Ff = reinterpret_cast<float*>(F);
+    if (d == 0)
+      k_face<NS, D, 0><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, Ff, flags, stats);
+    else if (d == 1)
+      k_face<NS, D, (D > 1 ? 1 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, Ff, flags,
+                                                                 stats);
+    else
+      k_face<NS, D, (D > 2 ? 2 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, Ff, flags,
+                                                                 stats);
   }
   static void update(const KParams& P, cudaStream_t s, const double* Un, const double* Uk, double* const* F,
                      const double* scal, double rk0, double rk1, double rk2, double* Uout, double* dUdt,

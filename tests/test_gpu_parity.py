@@ -285,12 +285,21 @@ def test_iec_on_gpu(mp):
     p = W.interface_advection_1d(n=400, cdi=1)
     o = Oracle(p)
     ctx = mp.Context(p)
+    nsteps = 300
     U = ctx.init_state(torch.from_numpy(p.prim))
-    ctx.step_n(U, 300)
+    ctx.step_n(U, nsteps)
     Uh = U.cpu().numpy()
     pr = o.primitives(Uh)
     u = Uh[2] / Uh[:2].sum(0)
-    assert np.abs(pr["P"] / 1e5 - 1).max() < 1e-10
+    # the liquid's pressure (P << Pinf) is a difference of energies ~gamma Pinf:
+    # one FP64 rounding of E moves P by eps gamma Pinf / P relative, and the
+    # roundings of n steps add up like a random walk (the oracle reaches 6e-11
+    # here, the same from a start perturbed by 1e-16)
+    liq = max(p.species, key=lambda sp: sp.pinf)
+    amp = np.finfo(float).eps * liq.gamma * liq.pinf / 1e5
+    eP = np.abs(pr["P"] / 1e5 - 1).max()
+    print(f"IEC after {nsteps} steps: P {eP:.2e} (bound {10 * np.sqrt(nsteps) * amp:.2e})")
+    assert eP < 10 * np.sqrt(nsteps) * amp
     assert np.abs(pr["T"] / 300 - 1).max() < 1e-12
     assert np.abs(u / 100 - 1).max() < 1e-12
 
