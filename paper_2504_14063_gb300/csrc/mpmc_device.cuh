@@ -495,13 +495,16 @@ __device__ __forceinline__ bool admissible(const KParams& P, const double* U) {
     if (P.has_b) sb += U[k] * P.b[k];
     if (P.has_q) sq += U[k] * P.q[k];
   }
-  bool ok = rho > 0.0 && (1.0 - sb) > 0.0;
+  // (without covolumes or reference energies the b and q terms are zero:
+  // they are skipped, not evaluated as 1 - 0 and x - 0)
+  bool ok = rho > 0.0 && (!P.has_b || (1.0 - sb) > 0.0);
 #pragma unroll
   for (int k = 0; k < NS; ++k) ok = ok && (U[k] >= -YTOL * rho);
   double mm = 0.0;
 #pragma unroll
   for (int d = 0; d < D; ++d) mm += U[NS + d] * U[NS + d];
-  return ok && (rho * U[NS + D] - 0.5 * mm - rho * sq > 0.0);
+  const double ei = rho * U[NS + D] - 0.5 * mm;
+  return ok && ((P.has_q ? ei - rho * sq : ei) > 0.0);
 }
 
 // mass-fraction limiter of Sec. 3.3.1 on one face side (Yc: cell values)

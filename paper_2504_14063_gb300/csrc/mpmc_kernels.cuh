@@ -538,6 +538,9 @@ __global__ void __launch_bounds__(CELL_THREADS)
   // the flux differences are summed first and scaled once (the FP64 pipe
   // binds this kernel on GB300); a zero coefficient skips its state's load
   const double sdx = (rk2 * dt) * P.inv_dx;
+  // the coefficient tests, once per thread as integers (FP64 comparisons
+  // issue on the FP64 pipe, and would otherwise be repeated per variable)
+  const int keep = dt == 0.0, use_k = rk1 != 0.0, use_n = rk0 != 0.0;
   double Uo[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -546,12 +549,12 @@ __global__ void __launch_bounds__(CELL_THREADS)
     for (int d = 1; d < D; ++d) fs += Fd[d][(long long)v * nf[d] + fm[d]] - Fd[d][(long long)v * nf[d] + fp[d]];
     if (dUdt) dUdt[(long long)v * P.ncell + c] = fs * P.inv_dx;
     // a zero-length step (a run past its end time) leaves the state as it is
-    if (dt == 0.0) {
+    if (keep) {
       Uo[v] = Uk[(long long)v * P.ncell + c];
     } else {
       double t = sdx * fs;
-      if (rk1 != 0.0) t = fma(rk1, Uk[(long long)v * P.ncell + c], t);
-      if (rk0 != 0.0) t = fma(rk0, Un[(long long)v * P.ncell + c], t);
+      if (use_k) t = fma(rk1, Uk[(long long)v * P.ncell + c], t);
+      if (use_n) t = fma(rk0, Un[(long long)v * P.ncell + c], t);
       Uo[v] = t;
     }
   }

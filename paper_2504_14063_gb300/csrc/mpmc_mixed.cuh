@@ -825,6 +825,9 @@ __global__ void __launch_bounds__(CELL_THREADS)
   // pipes): each flux enters its two cells with opposite signs and the same
   // FP64 value, so the sum over cells telescopes to FP64 rounding
   const double sdx = (rk2 * dt) * P.inv_dx;
+  // the coefficient tests, once per thread as integers (FP64 comparisons
+  // issue on the FP64 pipe, and would otherwise be repeated per variable)
+  const int keep = dt == 0.0, use_k = rk1 != 0.0, use_n = rk0 != 0.0;
   double Uo[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -834,12 +837,12 @@ __global__ void __launch_bounds__(CELL_THREADS)
       fs += widen(Fd[d][(long long)v * nf[d] + fm[d]]) - widen(Fd[d][(long long)v * nf[d] + fp[d]]);
     if (dUdt) dUdt[(long long)v * P.ncell + c] = fs * P.inv_dx;
     // a zero-length step (a run past its end time) leaves the state as it is
-    if (dt == 0.0) {
+    if (keep) {
       Uo[v] = Uk[(long long)v * P.ncell + c];
     } else {
       double t = sdx * fs;
-      if (rk1 != 0.0) t = fma(rk1, Uk[(long long)v * P.ncell + c], t);
-      if (rk0 != 0.0) t = fma(rk0, Un[(long long)v * P.ncell + c], t);
+      if (use_k) t = fma(rk1, Uk[(long long)v * P.ncell + c], t);
+      if (use_n) t = fma(rk0, Un[(long long)v * P.ncell + c], t);
       Uo[v] = t;
     }
   }
