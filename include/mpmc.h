@@ -131,7 +131,9 @@ typedef struct mpmc_ctx mpmc_ctx;
 /* Creates a context for one grid / species table / model on the current
  * CUDA device; allocates all scratch sized by the grid.  stream: cudaStream_t
  * or NULL.  Returns MPMC_INVALID_ARG for unsupported sizes (ns > MPMC_MAXS,
- * dim outside 1..3, an active n[d] < 3, dx <= 0), MPMC_OUT_OF_MEMORY if an
+ * dim outside 1..3, an active n[d] < 3, dx <= 0, 2^31 - 1 or more cells or
+ * faces in one direction: the kernels index them in 32 bits, and no such
+ * grid's state and scratch fit in one GPU's memory), MPMC_OUT_OF_MEMORY if an
  * allocation fails.  *out is NULL on failure. */
 int mpmc_create(const mpmc_grid* grid, const mpmc_eos* eos, const mpmc_model* model, void* stream,
                 mpmc_ctx** out);

@@ -131,7 +131,7 @@ __device__ __forceinline__ void face_avg_fwd(const KParams& P, const double* Uk,
 #pragma unroll
   for (int v = 0; v < NV; ++v) f.Ub[v] = 0.5 * (Ui[v] + Uj[v]);
   decode<NS, D, false>(f.Ub, f.rb, f.Yb, f.ub, f.eb, f.vb);
-  pt_equilibrium<NS, false>(P, f.Yb, f.eb, f.vb, f.pb, f.Tb);
+  pt_equilibrium<NS, false>(P, f.Yb, f.eb, f.vb, f.pb, f.Tb, f.rb);
 #pragma unroll
   for (int k = 0; k < NS; ++k) f.tb.Y[k] = f.Yb[k];
   f.tb.p = f.pb;
@@ -180,10 +180,7 @@ __global__ void __launch_bounds__(VJP_THREADS)
   const Lay<NS, D> L(P.cdi, P.diffusion);
   auto put = [&](int q, double v) { C[(long long)q * nf + fid] = v; };
   int fc[3];
-  fc[0] = (int)(fid % f0);
-  const long long rr = fid / f0;
-  fc[1] = (int)(rr % f1);
-  fc[2] = (int)(rr / f1);
+  unflatten(fid, f0, f1, fc);
   int ci[3] = {fc[0], fc[1], fc[2]};
   ci[d] -= 1;
   const double Gamma = scal[1];
@@ -781,10 +778,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
   if (c >= P.ncell) return;
   const Lay<NS, D> L(P.cdi, P.diffusion);
   int cc[3];
-  cc[0] = (int)(c % P.n[0]);
-  const long long r = c / P.n[0];
-  cc[1] = (int)(r % P.n[1]);
-  cc[2] = (int)(r / P.n[1]);
+  unflatten(c, P.n[0], P.n[1], cc);
   const int f0 = P.n[0] + (d == 0), f1 = P.n[1] + (d == 1), f2 = P.n[2] + (d == 2);
   const long long nf = (long long)f0 * f1 * f2;
   auto face = [&](const int* fc) { return ((long long)fc[2] * f1 + fc[1]) * f0 + fc[0]; };

@@ -79,6 +79,18 @@ inline void round_consts32(KParams& P) {
   P.f32.mu_liquid = (float)P.mu_liquid;
 }
 
+// (x, y, z) of the linear index l of an n0 x n1 x n2 box, in 32-bit unsigned
+// arithmetic (mpmc_create admits no grid with 2^31 - 1 cells or faces; a
+// 64-bit division costs the FP64 pipe, which binds these kernels on GB300)
+__device__ __forceinline__ void unflatten(long long l, int n0, int n1, int* x) {
+  const unsigned u = (unsigned)l, a = (unsigned)n0, b = (unsigned)n1;
+  const unsigned r = u / a;
+  const unsigned z = r / b;
+  x[0] = (int)(u - r * a);
+  x[1] = (int)(r - z * b);
+  x[2] = (int)z;
+}
+
 // ---------------------------------------------------------------------------
 // boundary ghosts by index mapping.  Directions are resolved in order x, y,
 // z: periodic and zero-gradient remap the coordinate, a wall mirrors it and
@@ -234,7 +246,8 @@ __device__ __forceinline__ void decode(const double* U, double& rho, double* Y, 
 // on the common-pressure residual, started from the quadratic with a
 // Y-weighted Pinf, at most 100 iterations.
 template <int NS, bool EX = true>
-__device__ int pt_equilibrium(const KParams& P, const double* Y, double e, double v, double& p, double& T) {
+__device__ int pt_equilibrium(const KParams& P, const double* Y, double e, double v, double& p, double& T,
+                              double rho = 0.0) {
   double Cv = 0.0, q = 0.0, b = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
@@ -245,7 +258,9 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
   const double em = sub_<EX>(e, q), vm = sub_<EX>(v, b);
   int st = ST_OK;
   if (!(em > 0.0) || !(vm > 0.0)) st = ST_INADMISSIBLE;
-  const double Ep = em / vm;
+  // (the contracted form takes E' = (e - q) rho, one division fewer, when no
+  // species has a covolume and the caller passes rho = 1/v)
+  const double Ep = (!EX && !P.has_b && rho > 0.0) ? em * rho : em / vm;
   double pl = -1.0, pmin = 1e300, Rg = 0.0, Rl = 0.0, wpl = 0.0;
   bool multi = false, gas = false;
 #pragma unroll
@@ -319,6 +334,26 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
     }
     if (!conv && st == ST_OK) st = ST_EOS_NO_CONVERGE;
     p = x;
+  }
+  if (!EX && !multi && pl > 0.0) {
+    // every stiffened species present shares P + pl: T = em (P + pl) /
+    // (sum_gas Y cv (P + pl) + sum_liquid Y cv (P + gamma pl)), one division
+    // (a species with another Pinf can only be a trace below zero, which
+    // did not set pl: it keeps its own ratio)
+    const double pp = p + pl;
+    double g = 0.0, l = 0.0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+      if (Y[k] != 0.0) {
+        if (P.pinf[k] == 0.0)
+          g += Y[k] * P.cv[k];
+        else if (P.pinf[k] == pl)
+          l += Y[k] * P.cv[k] * (p + P.gam[k] * pl);
+        else
+          g += Y[k] * P.cv[k] * (p + P.gam[k] * P.pinf[k]) / (p + P.pinf[k]);
+      }
+    T = em * pp / (g * pp + l);
+    return st;
   }
   double den = 0.0;
 #pragma unroll
@@ -431,6 +466,26 @@ struct State {
   double rho, rhoY[NS], u[3], m[3], p, E, a;
 };
 
+// F(S) + s (U*_S - U_S): the HLLC flux on the side S of the contact the
+// face lies on (s = min(0, s_L) for the left side, max(0, s_R) for the right,
+// sS its wave speed, dS = sS - u_S)
+template <int NS, int D>
+__device__ __forceinline__ void hllc_side(int d, const State<NS>& S, double s, double sS, double dS, double ss,
+                                          double* F) {
+  const double f = dS / (sS - ss);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) F[k] = S.rhoY[k] * S.u[d] + s * (f * S.rhoY[k] - S.rhoY[k]);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const double Fs = S.rho * S.u[d] * S.u[j] + (j == d ? S.p : 0.0);
+    const double Us = f * S.rho * (j == d ? ss : S.u[j]);
+    F[NS + j] = Fs + s * (Us - S.m[j]);
+  }
+  const double Fs = S.u[d] * (S.E + S.p);
+  const double Us = f * (S.E + (ss - S.u[d]) * (S.rho * ss + S.p / dS));
+  F[NS + D] = Fs + s * (Us - S.E);
+}
+
 template <int NS, int D>
 __device__ __forceinline__ void hllc(int d, const State<NS>& L, const State<NS>& R, double* F) {
   const double ub = 0.5 * (L.u[d] + R.u[d]), ab = 0.5 * (L.a + R.a);
@@ -439,28 +494,19 @@ __device__ __forceinline__ void hllc(int d, const State<NS>& L, const State<NS>&
   const double sm = fmin(0.0, sL), sp = fmax(0.0, sR);
   const double dL = sL - L.u[d], dR = sR - R.u[d];
   const double ss = (R.p - L.p + L.rho * L.u[d] * dL - R.rho * R.u[d] * dR) / (L.rho * dL - R.rho * dR);
-  // sign(0) = 0: both branches with weight 1/2
-  const double wl = ss > 0.0 ? 1.0 : (ss < 0.0 ? 0.0 : 0.5);
-  const double wr = 1.0 - wl;
-  const double fL = dL / (sL - ss), fR = dR / (sR - ss);
+  // only the side of the contact the face lies on is evaluated; sign(0) = 0
+  // takes both with weight 1/2
+  if (ss > 0.0) {
+    hllc_side<NS, D>(d, L, sm, sL, dL, ss, F);
+  } else if (ss < 0.0) {
+    hllc_side<NS, D>(d, R, sp, sR, dR, ss, F);
+  } else {
+    constexpr int NV = NS + D + 1;
+    double FL[NV], FR[NV];
+    hllc_side<NS, D>(d, L, sm, sL, dL, ss, FL);
+    hllc_side<NS, D>(d, R, sp, sR, dR, ss, FR);
 #pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    const double FL = L.rhoY[k] * L.u[d], FR = R.rhoY[k] * R.u[d];
-    F[k] = wl * (FL + sm * (fL * L.rhoY[k] - L.rhoY[k])) + wr * (FR + sp * (fR * R.rhoY[k] - R.rhoY[k]));
-  }
-#pragma unroll
-  for (int j = 0; j < D; ++j) {
-    const double FL = L.rho * L.u[d] * L.u[j] + (j == d ? L.p : 0.0);
-    const double FR = R.rho * R.u[d] * R.u[j] + (j == d ? R.p : 0.0);
-    const double UsL = fL * L.rho * (j == d ? ss : L.u[j]);
-    const double UsR = fR * R.rho * (j == d ? ss : R.u[j]);
-    F[NS + j] = wl * (FL + sm * (UsL - L.m[j])) + wr * (FR + sp * (UsR - R.m[j]));
-  }
-  {
-    const double FL = L.u[d] * (L.E + L.p), FR = R.u[d] * (R.E + R.p);
-    const double UsL = fL * (L.E + (ss - L.u[d]) * (L.rho * ss + L.p / dL));
-    const double UsR = fR * (R.E + (ss - R.u[d]) * (R.rho * ss + R.p / dR));
-    F[NS + D] = wl * (FL + sm * (UsL - L.E)) + wr * (FR + sp * (UsR - R.E));
+    for (int v = 0; v < NV; ++v) F[v] = 0.5 * FL[v] + 0.5 * FR[v];
   }
 }
 

@@ -217,10 +217,7 @@ __global__ void __launch_bounds__(FACE_THREADS)
   const long long fid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (fid >= nf) return;
   int fc[3];
-  fc[0] = (int)(fid % f0);
-  const long long rr = fid / f0;
-  fc[1] = (int)(rr % f1);
-  fc[2] = (int)(rr / f1);
+  unflatten(fid, f0, f1, fc);
   int ci[3] = {fc[0], fc[1], fc[2]};
   ci[d] -= 1;  // the cell on the low side of the face
   const double dt = scal[0], Gamma = scal[1];
@@ -249,7 +246,7 @@ __global__ void __launch_bounds__(FACE_THREADS)
     double rho, Y[NS], uu[3], e, vol;
     decode<NS, D, false>(Ui, rho, Y, uu, e, vol);
     double p, T, a, al, be;
-    pt_equilibrium<NS, false>(P, Y, e, vol, p, T);
+    pt_equilibrium<NS, false>(P, Y, e, vol, p, T, rho);
     eos_char<NS>(P, Y, p, T, rho, a, al, be);
     X = (rho * a * a * be - 1.0) / (al * a * a * rho);
     c = a * rho;
@@ -521,9 +518,9 @@ __global__ void __launch_bounds__(CELL_THREADS)
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= P.ncell) return;
   const int n0 = P.n[0], n1 = P.n[1];
-  const int i = (int)(c % n0);
-  const long long r = c / n0;
-  const int j = (int)(r % n1), k = (int)(r / n1);
+  int ijk[3];
+  unflatten(c, n0, n1, ijk);
+  const int i = ijk[0], j = ijk[1], k = ijk[2];
   const double* Fd[3] = {F0, F1, F2};
   long long fm[3], fp[3], nf[3];
 #pragma unroll

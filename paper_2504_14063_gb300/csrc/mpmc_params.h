@@ -27,6 +27,17 @@ inline int build_params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_mode
     if (d < g->dim && ((g->bc_lo[d] == MPMC_BC_PERIODIC) != (g->bc_hi[d] == MPMC_BC_PERIODIC)))
       return MPMC_INVALID_ARG;
   }
+  // cells (plus the inflow slot) and the faces of each direction are
+  // indexed in 32 bits on the device
+  {
+    long long lim = (long long)g->n[0] * g->n[1] * g->n[2] + 1;
+    for (int d = 0; d < g->dim; ++d) {
+      long long nf = 1;
+      for (int e = 0; e < 3; ++e) nf *= (long long)g->n[e] + (e == d);
+      if (nf > lim) lim = nf;
+    }
+    if (lim >= 2147483647LL) return MPMC_INVALID_ARG;
+  }
   memset(&P, 0, sizeof(P));
   const int ns = eos->n_species, D = g->dim;
   P.dim = D;

@@ -73,3 +73,9 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     g.n[0] = 2
     assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
     assert h.value is None
+    # 2^31 - 1 cells or faces: beyond the kernels' 32-bit indexing
+    g.n[0] = 2 ** 31 - 1
+    assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
+    g.n[0] = 2 ** 31 - 2     # 2^31 - 2 cells + the inflow slot, 2^31 - 1 faces
+    assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
+    assert h.value is None
