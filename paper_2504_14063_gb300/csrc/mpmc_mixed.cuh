@@ -10,7 +10,7 @@
 #pragma once
 #include "mpmc_device.cuh"
 #include "mpmc_ops.h"
-#include "mpmc_widen.h"
+#include "mpmc_update.cuh"
 
 namespace mpmc {
 namespace mx {
@@ -472,7 +472,7 @@ template <int NS, int D, int DIR>
 __global__ void __launch_bounds__(FACE_THREADS, 5)
     k_face(const KParams P, const float* __restrict__ Wc, const double* __restrict__ Un,
            const double* __restrict__ Uk, const double* __restrict__ Uin, const double* __restrict__ scal,
-           const double rk0, const double rk1, const double rk2, float* __restrict__ F,
+           const double rk0, const double rk1, const double rk2, double* __restrict__ F,
            uint32_t* __restrict__ flags, unsigned long long* __restrict__ stats) {
   constexpr int NV = NS + D + 1;
   constexpr int d = DIR;
@@ -794,7 +794,10 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
   }
 
 #pragma unroll
-  for (int v = 0; v < NV; ++v) F[(long long)v * nf + fid] = Fx[v];
+  // stored widened to FP64 (exact): the update then takes every flux with
+  // the same FP64 value in its two cells, and the widening happens once per
+  // face, here, where the FP64 pipe is otherwise idle
+  for (int v = 0; v < NV; ++v) F[(long long)v * nf + fid] = (double)Fx[v];
   if (flags) flags[fid] = fl;
   if (stats && fl) {
     if (fl & F_HLLC_FALLBACK) atomicAdd(stats + 1, 1ull);
@@ -805,60 +808,16 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
   }
 }
 
-// divergence of the FP32 fluxes and the RK combination, both in FP64
+// divergence and RK combination in FP64 (the FP64 path's, on the widened fluxes)
 template <int NS, int D>
 __global__ void __launch_bounds__(CELL_THREADS)
     k_update(const KParams P, const double* __restrict__ Un, const double* __restrict__ Uk,
-             const float* __restrict__ F0, const float* __restrict__ F1, const float* __restrict__ F2,
+             const double* __restrict__ F0, const double* __restrict__ F1, const double* __restrict__ F2,
              const double* __restrict__ scal, const double rk0, const double rk1, const double rk2,
              double* __restrict__ Uout, double* __restrict__ dUdt, int* __restrict__ status) {
-  constexpr int NV = NS + D + 1;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= P.ncell) return;
-  const int n0 = P.n[0], n1 = P.n[1];
-  int ijk[3];
-  unflatten(c, n0, n1, ijk);
-  const int i = ijk[0], j = ijk[1], k = ijk[2];
-  const float* Fd[3] = {F0, F1, F2};
-  long long fm[3], fp[3], nf[3];
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    const int f0 = n0 + (d == 0), f1 = n1 + (d == 1), f2 = P.n[2] + (d == 2);
-    nf[d] = (long long)f0 * f1 * f2;
-    fm[d] = ((long long)k * f1 + j) * f0 + i;
-    fp[d] = fm[d] + (d == 0 ? 1 : (d == 1 ? f0 : (long long)f0 * f1));
-  }
-  const double dt = scal[0];
-  // as the FP64 update, on the FP32 fluxes widened exactly (on the integer
-  // pipes): each flux enters its two cells with opposite signs and the same
-  // FP64 value, so the sum over cells telescopes to FP64 rounding
-  const double sdx = (rk2 * dt) * P.inv_dx;
-  // the coefficient tests, once per thread as integers (FP64 comparisons
-  // issue on the FP64 pipe, and would otherwise be repeated per variable)
-  const int keep = dt == 0.0, use_k = rk1 != 0.0, use_n = rk0 != 0.0;
-  double Uo[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    double fs = widen(Fd[0][(long long)v * nf[0] + fm[0]]) - widen(Fd[0][(long long)v * nf[0] + fp[0]]);
-#pragma unroll
-    for (int d = 1; d < D; ++d)
-      fs += widen(Fd[d][(long long)v * nf[d] + fm[d]]) - widen(Fd[d][(long long)v * nf[d] + fp[d]]);
-    if (dUdt) dUdt[(long long)v * P.ncell + c] = fs * P.inv_dx;
-    // a zero-length step (a run past its end time) leaves the state as it is
-    if (keep) {
-      Uo[v] = Uk[(long long)v * P.ncell + c];
-    } else {
-      double t = sdx * fs;
-      if (use_k) t = fma(rk1, Uk[(long long)v * P.ncell + c], t);
-      if (use_n) t = fma(rk0, Un[(long long)v * P.ncell + c], t);
-      Uo[v] = t;
-    }
-  }
-  if (Uout) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Uout[(long long)v * P.ncell + c] = Uo[v];
-    if (!admissible<NS, D>(P, Uo)) atomicMax(status, (int)ST_INADMISSIBLE);
-  }
+  update_cell<NS, D>(P, c, Un, Uk, F0, F1, F2, scal, rk0, rk1, rk2, Uout, dUdt, status);
 }
 
 inline unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -877,24 +836,20 @@ struct Impl {
     for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
     const unsigned nb = nblocks(nf, FACE_THREADS);
     const float* W = reinterpret_cast<const float*>(Wc);
-    float* Ff = reinterpret_cast<float*>(F);
     if (d == 0)
-      k_face<NS, D, 0><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, Ff, flags, stats);
+      k_face<NS, D, 0><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags, stats);
     else if (d == 1)
-      k_face<NS, D, (D > 1 ? 1 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, Ff, flags,
+      k_face<NS, D, (D > 1 ? 1 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags,
                                                                  stats);
     else
-      k_face<NS, D, (D > 2 ? 2 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, Ff, flags,
+      k_face<NS, D, (D > 2 ? 2 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags,
                                                                  stats);
   }
   static void update(const KParams& P, cudaStream_t s, const double* Un, const double* Uk, double* const* F,
                      const double* scal, double rk0, double rk1, double rk2, double* Uout, double* dUdt,
                      int* status) {
-    const float* F0 = reinterpret_cast<const float*>(F[0]);
-    const float* F1 = reinterpret_cast<const float*>(D > 1 ? F[1] : F[0]);
-    const float* F2 = reinterpret_cast<const float*>(D > 2 ? F[2] : F[0]);
-    k_update<NS, D><<<nblocks(P.ncell, CELL_THREADS), CELL_THREADS, 0, s>>>(P, Un, Uk, F0, F1, F2, scal, rk0, rk1,
-                                                                             rk2, Uout, dUdt, status);
+    k_update<NS, D><<<nblocks(P.ncell, CELL_THREADS), CELL_THREADS, 0, s>>>(
+        P, Un, Uk, F[0], D > 1 ? F[1] : F[0], D > 2 ? F[2] : F[0], scal, rk0, rk1, rk2, Uout, dUdt, status);
   }
 };
 
