@@ -80,8 +80,8 @@ inline void round_consts32(KParams& P) {
 }
 
 // (x, y, z) of the linear index l of an n0 x n1 x n2 box, in 32-bit unsigned
-// arithmetic (mpmc_create admits no grid with 2^31 - 1 cells or faces; a
-// 64-bit division costs the FP64 pipe, which binds these kernels on GB300)
+// arithmetic, cheaper than 64-bit division (mpmc_create admits no grid with
+// 2^31 - 1 cells or faces)
 __device__ __forceinline__ void unflatten(long long l, int n0, int n1, int* x) {
   const unsigned u = (unsigned)l, a = (unsigned)n0, b = (unsigned)n1;
   const unsigned r = u / a;
