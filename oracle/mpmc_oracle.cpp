@@ -406,6 +406,207 @@ R weno5z(const R& v0, const R& v1, const R& v2, const R& v3, const R& v4, double
 }
 
 /* ------------------------------------------------------------------------ */
+/* The other ENO-type interpolations the paper runs beside WENO5-Z (Sec. 4.1 */
+/* gas-liquid Riemann problem, Table DropAdvectionIECResults, Shu-Osher and  */
+/* 2D Riemann problems): WENO5-JS (Jiang & Shu 1996), TENO5 and TENO6 (Fu,   */
+/* Hu & Adams 2016).  The paper cites them without restating them; these    */
+/* follow the cited definitions.  v[0..5] are the cells i-2..i+3 of a value */
+/* at the right face of cell i (TENO6 alone reads v[5]).                    */
+/* ------------------------------------------------------------------------ */
+
+/* Candidate polynomial of the stencil of n cells starting at offset o
+ * (cell i is [0,1], cell c is [c, c+1]) from its cell averages, taken as
+ * deviations from cell i (a constant changes neither the smoothness
+ * indicator nor the deviation of the value): a_k of p(x) = sum a_k x^k solve
+ * sum_k a_k int_c^{c+1} x^k dx = v_c - v_i.  The moment matrix depends on
+ * (o, n) alone; its inverse is formed once, by Gauss-Jordan elimination
+ * with partial pivoting, for every stencil inside i-2..i+3. */
+struct MomentInverses {
+  double inv[3][7][6][6];  /* [o + 2][n][row][col] */
+  MomentInverses() {
+    for (int o = -2; o <= 0; ++o)
+      for (int n = 1; n <= 6; ++n) {
+        if (o + n - 1 > 3) continue;
+        double A[6][12];
+        for (int r = 0; r < n; ++r) {
+          const double c = o + r;
+          for (int k = 0; k < n; ++k) A[r][k] = (std::pow(c + 1.0, k + 1) - std::pow(c, k + 1)) / (k + 1);
+          for (int k = 0; k < n; ++k) A[r][n + k] = r == k ? 1.0 : 0.0;
+        }
+        for (int col = 0; col < n; ++col) {
+          int piv = col;
+          for (int r = col + 1; r < n; ++r)
+            if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+          for (int k = 0; k < 2 * n; ++k) std::swap(A[piv][k], A[col][k]);
+          const double pv = A[col][col];
+          for (int k = 0; k < 2 * n; ++k) A[col][k] /= pv;
+          for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const double f = A[r][col];
+            for (int k = 0; k < 2 * n; ++k) A[r][k] -= f * A[col][k];
+          }
+        }
+        for (int r = 0; r < n; ++r)
+          for (int k = 0; k < n; ++k) inv[o + 2][n][r][k] = A[r][n + k];
+      }
+  }
+};
+
+template <class R>
+void candidate_poly(const R* v, int o, int n, R* a) {
+  static const MomentInverses M;
+  const double(*Ai)[6] = M.inv[o + 2][n];
+  for (int k = 0; k < n; ++k) {
+    R s(0.0);
+    for (int r = 0; r < n; ++r) s = s + Ai[k][r] * (v[2 + o + r] - v[2]);
+    a[k] = s;
+  }
+}
+
+/* Jiang-Shu smoothness indicator of a candidate polynomial on cell i:
+ * sum_{l=1}^{n-1} int_0^1 (d^l p / dx^l)^2 dx (unit cell width) */
+template <class R>
+R jiang_shu_beta(const R* a, int n) {
+  R beta(0.0);
+  for (int l = 1; l < n; ++l) {
+    R c[6];
+    int m = 0;
+    for (int k = l; k < n; ++k) {
+      double f = 1.0;
+      for (int j = 0; j < l; ++j) f *= (k - j);
+      c[m++] = f * a[k];  /* coefficient of x^(k-l) */
+    }
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) beta = beta + c[i] * c[j] / (double)(i + j + 1);
+  }
+  return beta;
+}
+
+/* value at x = 1 (the right face of cell i) */
+template <class R>
+R poly_at_one(const R& vi, const R* a, int n) {
+  R s = vi;
+  for (int k = 0; k < n; ++k) s = s + a[k];
+  return s;
+}
+
+/* WENO5-JS: the WENO5 candidates and indicators, alpha_k = d_k / (eps + beta_k)^2
+ * (reading: eps = 1e-6 and exponent 2, the values of Jiang & Shu) */
+template <class R>
+R weno5js(const R* v) {
+  const double eps = 1e-6;
+  R q0 = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0;
+  R q1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;
+  R q2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;
+  R t = v[0] - 2.0 * v[1] + v[2], s = v[0] - 4.0 * v[1] + 3.0 * v[2];
+  R b0 = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  t = v[1] - 2.0 * v[2] + v[3];
+  s = v[1] - v[3];
+  R b1 = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  t = v[2] - 2.0 * v[3] + v[4];
+  s = 3.0 * v[2] - 4.0 * v[3] + v[4];
+  R b2 = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  R a0 = 0.1 / ((eps + b0) * (eps + b0));
+  R a1 = 0.6 / ((eps + b1) * (eps + b1));
+  R a2 = 0.3 / ((eps + b2) * (eps + b2));
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+/* TENO selection: gamma_k = (C + tau / (beta_k + eps))^q with C = 1, q = 6,
+ * eps = 1e-40; chi_k = gamma_k / sum gamma; a candidate is kept when
+ * chi_k >= CT; the kept candidates combine with their optimal weights
+ * renormalized.  (Reading: chi_k is formed from (r_k / max r)^6, the same
+ * ratio, because r_k^6 overflows FP64 when a stencil is exactly flat beside
+ * a jump.) */
+template <class R>
+R teno_select(int K, const R* q, const R* beta, const double* d, const R& tau, double CT) {
+  const double eps = 1e-40;
+  R r[4];
+  double rmax = 0.0;
+  for (int k = 0; k < K; ++k) {
+    r[k] = 1.0 + tau / (beta[k] + eps);
+    rmax = std::max(rmax, val(r[k]));
+  }
+  double g[4], gs = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double x = val(r[k]) / rmax;
+    const double x2 = x * x;
+    g[k] = x2 * x2 * x2;
+    gs += g[k];
+  }
+  R num(0.0);
+  double den = 0.0;
+  for (int k = 0; k < K; ++k)
+    if (!(g[k] < CT * gs)) {
+      num = num + d[k] * q[k];
+      den += d[k];
+    }
+  return num / den;
+}
+
+/* TENO5: candidates central (i-1..i+1), left (i-2..i), right (i..i+2) with
+ * optimal weights (3/5, 1/10, 3/10); tau5 = |beta_left - beta_right|;
+ * reading: CT = 1e-5 */
+template <class R>
+R teno5(const R* v) {
+  const R ql = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0;
+  const R qc = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;
+  const R qr = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;
+  R t = v[0] - 2.0 * v[1] + v[2], s = v[0] - 4.0 * v[1] + 3.0 * v[2];
+  const R bl = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  t = v[1] - 2.0 * v[2] + v[3];
+  s = v[1] - v[3];
+  const R bc = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  t = v[2] - 2.0 * v[3] + v[4];
+  s = 3.0 * v[2] - 4.0 * v[3] + v[4];
+  const R br = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  const R q[3] = {qc, ql, qr}, beta[3] = {bc, bl, br};
+  const double d[3] = {0.6, 0.1, 0.3};
+  return teno_select(3, q, beta, d, fabs(bl - br), 1e-5);
+}
+
+/* TENO6: TENO5's three candidates plus the four-cell right candidate
+ * (i..i+3), optimal weights (9/20, 1/20, 3/10, 1/5) reproducing the six-cell
+ * interpolation; tau6 = |beta6 - (beta_left + beta_right + 4 beta_central) / 6|
+ * with beta6 the indicator of the six-cell polynomial (the combination that
+ * vanishes to O(dx^6) on smooth data); reading: CT = 1e-7.  The new
+ * candidate and both new indicators come from the definitions above. */
+template <class R>
+R teno6(const R* v) {
+  R a4[6], a6[6];
+  candidate_poly(v, 0, 4, a4);
+  candidate_poly(v, -2, 6, a6);
+  const R ql = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0;
+  const R qc = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;
+  const R qr = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;
+  const R q4 = poly_at_one(v[2], a4, 4);
+  R t = v[0] - 2.0 * v[1] + v[2], s = v[0] - 4.0 * v[1] + 3.0 * v[2];
+  const R bl = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  t = v[1] - 2.0 * v[2] + v[3];
+  s = v[1] - v[3];
+  const R bc = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  t = v[2] - 2.0 * v[3] + v[4];
+  s = 3.0 * v[2] - 4.0 * v[3] + v[4];
+  const R br = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  const R b4 = jiang_shu_beta(a4, 4);
+  const R b6 = jiang_shu_beta(a6, 6);
+  const R q[4] = {qc, ql, qr, q4}, beta[4] = {bc, bl, br, b4};
+  const double d[4] = {0.45, 0.05, 0.3, 0.2};
+  return teno_select(4, q, beta, d, fabs(b6 - (bl + br + 4.0 * bc) / 6.0), 1e-7);
+}
+
+/* the interpolation the model selects (ORC_RECON_*) */
+template <class R>
+R reconstruct(int kind, const R* v, double eps) {
+  switch (kind) {
+    case 1: return weno5js(v);
+    case 2: return teno5(v);
+    case 3: return teno6(v);
+    default: return weno5z(v[0], v[1], v[2], v[3], v[4], eps);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* characteristic matrices, Appendix A                                       */
 /* ------------------------------------------------------------------------ */
 /* Ordering.  W  = [T, Y_0..Y_{ns-2}, u_0..u_{D-1}, P]                        */
@@ -787,11 +988,14 @@ struct Solver {
           Wt[j][r] = s;
         }
       }
-      /* step 2: WENO5-Z of each characteristic variable, both sides */
+      /* step 2: ENO-type interpolation (WENO5-Z unless the model selects
+       * another) of each characteristic variable, both sides */
       R WtL[MAXC], WtR[MAXC];
       for (int r = 0; r < nc; ++r) {
-        WtL[r] = weno5z(Wt[0][r], Wt[1][r], Wt[2][r], Wt[3][r], Wt[4][r], p.weno_eps);
-        WtR[r] = weno5z(Wt[5][r], Wt[4][r], Wt[3][r], Wt[2][r], Wt[1][r], p.weno_eps);
+        const R sl[6] = {Wt[0][r], Wt[1][r], Wt[2][r], Wt[3][r], Wt[4][r], Wt[5][r]};
+        const R sr[6] = {Wt[5][r], Wt[4][r], Wt[3][r], Wt[2][r], Wt[1][r], Wt[0][r]};
+        WtL[r] = reconstruct(p.recon, sl, p.weno_eps);
+        WtR[r] = reconstruct(p.recon, sr, p.weno_eps);
       }
       /* step 3: back to physical space */
       R WL[MAXC], WR[MAXC];
@@ -818,22 +1022,38 @@ struct Solver {
       PR = WR[ns + D];
       /* the species left out of the projection, interpolated on its own */
       const int kl = ns - 1;
-      YL[kl] = weno5z(cc[0]->Y[kl], cc[1]->Y[kl], cc[2]->Y[kl], cc[3]->Y[kl], cc[4]->Y[kl], p.weno_eps);
-      YR[kl] = weno5z(cc[5]->Y[kl], cc[4]->Y[kl], cc[3]->Y[kl], cc[2]->Y[kl], cc[1]->Y[kl], p.weno_eps);
+      {
+        const R sl[6] = {cc[0]->Y[kl], cc[1]->Y[kl], cc[2]->Y[kl], cc[3]->Y[kl], cc[4]->Y[kl], cc[5]->Y[kl]};
+        const R sr[6] = {cc[5]->Y[kl], cc[4]->Y[kl], cc[3]->Y[kl], cc[2]->Y[kl], cc[1]->Y[kl], cc[0]->Y[kl]};
+        YL[kl] = reconstruct(p.recon, sl, p.weno_eps);
+        YR[kl] = reconstruct(p.recon, sr, p.weno_eps);
+      }
     } else {
       /* negative control: component-wise [rhoY, u, P] without projection;
        * T on the face then follows from rho, P, Y through NASG_T2 */
       R rYL[MAXS], rYR[MAXS];
+      auto both = [&](const R* s6, R& l, R& r) {
+        const R sr[6] = {s6[5], s6[4], s6[3], s6[2], s6[1], s6[0]};
+        l = reconstruct(p.recon, s6, p.weno_eps);
+        r = reconstruct(p.recon, sr, p.weno_eps);
+      };
       for (int k = 0; k < ns; ++k) {
-        rYL[k] = weno5z(cc[0]->rhoY[k], cc[1]->rhoY[k], cc[2]->rhoY[k], cc[3]->rhoY[k], cc[4]->rhoY[k], p.weno_eps);
-        rYR[k] = weno5z(cc[5]->rhoY[k], cc[4]->rhoY[k], cc[3]->rhoY[k], cc[2]->rhoY[k], cc[1]->rhoY[k], p.weno_eps);
+        const R s6[6] = {cc[0]->rhoY[k], cc[1]->rhoY[k], cc[2]->rhoY[k], cc[3]->rhoY[k], cc[4]->rhoY[k], cc[5]->rhoY[k]};
+        both(s6, rYL[k], rYR[k]);
       }
       for (int t = 0; t < 3; ++t) {
-        uL[t] = t < D ? weno5z(cc[0]->u[t], cc[1]->u[t], cc[2]->u[t], cc[3]->u[t], cc[4]->u[t], p.weno_eps) : R(0.0);
-        uR[t] = t < D ? weno5z(cc[5]->u[t], cc[4]->u[t], cc[3]->u[t], cc[2]->u[t], cc[1]->u[t], p.weno_eps) : R(0.0);
+        if (t < D) {
+          const R s6[6] = {cc[0]->u[t], cc[1]->u[t], cc[2]->u[t], cc[3]->u[t], cc[4]->u[t], cc[5]->u[t]};
+          both(s6, uL[t], uR[t]);
+        } else {
+          uL[t] = R(0.0);
+          uR[t] = R(0.0);
+        }
       }
-      PL = weno5z(cc[0]->P, cc[1]->P, cc[2]->P, cc[3]->P, cc[4]->P, p.weno_eps);
-      PR = weno5z(cc[5]->P, cc[4]->P, cc[3]->P, cc[2]->P, cc[1]->P, p.weno_eps);
+      {
+        const R s6[6] = {cc[0]->P, cc[1]->P, cc[2]->P, cc[3]->P, cc[4]->P, cc[5]->P};
+        both(s6, PL, PR);
+      }
       R rl(0.0), rr(0.0);
       for (int k = 0; k < ns; ++k) {
         rl = rl + rYL[k];
@@ -1240,6 +1460,15 @@ int orc_eos_forward(const orc_params* p, const double* Y, double P, double T, do
 }
 
 double orc_weno5z(const double* v, double eps) { return weno5z<double>(v[0], v[1], v[2], v[3], v[4], eps); }
+
+double orc_reconstruct(int kind, const double* v6, double eps) { return reconstruct<double>(kind, v6, eps); }
+
+void orc_candidate(const double* v6, int offset, int n, double* value, double* beta) {
+  double a[6];
+  candidate_poly<double>(v6, offset, n, a);
+  *value = poly_at_one<double>(v6[2], a, n);
+  *beta = jiang_shu_beta<double>(a, n);
+}
 
 int orc_char_matrices(const orc_params* p, int d, const double* Ubar, double* Sinv, double* S, double* scal) {
   double rho, a, al, be, X, rhoa;

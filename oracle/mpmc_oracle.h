@@ -70,6 +70,8 @@ typedef struct {
                         1: component-wise [rhoY, u, P] (negative control, test only) */
   int eos_iterative; /* 1: force the iterative p-T solve even when the closed form applies */
   int nthreads;      /* OpenMP threads, <= 0: library default */
+  int recon;         /* ENO-type interpolation: 0 WENO5-Z (the method's default),
+                        1 WENO5-JS, 2 TENO5, 3 TENO6 (Sec. 4.1's other schemes) */
 } orc_params;
 
 /* status codes */
@@ -106,6 +108,13 @@ int orc_eos_pt(const orc_params* p, const double* Y, double e, double v, double*
 /* forward EOS at (P, T, Y): out = [rho, e, a, alpha, beta, cp] */
 int orc_eos_forward(const orc_params* p, const double* Y, double P, double T, double* out);
 double orc_weno5z(const double* v5, double eps);
+/* the interpolation of kind 0..3 (see orc_params.recon) at the right face of
+ * cell i from the cells i-2..i+3 */
+double orc_reconstruct(int kind, const double* v6, double eps);
+/* candidate polynomial of the n cells starting at offset (relative to cell
+ * i = v6[2]) fitted to the cell averages: its value at the right face of
+ * cell i and its Jiang-Shu smoothness indicator on cell i */
+void orc_candidate(const double* v6, int offset, int n, double* value, double* beta);
 /* characteristic matrices of direction d at the conserved state Ubar:
  * Sinv, S dense nc x nc row-major, nc = ns + dim + 1; scal = [rho, a, alpha, beta, X, rho*a] */
 int orc_char_matrices(const orc_params* p, int d, const double* Ubar, double* Sinv, double* S, double* scal);

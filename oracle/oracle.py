@@ -65,7 +65,7 @@ class OrcParams(ctypes.Structure):
         ("pos_limiter", ctypes.c_int), ("cdi_eps", ctypes.c_double), ("cdi_gamma", ctypes.c_double),
         ("phi_min", ctypes.c_double), ("psi_delta", ctypes.c_double), ("cfl", ctypes.c_double),
         ("mu_liquid", ctypes.c_double), ("recon_basis", ctypes.c_int), ("eos_iterative", ctypes.c_int),
-        ("nthreads", ctypes.c_int),
+        ("nthreads", ctypes.c_int), ("recon", ctypes.c_int),
     ]
 
 
@@ -101,6 +101,10 @@ def _declare(L):
         f.restype = ctypes.c_int
     L.orc_weno5z.argtypes = [_dp, d]
     L.orc_weno5z.restype = d
+    L.orc_reconstruct.argtypes = [ctypes.c_int, _dp, d]
+    L.orc_reconstruct.restype = d
+    L.orc_candidate.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]
+    L.orc_candidate.restype = None
     L.orc_weno5z_jvp.argtypes = [_dp, _dp, d, _dp]
     L.orc_weno5z_jvp.restype = d
 
@@ -141,7 +145,7 @@ class Oracle:
         m = pr.model
         fields = dict(weno_eps=m.weno_eps, cdi=m.cdi, diffusion=m.diffusion, pos_limiter=m.pos_limiter,
                       cdi_eps=m.cdi_eps, cdi_gamma=m.cdi_gamma, phi_min=m.phi_min, psi_delta=m.psi_delta,
-                      cfl=m.cfl, mu_liquid=m.mu_liquid)
+                      cfl=m.cfl, mu_liquid=m.mu_liquid, recon=m.recon)
         fields.update(model_overrides)
         for k, v in fields.items():
             setattr(p, k, v)
@@ -271,6 +275,21 @@ class Oracle:
     def weno5z(self, v5, eps=None):
         v = np.ascontiguousarray(v5, dtype=np.float64)
         return self.lib.orc_weno5z(_ptr(v), self.p.weno_eps if eps is None else eps)
+
+    def reconstruct(self, kind, v6, eps=None):
+        """value at the right face of cell i from cells i-2..i+3 (kind: the
+        workloads RECON_* constants)"""
+        v = np.ascontiguousarray(v6, dtype=np.float64)
+        assert v.shape == (6,)
+        return self.lib.orc_reconstruct(int(kind), _ptr(v), self.p.weno_eps if eps is None else eps)
+
+    def candidate(self, v6, offset, n):
+        """(value at the right face of cell i, Jiang-Shu indicator) of the
+        polynomial fitted to the n cell averages starting at offset from cell i"""
+        v = np.ascontiguousarray(v6, dtype=np.float64)
+        val, beta = ctypes.c_double(), ctypes.c_double()
+        self.lib.orc_candidate(_ptr(v), int(offset), int(n), ctypes.byref(val), ctypes.byref(beta))
+        return val.value, beta.value
 
     def char_matrices(self, d, Ubar):
         nc = self.problem.ns + self.problem.dim + 1

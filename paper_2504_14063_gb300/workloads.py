@@ -64,6 +64,10 @@ WATER_NASG = Species("water", LIQUID, cv=4.185e3 / 1.0123, gamma=1.0123, q=-1.14
 AIR_TABLE = Species("air", GAS, cv=1.011e3 / 1.4, gamma=1.4, W=0.029, mu=1.81e-5, Sc=1.0)
 
 
+# ENO-type interpolations (Sec. 4.1 runs all four; WENO5-Z is the default)
+RECON_WENO5Z, RECON_WENO5JS, RECON_TENO5, RECON_TENO6 = 0, 1, 2, 3
+
+
 @dataclasses.dataclass
 class Model:
     weno_eps: float = 1e-40
@@ -76,6 +80,7 @@ class Model:
     psi_delta: float = 1e-100
     cfl: float = 0.5
     mu_liquid: float = 8.9e-4
+    recon: int = RECON_WENO5Z
 
 
 @dataclasses.dataclass
