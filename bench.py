@@ -287,6 +287,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--compare-steps", type=int, default=100)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-recon", action="store_true")
+    ap.add_argument("--recon-steps", type=int, default=5)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -400,6 +402,41 @@ def main():
                  "status": mstat}
         del ctxm, Um, A, B
 
+    # ---- Sec. 4.1's other ENO-type interpolations: the same FP64 step ------
+    recon = None
+    if not args.no_recon:
+        recon = {"note": "the FP64 SSP-RK3 step of the same workload with each interpolation, "
+                         "same timing (CUDA events per step, L2 flushed between steps)"}
+        for rname, rkind in (("WENO5JS", W.RECON_WENO5JS), ("TENO5", W.RECON_TENO5), ("TENO6", W.RECON_TENO6)):
+            pr_ = W.shock_bubble_2d(nx=1024, ny=512, seed=0)
+            pr_.model.recon = rkind
+            ctxr = mp.Context(pr_)
+            Ur = ctxr.init_state(torch.from_numpy(pr_.prim))
+            for _ in range(args.warmup):
+                ctxr.rk_step(Ur)
+            torch.cuda.synchronize()
+            evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.recon_steps)]
+            ctxr.set_profiling(True)
+            for k in range(args.recon_steps):
+                flush.fill_(k & 0xFF)
+                evr[k][0].record()
+                ctxr.rk_step(Ur)
+                evr[k][1].record()
+            torch.cuda.synchronize()
+            ctxr.set_profiling(False)
+            rprof = ctxr.profile(reset=True)
+            tr = sum(a.elapsed_time(b) for a, b in evr) / 1e3
+            if world > 1:
+                t = torch.tensor([tr], device="cuda", dtype=torch.float64)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                tr = float(t.item())
+            vr = world * pr_.ncells * args.recon_steps / tr
+            recon[rname] = {"value": vr, "unit": UNIT, "ms_per_step": 1e3 * tr / args.recon_steps,
+                            "vs_weno5z": vr / value, "steps": args.recon_steps,
+                            "face_ms_per_step": rprof["face"][0] / args.recon_steps, "status": ctxr.status()}
+            del ctxr, Ur
+
     adjoint = None
     if not args.no_adjoint and rank == 0:
         adjoint = adjoint_section(mp, torch, nsteps=args.adjoint_steps)
@@ -437,6 +474,8 @@ def main():
         }
         if mixed is not None:
             line["mixed"] = mixed
+        if recon is not None:
+            line["interpolations"] = recon
         if adjoint is not None:
             line["adjoint"] = adjoint
         if world == 1 and not args.no_cpu_baseline:

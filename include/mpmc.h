@@ -61,6 +61,15 @@ extern "C" {
 #define MPMC_BC_ZEROGRAD 2 /* copy of the boundary cell */
 #define MPMC_BC_INFLOW 3   /* Dirichlet: the fixed primitive state mpmc_grid.inflow */
 
+/* ENO-type interpolation of the face states (Sec. 3.1.3; Sec. 4.1 runs all
+ * four).  WENO5-Z (Borges et al. 2008) is the method's; the others follow
+ * their cited definitions (Jiang & Shu 1996; Fu, Hu & Adams 2016) and are
+ * available on FP64 contexts without the adjoint. */
+#define MPMC_RECON_WENO5Z 0
+#define MPMC_RECON_WENO5JS 1 /* eps 1e-6, exponent 2 */
+#define MPMC_RECON_TENO5 2   /* C = 1, q = 6, CT = 1e-5 */
+#define MPMC_RECON_TENO6 3   /* C = 1, q = 6, CT = 1e-7, six-cell stencil i-2..i+3 */
+
 /* precision of the hot path */
 #define MPMC_FP64 0
 #define MPMC_MIXED 1 /* reconstruction, fluxes, diffusion in FP32; EOS inversion,
@@ -109,6 +118,9 @@ typedef struct {
   double cfl;       /* 0.5 */
   double mu_liquid; /* liquid-phase viscosity [Pa s] */
   int precision;    /* MPMC_FP64 or MPMC_MIXED */
+  int recon;        /* MPMC_RECON_*; 0 (WENO5-Z) is the default.  Another value
+                       needs an FP64 context (MPMC_INVALID_ARG otherwise, also
+                       from mpmc_rhs_noalloc); the adjoint entries reject it */
 } mpmc_model;
 
 /* One SSP-RK stage: U^(k+1) = rk0 U^n + rk1 U^(k) + rk2 dt L(U^(k)).

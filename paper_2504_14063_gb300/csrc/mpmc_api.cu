@@ -192,6 +192,9 @@ extern "C" int mpmc_create(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_m
     case 2: c->aops = adj_ops_d2(ns); break;
     default: c->aops = adj_ops_d3(ns); break;
   }
+  if (P.recon == MPMC_RECON_WENO5JS) c->ops.face = face_fp64_weno5js(D, ns);
+  else if (P.recon == MPMC_RECON_TENO5) c->ops.face = face_fp64_teno5(D, ns);
+  else if (P.recon == MPMC_RECON_TENO6) c->ops.face = face_fp64_teno6(D, ns);
   if (!c->ops.face || !c->aops.face) {
     delete c;
     return MPMC_INVALID_ARG;
@@ -421,6 +424,8 @@ extern "C" int mpmc_dt_gamma(mpmc_ctx* c, const double* U, double* out_dev) {
 // discrete adjoint (FP64 contexts)
 static int ensure_adjoint(mpmc_ctx* c) {
   if (c->precision != MPMC_FP64) return fail(c, MPMC_INVALID_ARG, "adjoint: needs an FP64 context");
+  if (c->P.recon != MPMC_RECON_WENO5Z)
+    return fail(c, MPMC_INVALID_ARG, "adjoint: the reverse kernels differentiate WENO5-Z only");
   const KParams& P = c->P;
   int rc = MPMC_OK;
   const size_t st_bytes = (size_t)P.nv * P.ncell * sizeof(double);

@@ -38,6 +38,7 @@ struct KParams {
   double wilke[MAXS][MAXS];  // (W_i / W_j) Phi_ij of Wilke's rule (gas species)
   double weno_eps;
   int cdi, diffusion, pos_limiter, two_phase, has_inflow;
+  int recon;  // MPMC_RECON_* (the face kernels take it as a template parameter)
   int has_b, has_q;  // some species has a nonzero NASG covolume b / reference energy q
   double cdi_eps, cdi_gamma, phi_min, psi_delta, cfl, mu_liquid, sharp0;
   // primitive cache: field f of cell c at Wc[f * wstride + c]; slot ncell
@@ -457,6 +458,117 @@ __device__ __forceinline__ double weno5z(double v0, double v1, double v2, double
   const double a1 = 0.6 * (c1 + tau) * c0 * c2;
   const double a2 = 0.3 * (c2 + tau) * c0 * c1;
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// ---------------------------------------------------------------------------
+// The other ENO-type interpolations that Sec. 4.1 runs beside WENO5-Z:
+// WENO5-JS (Jiang & Shu 1996) and TENO5 / TENO6 (Fu, Hu & Adams 2016), as
+// those works define them (the paper cites them).  Value at the right face of
+// cell i from the cells i-2..i+3 (v5 is read by TENO6 alone).  Readings:
+// WENO5-JS eps = 1e-6, exponent 2; TENO C = 1, q = 6, eps = 1e-40,
+// CT = 1e-5 (TENO5) / 1e-7 (TENO6).
+enum { RC_WENO5Z = 0, RC_WENO5JS = 1, RC_TENO5 = 2, RC_TENO6 = 3 };
+
+// the three-cell candidates (left i-2..i, central i-1..i+1, right i..i+2)
+// and their Jiang-Shu indicators
+struct Eno3 {
+  double ql, qc, qr, bl, bc, br;
+};
+
+__device__ __forceinline__ Eno3 eno3(double v0, double v1, double v2, double v3, double v4) {
+  Eno3 e;
+  e.ql = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
+  e.qc = (-v1 + 5.0 * v2 + 2.0 * v3) * (1.0 / 6.0);
+  e.qr = (2.0 * v2 + 5.0 * v3 - v4) * (1.0 / 6.0);
+  double t = v0 - 2.0 * v1 + v2, s = v0 - 4.0 * v1 + 3.0 * v2;
+  e.bl = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  t = v1 - 2.0 * v2 + v3;
+  s = v1 - v3;
+  e.bc = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  t = v2 - 2.0 * v3 + v4;
+  s = 3.0 * v2 - 4.0 * v3 + v4;
+  e.br = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  return e;
+}
+
+__device__ __forceinline__ double weno5js(double v0, double v1, double v2, double v3, double v4) {
+  const Eno3 e = eno3(v0, v1, v2, v3, v4);
+  constexpr double eps = 1e-6;
+  const double il = 1.0 / (eps + e.bl), ic = 1.0 / (eps + e.bc), ir = 1.0 / (eps + e.br);
+  const double al = 0.1 * il * il, ac = 0.6 * ic * ic, ar = 0.3 * ir * ir;
+  return (al * e.ql + ac * e.qc + ar * e.qr) / (al + ac + ar);
+}
+
+// TENO selection: r_k = C + tau / (beta_k + eps); chi_k = r_k^q / sum r^q,
+// formed from r_k / max r (r_k^6 overflows beside a large jump); candidates
+// with chi_k < CT are cut off, the rest combine with their optimal weights
+template <int K>
+__device__ __forceinline__ double teno_select(const double* q, const double* b, const double* dk, double tau,
+                                              double CT) {
+  double r[K], rmax = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    r[k] = 1.0 + tau / (b[k] + 1e-40);
+    rmax = fmax(rmax, r[k]);
+  }
+  const double irm = 1.0 / rmax;
+  double g[K], gs = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double x = r[k] * irm, x2 = x * x;
+    g[k] = x2 * x2 * x2;
+    gs += g[k];
+  }
+  double num = 0.0, den = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (!(g[k] < CT * gs)) {
+      num += dk[k] * q[k];
+      den += dk[k];
+    }
+  return num / den;
+}
+
+// TENO5: optimal weights (3/5, 1/10, 3/10) for (central, left, right),
+// tau5 = |beta_left - beta_right|
+__device__ __forceinline__ double teno5(double v0, double v1, double v2, double v3, double v4) {
+  const Eno3 e = eno3(v0, v1, v2, v3, v4);
+  const double q[3] = {e.qc, e.ql, e.qr}, b[3] = {e.bc, e.bl, e.br}, dk[3] = {0.6, 0.1, 0.3};
+  return teno_select<3>(q, b, dk, fabs(e.bl - e.br), 1e-5);
+}
+
+// TENO6: adds the four-cell candidate i..i+3; optimal weights
+// (9/20, 1/20, 3/10, 1/5) reproduce the six-cell interpolation;
+// tau6 = |beta6 - (beta_left + beta_right + 4 beta_central) / 6|.  The four-
+// and six-cell Jiang-Shu indicators are written as positive multiples of
+// squared zero-sum combinations (exact rational coefficients), evaluated on
+// deviations from cell i.
+__device__ __forceinline__ double teno6(double v0, double v1, double v2, double v3, double v4, double v5) {
+  const Eno3 e = eno3(v0, v1, v2, v3, v4);
+  const double q4 = (3.0 * v2 + 13.0 * v3 - 5.0 * v4 + v5) * (1.0 / 12.0);
+  const double e0 = v0 - v2, e1 = v1 - v2, e3 = v3 - v2, e4 = v4 - v2, e5 = v5 - v2;
+  double s = 18.0 * e3 - 9.0 * e4 + 2.0 * e5, t = -5.0 * e3 + 4.0 * e4 - e5, u = 3.0 * e3 - 3.0 * e4 + e5;
+  const double b4 = (1.0 / 36.0) * s * s + (13.0 / 12.0) * t * t + (781.0 / 720.0) * u * u;
+  const double c1 = 3.0 * e0 - 30.0 * e1 + 60.0 * e3 - 15.0 * e4 + 2.0 * e5;
+  const double c2 = -11.0 * e0 + 174.0 * e1 + 174.0 * e3 - 11.0 * e4;
+  const double c3 = -16315.0 * e0 - 16831.0 * e1 - 230474.0 * e3 + 115237.0 * e4 - 16487.0 * e5;
+  const double c4 = e0 - 4.0 * e1 - 4.0 * e3 + e4;
+  const double c5 = -e0 + 5.0 * e1 + 10.0 * e3 - 5.0 * e4 + e5;
+  const double b6 = (1.0 / 3600.0) * c1 * c1 + (1.0 / 15600.0) * c2 * c2 + (1.0 / 3967729920.0) * c3 * c3 +
+                    (1421461.0 / 1310400.0) * c4 * c4 + (21520059541.0 / 19838649600.0) * c5 * c5;
+  const double q[4] = {e.qc, e.ql, e.qr, q4}, b[4] = {e.bc, e.bl, e.br, b4}, dk[4] = {0.45, 0.05, 0.3, 0.2};
+  return teno_select<4>(q, b, dk, fabs(b6 - (e.bl + e.br + 4.0 * e.bc) * (1.0 / 6.0)), 1e-7);
+}
+
+// the interpolation of kind RC on the stencil v0..v5 (left side: cells
+// i-2..i+3; right side: the same cells mirrored)
+template <int RC>
+__device__ __forceinline__ double recon(double v0, double v1, double v2, double v3, double v4, double v5,
+                                        double eps) {
+  if constexpr (RC == RC_WENO5JS) return weno5js(v0, v1, v2, v3, v4);
+  else if constexpr (RC == RC_TENO5) return teno5(v0, v1, v2, v3, v4);
+  else if constexpr (RC == RC_TENO6) return teno6(v0, v1, v2, v3, v4, v5);
+  else return weno5z(v0, v1, v2, v3, v4, eps);
 }
 
 // ---------------------------------------------------------------------------

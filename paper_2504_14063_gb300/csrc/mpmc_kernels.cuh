@@ -204,8 +204,9 @@ __global__ void __launch_bounds__(CELL_THREADS)
 
 // ---------------------------------------------------------------------------
 // DIR: the face direction, a template parameter so that every array indexed
-// by it is indexed by a constant (registers, not the stack)
-template <int NS, int D, int DIR>
+// by it is indexed by a constant (registers, not the stack).  RC: the
+// ENO-type interpolation (RC_WENO5Z, the method's, or one of Sec. 4.1's others)
+template <int NS, int D, int DIR, int RC>
 __global__ void __launch_bounds__(FACE_THREADS)
     k_face(const KParams P, const double* __restrict__ Wc, const double* __restrict__ Un,
            const double* __restrict__ Uk, const double* __restrict__ Uin, const double* __restrict__ scal,
@@ -254,7 +255,8 @@ __global__ void __launch_bounds__(FACE_THREADS)
     ic = 1.0 / c;
   }
 
-  // steps 2-3: project, WENO5-Z both sides, back to physical space
+  // steps 2-3: project, interpolate both sides (WENO5-Z unless RC says
+  // otherwise), back to physical space
   double YL[NS], YR[NS], uL[3] = {0.0, 0.0, 0.0}, uR[3] = {0.0, 0.0, 0.0}, PL, PR, TL, TR;
   const double eps = P.weno_eps;
   {
@@ -268,12 +270,12 @@ __global__ void __launch_bounds__(FACE_THREADS)
       w5[j] = (0.5 * c) * un + 0.5 * p;
       w6[j] = (-0.5 * c) * un + 0.5 * p;
     }
-    const double w1L = weno5z(w1[0], w1[1], w1[2], w1[3], w1[4], eps);
-    const double w1R = weno5z(w1[5], w1[4], w1[3], w1[2], w1[1], eps);
-    const double w5L = weno5z(w5[0], w5[1], w5[2], w5[3], w5[4], eps);
-    const double w5R = weno5z(w5[5], w5[4], w5[3], w5[2], w5[1], eps);
-    const double w6L = weno5z(w6[0], w6[1], w6[2], w6[3], w6[4], eps);
-    const double w6R = weno5z(w6[5], w6[4], w6[3], w6[2], w6[1], eps);
+    const double w1L = recon<RC>(w1[0], w1[1], w1[2], w1[3], w1[4], w1[5], eps);
+    const double w1R = recon<RC>(w1[5], w1[4], w1[3], w1[2], w1[1], w1[0], eps);
+    const double w5L = recon<RC>(w5[0], w5[1], w5[2], w5[3], w5[4], w5[5], eps);
+    const double w5R = recon<RC>(w5[5], w5[4], w5[3], w5[2], w5[1], w5[0], eps);
+    const double w6L = recon<RC>(w6[0], w6[1], w6[2], w6[3], w6[4], w6[5], eps);
+    const double w6R = recon<RC>(w6[5], w6[4], w6[3], w6[2], w6[1], w6[0], eps);
     TL = w1L + X * w5L + X * w6L;
     TR = w1R + X * w5R + X * w6R;
     uL[d] = ic * w5L + (-ic) * w6L;
@@ -286,8 +288,8 @@ __global__ void __launch_bounds__(FACE_THREADS)
     double y[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) y[j] = wget(P, Wc, P.wY + k, cr[j]);
-    YL[k] = weno5z(y[0], y[1], y[2], y[3], y[4], eps);
-    YR[k] = weno5z(y[5], y[4], y[3], y[2], y[1], eps);
+    YL[k] = recon<RC>(y[0], y[1], y[2], y[3], y[4], y[5], eps);
+    YR[k] = recon<RC>(y[5], y[4], y[3], y[2], y[1], y[0], eps);
   }
 #pragma unroll
   for (int t = 0; t < D; ++t) {
@@ -295,8 +297,8 @@ __global__ void __launch_bounds__(FACE_THREADS)
     double y[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) y[j] = wget(P, Wc, P.wU + t, cr[j]) * sgn_flip(cr[j].flip, t);
-    uL[t] = weno5z(y[0], y[1], y[2], y[3], y[4], eps);
-    uR[t] = weno5z(y[5], y[4], y[3], y[2], y[1], eps);
+    uL[t] = recon<RC>(y[0], y[1], y[2], y[3], y[4], y[5], eps);
+    uR[t] = recon<RC>(y[5], y[4], y[3], y[2], y[1], y[0], eps);
   }
 
   // cell values of the two face neighbours
@@ -523,6 +525,46 @@ __global__ void __launch_bounds__(CELL_THREADS)
 // ---------------------------------------------------------------------------
 inline unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// the FP64 face pass of one direction with interpolation RC
+template <int NS, int D, int RC>
+struct FaceImpl {
+  static void face(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* Un, const double* Uk,
+                   const double* Uin, const double* scal, double rk0, double rk1, double rk2, double* F,
+                   uint32_t* flags, unsigned long long* stats) {
+    long long nf = 1;
+    for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
+    const unsigned nb = nblocks(nf, FACE_THREADS);
+    if (d == 0)
+      k_face<NS, D, 0, RC><<<nb, FACE_THREADS, 0, s>>>(P, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags, stats);
+    else if (d == 1)
+      k_face<NS, D, (D > 1 ? 1 : 0), RC><<<nb, FACE_THREADS, 0, s>>>(P, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F,
+                                                                     flags, stats);
+    else
+      k_face<NS, D, (D > 2 ? 2 : 0), RC><<<nb, FACE_THREADS, 0, s>>>(P, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F,
+                                                                     flags, stats);
+  }
+};
+
+// the face pass of interpolation RC for (dimension, species count), or null
+template <int RC>
+FaceFn face_fp64(int dim, int ns) {
+  switch (dim * 8 + ns) {
+    case 9: return &FaceImpl<1, 1, RC>::face;
+    case 10: return &FaceImpl<2, 1, RC>::face;
+    case 11: return &FaceImpl<3, 1, RC>::face;
+    case 12: return &FaceImpl<4, 1, RC>::face;
+    case 17: return &FaceImpl<1, 2, RC>::face;
+    case 18: return &FaceImpl<2, 2, RC>::face;
+    case 19: return &FaceImpl<3, 2, RC>::face;
+    case 20: return &FaceImpl<4, 2, RC>::face;
+    case 25: return &FaceImpl<1, 3, RC>::face;
+    case 26: return &FaceImpl<2, 3, RC>::face;
+    case 27: return &FaceImpl<3, 3, RC>::face;
+    case 28: return &FaceImpl<4, 3, RC>::face;
+    default: return nullptr;
+  }
+}
+
 template <int NS, int D>
 struct Impl {
   static void init(const KParams& P, cudaStream_t s, const double* prim, double* U, long long n) {
@@ -536,17 +578,7 @@ struct Impl {
   static void face(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* Un, const double* Uk,
                    const double* Uin, const double* scal, double rk0, double rk1, double rk2, double* F,
                    uint32_t* flags, unsigned long long* stats) {
-    long long nf = 1;
-    for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
-    const unsigned nb = nblocks(nf, FACE_THREADS);
-    if (d == 0)
-      k_face<NS, D, 0><<<nb, FACE_THREADS, 0, s>>>(P, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags, stats);
-    else if (d == 1)
-      k_face<NS, D, (D > 1 ? 1 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags,
-                                                                 stats);
-    else
-      k_face<NS, D, (D > 2 ? 2 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags,
-                                                                 stats);
+    FaceImpl<NS, D, RC_WENO5Z>::face(P, s, d, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags, stats);
   }
   static void update(const KParams& P, cudaStream_t s, const double* Un, const double* Uk, double* const* F,
                      const double* scal, double rk0, double rk1, double rk2, double* Uout, double* dUdt,

@@ -61,9 +61,9 @@ __global__ void k_put(Inflow in, double* dst, int n) {
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Kernel parameters as mpmc_create sets them up (FP64 only)
+// Kernel parameters as mpmc_create sets them up (FP64, WENO5-Z only)
 int params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_model* m, KParams& P) {
-  if (m && m->precision != MPMC_FP64) return MPMC_INVALID_ARG;
+  if (m && (m->precision != MPMC_FP64 || m->recon != MPMC_RECON_WENO5Z)) return MPMC_INVALID_ARG;
   return build_params(g, eos, m, P);
 }
 

@@ -32,6 +32,14 @@ struct AdjOps {
   void (*init)(const KParams&, cudaStream_t, const double* prim, const double* lamU, double* lprim, long long n);
 };
 
+using FaceFn = decltype(Ops::face);
+// FP64 face passes with Sec. 4.1's other ENO-type interpolations, for
+// (dimension, species count), null if none: defined in
+// mpmc_recon_{weno5js,teno5,teno6}.cu
+FaceFn face_fp64_weno5js(int dim, int ns);
+FaceFn face_fp64_teno5(int dim, int ns);
+FaceFn face_fp64_teno6(int dim, int ns);
+
 // per-dimension tables, defined in mpmc_kernels_d{1,2,3}.cu (FP64) and
 // mpmc_mixed_d{1,2,3}.cu (mixed precision; init is the FP64 one)
 Ops ops_fp64_d1(int ns);

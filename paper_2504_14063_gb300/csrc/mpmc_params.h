@@ -19,6 +19,8 @@ inline int build_params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_mode
   if (g->dim < 1 || g->dim > 3 || eos->n_species < 1 || eos->n_species > MPMC_MAXS || !(g->dx > 0.0))
     return MPMC_INVALID_ARG;
   if (m->precision != MPMC_FP64 && m->precision != MPMC_MIXED) return MPMC_INVALID_ARG;
+  if (m->recon < MPMC_RECON_WENO5Z || m->recon > MPMC_RECON_TENO6) return MPMC_INVALID_ARG;
+  if (m->recon != MPMC_RECON_WENO5Z && m->precision != MPMC_FP64) return MPMC_INVALID_ARG;
   for (int d = 0; d < 3; ++d) {
     if (d < g->dim && g->n[d] < 3) return MPMC_INVALID_ARG;
     if (d >= g->dim && g->n[d] != 1) return MPMC_INVALID_ARG;
@@ -82,6 +84,7 @@ inline int build_params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_mode
   P.cdi = m->cdi ? 1 : 0;
   P.diffusion = m->diffusion ? 1 : 0;
   P.pos_limiter = m->pos_limiter ? 1 : 0;
+  P.recon = m->recon;
   P.cdi_eps = m->cdi_eps > 0.0 ? m->cdi_eps : g->dx;
   P.cdi_gamma = m->cdi_gamma;
   P.phi_min = m->phi_min;

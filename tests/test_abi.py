@@ -46,8 +46,8 @@ def test_struct_layouts_match_header(tmp_path):
 int main(void) {{
   printf("%zu %zu %zu %zu %zu\\n", sizeof(mpmc_grid), sizeof(mpmc_eos), sizeof(mpmc_model),
          sizeof(mpmc_stage), sizeof(mpmc_stats));
-  printf("%zu %zu %zu %zu\\n", offsetof(mpmc_grid, inflow), offsetof(mpmc_eos, Sc),
-         offsetof(mpmc_model, precision), offsetof(mpmc_stage, Gamma));
+  printf("%zu %zu %zu %zu %zu\\n", offsetof(mpmc_grid, inflow), offsetof(mpmc_eos, Sc),
+         offsetof(mpmc_model, precision), offsetof(mpmc_model, recon), offsetof(mpmc_stage, Gamma));
   return 0;
 }}
 """)
@@ -57,7 +57,8 @@ int main(void) {{
     sizes = [int(x) for x in out[:5]]
     offs = [int(x) for x in out[5:]]
     assert sizes == [ctypes.sizeof(t) for t in (b.Grid, b.Eos, b.ModelC, b.StageC, b.StatsC)]
-    assert offs == [b.Grid.inflow.offset, b.Eos.Sc.offset, b.ModelC.precision.offset, b.StageC.Gamma.offset]
+    assert offs == [b.Grid.inflow.offset, b.Eos.Sc.offset, b.ModelC.precision.offset, b.ModelC.recon.offset,
+                    b.StageC.Gamma.offset]
 
 
 def test_invalid_arguments_are_rejected_without_a_gpu(lib):
@@ -77,5 +78,12 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     g.n[0] = 2 ** 31 - 1
     assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
     g.n[0] = 2 ** 31 - 2     # 2^31 - 2 cells + the inflow slot, 2^31 - 1 faces
+    assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
+    assert h.value is None
+    # interpolations: an unknown kind; TENO6 on a mixed-precision context
+    g.n[0] = 16
+    m.recon = 4
+    assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
+    m.recon, m.precision = 3, b.MIXED
     assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
     assert h.value is None
