@@ -407,8 +407,9 @@ def main():
     if not args.no_recon:
         recon = {"note": "the FP64 SSP-RK3 step of the same workload with each interpolation, "
                          "same timing (CUDA events per step, L2 flushed between steps)"}
+        from paper_2504_14063_gb300 import workloads as W
         for rname, rkind in (("WENO5JS", W.RECON_WENO5JS), ("TENO5", W.RECON_TENO5), ("TENO6", W.RECON_TENO6)):
-            pr_ = W.shock_bubble_2d(nx=1024, ny=512, seed=0)
+            pr_ = workload()
             pr_.model.recon = rkind
             ctxr = mp.Context(pr_)
             Ur = ctxr.init_state(torch.from_numpy(pr_.prim))
