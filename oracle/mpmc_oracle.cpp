@@ -215,8 +215,9 @@ struct Cell {
   /* interface regularization: phase volume fraction, psi, (Y^c/Y_p) rho_p, h_p rho_p */
   R phi[2], psi, yrho[MAXS], hrho[2];
   bool present[2];
-  /* diffusion: X^c/X_p, W^c D^c_p / W_p, h^c; mixture viscosity */
-  R xr[MAXS], B[MAXS], h[MAXS], mu;
+  /* diffusion: X^c/X_p, W^c D^c_p / W_p, h^c; mixture viscosity and heat
+   * conductivity */
+  R xr[MAXS], B[MAXS], h[MAXS], mu, lam;
   int status;
 };
 
@@ -332,6 +333,18 @@ void cell_from_conserved(const orc_params& p, int D, const R* U, Cell<R>& c) {
   }
   /* mixture viscosity mu = sum_p phi_p mu_p (Sec. 2.2.2) */
   c.mu = c.phi[0] * mu_p[0] + c.phi[1] * mu_p[1];
+  /* mixture heat conductivity lambda = sum_p phi_p lambda_p: constant in the
+   * liquid, lambda_g = (mu_g / Pr) sum_{c in gas} (Y^c / Y_g) Cp^c (Sec. 2.2.2) */
+  {
+    R Yg(0.0), cpY(0.0);
+    for (int k = 0; k < ns; ++k)
+      if (p.phase[k] == 1) {
+        Yg = Yg + c.Y[k];
+        cpY = cpY + c.Y[k] * Cp(p, k);
+      }
+    R lam_g = val(Yg) >= 1e-300 ? mu_p[1] / p.prandtl * (cpY / Yg) : R(0.0);
+    c.lam = c.phi[0] * p.lambda_liquid + c.phi[1] * lam_g;
+  }
 
   /* species diffusion ingredients (Eq. SpeciesMassDiffusion, third form):
    *   X^c/X_p = (Y^c/W^c) / sum_{j in p} Y^j/W^j,
@@ -1222,6 +1235,40 @@ struct Solver {
       }
       F[ns + D] = F[ns + D] + Jh;
     }
+
+    /* viscous stress and heat conduction (Eq. DiffusionTerms and the stress
+     * tensor and heat flux of Sec. 2.1), second-order central: face values
+     * are the averages of the two cells; the normal derivative is
+     * (q_{i+1} - q_i)/dx, a tangential one the average of the two cells'
+     * central differences.  Reading: the energy row carries the physical
+     * -u.tau + q (the printed row has the opposite sign to the printed
+     * momentum rows -tau); q's enthalpy part is the diffusion block above. */
+    if (p.viscous) {
+      R gu[3][3];  /* gu[i][j] = d u_i / d x_j on the face */
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) gu[i][j] = R(0.0);
+      for (int i = 0; i < D; ++i) gu[i][d] = (cj.u[i] - ci.u[i]) / p.dx;
+      for (int t = 0; t < D; ++t) {
+        if (t == d) continue;
+        const long sT = G.stride(t);
+        const Cell<R>& ip = cells[(size_t)((long)c0 + sT)];
+        const Cell<R>& im = cells[(size_t)((long)c0 - sT)];
+        const Cell<R>& jp = cells[(size_t)((long)c1 + sT)];
+        const Cell<R>& jm = cells[(size_t)((long)c1 - sT)];
+        for (int i = 0; i < D; ++i)
+          gu[i][t] = 0.5 * ((ip.u[i] - im.u[i]) / (2.0 * p.dx) + (jp.u[i] - jm.u[i]) / (2.0 * p.dx));
+      }
+      R div(0.0);
+      for (int k = 0; k < D; ++k) div = div + gu[k][k];
+      const R mub = 0.5 * (ci.mu + cj.mu), lamb = 0.5 * (ci.lam + cj.lam);
+      R work(0.0);
+      for (int i = 0; i < D; ++i) {
+        R tau = mub * (gu[i][d] + gu[d][i] - (i == d ? (2.0 / 3.0) * div : R(0.0)));
+        F[ns + i] = F[ns + i] - tau;
+        work = work + 0.5 * (ci.u[i] + cj.u[i]) * tau;
+      }
+      F[ns + D] = F[ns + D] - work - lamb * (cj.T - ci.T) / p.dx;
+    }
     return flags;
   }
 
@@ -1321,7 +1368,14 @@ struct Solver {
             smax = std::max(smax, (ud + val(c.a)) / p.dx);
             gmax = std::max(gmax, ud);
           }
-          if (p.diffusion) smax = std::max(smax, 4.0 * val(c.mu) / val(c.rho) / (p.dx * p.dx));
+          if (p.diffusion || p.viscous) smax = std::max(smax, 4.0 * val(c.mu) / val(c.rho) / (p.dx * p.dx));
+          if (p.viscous) {
+            /* reading: the conduction limit with the thermal diffusivity
+             * lambda / (rho cv) */
+            double cv = 0.0;
+            for (int k = 0; k < ns; ++k) cv += val(c.Y[k]) * p.cv[k];
+            smax = std::max(smax, 4.0 * val(c.lam) / (val(c.rho) * cv) / (p.dx * p.dx));
+          }
         }
     dt = p.cfl / smax;
     Gamma = p.cdi_gamma > 0.0 ? p.cdi_gamma : gmax;

@@ -72,6 +72,9 @@ typedef struct {
   int nthreads;      /* OpenMP threads, <= 0: library default */
   int recon;         /* ENO-type interpolation: 0 WENO5-Z (the method's default),
                         1 WENO5-JS, 2 TENO5, 3 TENO6 (Sec. 4.1's other schemes) */
+  int viscous;       /* viscous stress and heat conduction on/off */
+  double prandtl;    /* gas-phase Prandtl number (lambda_g = mu_g cp_g / Pr) */
+  double lambda_liquid; /* liquid-phase heat conductivity [W/(m K)] */
 } orc_params;
 
 /* status codes */

@@ -65,7 +65,8 @@ class OrcParams(ctypes.Structure):
         ("pos_limiter", ctypes.c_int), ("cdi_eps", ctypes.c_double), ("cdi_gamma", ctypes.c_double),
         ("phi_min", ctypes.c_double), ("psi_delta", ctypes.c_double), ("cfl", ctypes.c_double),
         ("mu_liquid", ctypes.c_double), ("recon_basis", ctypes.c_int), ("eos_iterative", ctypes.c_int),
-        ("nthreads", ctypes.c_int), ("recon", ctypes.c_int),
+        ("nthreads", ctypes.c_int), ("recon", ctypes.c_int), ("viscous", ctypes.c_int),
+        ("prandtl", ctypes.c_double), ("lambda_liquid", ctypes.c_double),
     ]
 
 
@@ -145,7 +146,8 @@ class Oracle:
         m = pr.model
         fields = dict(weno_eps=m.weno_eps, cdi=m.cdi, diffusion=m.diffusion, pos_limiter=m.pos_limiter,
                       cdi_eps=m.cdi_eps, cdi_gamma=m.cdi_gamma, phi_min=m.phi_min, psi_delta=m.psi_delta,
-                      cfl=m.cfl, mu_liquid=m.mu_liquid, recon=m.recon)
+                      cfl=m.cfl, mu_liquid=m.mu_liquid, recon=m.recon, viscous=m.viscous,
+                      prandtl=m.prandtl, lambda_liquid=m.lambda_liquid)
         fields.update(model_overrides)
         for k, v in fields.items():
             setattr(p, k, v)

@@ -81,6 +81,9 @@ class Model:
     cfl: float = 0.5
     mu_liquid: float = 8.9e-4
     recon: int = RECON_WENO5Z
+    viscous: int = 0              # viscous stress and heat conduction
+    prandtl: float = 0.72         # gas-phase Prandtl number
+    lambda_liquid: float = 0.6    # liquid heat conductivity [W/(m K)]
 
 
 @dataclasses.dataclass
