@@ -121,6 +121,13 @@ typedef struct {
   int recon;        /* MPMC_RECON_*; 0 (WENO5-Z) is the default.  Another value
                        needs an FP64 context (MPMC_INVALID_ARG otherwise, also
                        from mpmc_rhs_noalloc); the adjoint entries reject it */
+  int viscous;      /* viscous stress and heat conduction (Eq. DiffusionTerms:
+                       tau = mu (grad u + grad u^T - 2/3 div u I),
+                       q = -lambda grad T + sum J h), second-order central on
+                       the faces; FP64 contexts only, not in the adjoint */
+  double prandtl;   /* gas-phase Prandtl number: lambda_g = mu_g cp_g / Pr
+                       (> 0 when viscous) */
+  double lambda_liquid; /* liquid-phase heat conductivity [W/(m K)] (>= 0) */
 } mpmc_model;
 
 /* One SSP-RK stage: U^(k+1) = rk0 U^n + rk1 U^(k) + rk2 dt L(U^(k)).

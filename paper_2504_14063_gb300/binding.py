@@ -44,7 +44,8 @@ class ModelC(ctypes.Structure):
     _fields_ = [("weno_eps", ctypes.c_double), ("cdi", ctypes.c_int), ("diffusion", ctypes.c_int),
                 ("pos_limiter", ctypes.c_int), ("cdi_eps", ctypes.c_double), ("cdi_gamma", ctypes.c_double),
                 ("phi_min", ctypes.c_double), ("psi_delta", ctypes.c_double), ("cfl", ctypes.c_double),
-                ("mu_liquid", ctypes.c_double), ("precision", ctypes.c_int), ("recon", ctypes.c_int)]
+                ("mu_liquid", ctypes.c_double), ("precision", ctypes.c_int), ("recon", ctypes.c_int),
+                ("viscous", ctypes.c_int), ("prandtl", ctypes.c_double), ("lambda_liquid", ctypes.c_double)]
 
 
 class StageC(ctypes.Structure):
@@ -132,7 +133,7 @@ def structs_from_problem(problem, precision=FP64):
     m = ModelC()
     pm = problem.model
     for f in ("weno_eps", "cdi", "diffusion", "pos_limiter", "cdi_eps", "cdi_gamma", "phi_min", "psi_delta",
-              "cfl", "mu_liquid", "recon"):
+              "cfl", "mu_liquid", "recon", "viscous", "prandtl", "lambda_liquid"):
         setattr(m, f, getattr(pm, f))
     m.precision = precision
     return g, e, m

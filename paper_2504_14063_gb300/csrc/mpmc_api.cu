@@ -426,6 +426,7 @@ static int ensure_adjoint(mpmc_ctx* c) {
   if (c->precision != MPMC_FP64) return fail(c, MPMC_INVALID_ARG, "adjoint: needs an FP64 context");
   if (c->P.recon != MPMC_RECON_WENO5Z)
     return fail(c, MPMC_INVALID_ARG, "adjoint: the reverse kernels differentiate WENO5-Z only");
+  if (c->P.viscous) return fail(c, MPMC_INVALID_ARG, "adjoint: viscous stress and conduction are not reversed");
   const KParams& P = c->P;
   int rc = MPMC_OK;
   const size_t st_bytes = (size_t)P.nv * P.ncell * sizeof(double);

@@ -39,11 +39,13 @@ struct KParams {
   double weno_eps;
   int cdi, diffusion, pos_limiter, two_phase, has_inflow;
   int recon;  // MPMC_RECON_* (the face kernels take it as a template parameter)
+  int viscous;  // viscous stress and heat conduction
+  double prandtl, lambda_liquid;
   int has_b, has_q;  // some species has a nonzero NASG covolume b / reference energy q
   double cdi_eps, cdi_gamma, phi_min, psi_delta, cfl, mu_liquid, sharp0;
   // primitive cache: field f of cell c at Wc[f * wstride + c]; slot ncell
   // holds the inflow state
-  int wT, wP, wRho, wA, wY, wU, wPhi0, wPsi, wYrho, wHrho, wXr, wB, nW;
+  int wT, wP, wRho, wA, wY, wU, wPhi0, wPsi, wYrho, wHrho, wXr, wB, wMu, wLam, nW;
   long long wstride;
   // mixed precision only: FP32 copy of U^n ([nv][wstride]) written by the
   // primitive pass that computes the step's dt and Gamma; FP32 copies of

@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(CELL_THREADS)
 #pragma unroll
     for (int d = 0; d < D; ++d) Wc[(P.wU + d) * ws + c] = u[d];
 
-    double mu = 0.0;
-    if (P.cdi || P.diffusion) {
+    double mu = 0.0, lam = 0.0;
+    if (P.cdi || P.diffusion || P.viscous) {
       double phi[2], Yp[2];
 #pragma unroll
       for (int ph = 0; ph < 2; ++ph) {
@@ -148,10 +148,9 @@ __global__ void __launch_bounds__(CELL_THREADS)
         Wc[P.wPhi0 * ws + c] = phi[0];
         Wc[P.wPsi * ws + c] = P.cdi_eps * log((phi[0] + P.psi_delta) / (phi[1] + P.psi_delta));
       }
-      if (P.diffusion) {
-        // phase viscosities: liquid constant, gas by Wilke's rule
-        double mup[2];
-        mup[0] = P.mu_liquid;
+      // phase viscosities: liquid constant, gas by Wilke's rule
+      double mup[2] = {P.mu_liquid, 0.0};
+      if (P.diffusion || P.viscous) {
         double num = 0.0;
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -164,6 +163,19 @@ __global__ void __launch_bounds__(CELL_THREADS)
         }
         mup[1] = Yp[1] >= ABSENT ? num : 0.0;
         mu = phi[0] * mup[0] + phi[1] * mup[1];
+      }
+      if (P.viscous) {
+        // heat conductivity: liquid constant, gas (mu_g / Pr) sum (Y^c/Y_g) Cp^c
+        double cpY = 0.0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+          if (P.phase[k] == 1) cpY += Y[k] * P.cp[k];
+        const double lam_g = Yp[1] >= ABSENT ? mup[1] / P.prandtl * (cpY / Yp[1]) : 0.0;
+        lam = phi[0] * P.lambda_liquid + phi[1] * lam_g;
+        Wc[P.wMu * ws + c] = mu;
+        Wc[P.wLam * ws + c] = lam;
+      }
+      if (P.diffusion) {
 #pragma unroll
         for (int ph = 0; ph < 2; ++ph) {
           double sY = 0.0;
@@ -195,7 +207,14 @@ __global__ void __launch_bounds__(CELL_THREADS)
         smax = fmax(smax, (ud + a) * P.inv_dx);
         gmax = fmax(gmax, ud);
       }
-      if (P.diffusion) smax = fmax(smax, 4.0 * mu / rho * (P.inv_dx * P.inv_dx));
+      if (P.diffusion || P.viscous) smax = fmax(smax, 4.0 * mu / rho * (P.inv_dx * P.inv_dx));
+      if (P.viscous) {
+        // conduction limit with the thermal diffusivity lambda / (rho cv)
+        double cv = 0.0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) cv += Y[k] * P.cv[k];
+        smax = fmax(smax, 4.0 * lam / (rho * cv) * (P.inv_dx * P.inv_dx));
+      }
     }
   }
   if (red) block_max2(smax, gmax, red);
@@ -496,6 +515,58 @@ __global__ void __launch_bounds__(FACE_THREADS)
       }
     }
     Fx[NS + D] += Jh;
+  }
+
+  // viscous stress and heat conduction (Eq. DiffusionTerms), second-order
+  // central: face averages of the two cells, normal derivative
+  // (q_j - q_i)/dx, a tangential one the mean of the two cells' central
+  // differences; the energy row carries -u.tau + q
+  if (P.viscous) {
+    double gu[3][3];  // gu[i][j] = d u_i / d x_j on the face
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) gu[i][j] = 0.0;
+    double ui[3] = {0.0, 0.0, 0.0}, uj[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      ui[i] = wget(P, Wc, P.wU + i, ri) * sgn_flip(ri.flip, i);
+      uj[i] = wget(P, Wc, P.wU + i, rj) * sgn_flip(rj.flip, i);
+      gu[i][d] = (uj[i] - ui[i]) * P.inv_dx;
+    }
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      if (t == d) continue;
+      int a0[3] = {ci[0], ci[1], ci[2]}, a1[3] = {ci[0], ci[1], ci[2]};
+      a0[t] += 1;
+      a1[t] -= 1;
+      int b0[3] = {a0[0], a0[1], a0[2]}, b1[3] = {a1[0], a1[1], a1[2]};
+      b0[d] += 1;
+      b1[d] += 1;
+      const CRef ip = map_cell(P, a0[0], a0[1], a0[2]), im = map_cell(P, a1[0], a1[1], a1[2]);
+      const CRef jp = map_cell(P, b0[0], b0[1], b0[2]), jm = map_cell(P, b1[0], b1[1], b1[2]);
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const double dip = wget(P, Wc, P.wU + i, ip) * sgn_flip(ip.flip, i) -
+                           wget(P, Wc, P.wU + i, im) * sgn_flip(im.flip, i);
+        const double djp = wget(P, Wc, P.wU + i, jp) * sgn_flip(jp.flip, i) -
+                           wget(P, Wc, P.wU + i, jm) * sgn_flip(jm.flip, i);
+        gu[i][t] = 0.25 * P.inv_dx * (dip + djp);
+      }
+    }
+    double div = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) div += gu[k][k];
+    const double mub = 0.5 * (wget(P, Wc, P.wMu, ri) + wget(P, Wc, P.wMu, rj));
+    const double lamb = 0.5 * (wget(P, Wc, P.wLam, ri) + wget(P, Wc, P.wLam, rj));
+    double work = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const double tau = mub * (gu[i][d] + gu[d][i] - (i == d ? (2.0 / 3.0) * div : 0.0));
+      Fx[NS + i] -= tau;
+      work += 0.5 * (ui[i] + uj[i]) * tau;
+    }
+    Fx[NS + D] -= work + lamb * (Tj - Ti) * P.inv_dx;
   }
 
 #pragma unroll

@@ -21,6 +21,8 @@ inline int build_params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_mode
   if (m->precision != MPMC_FP64 && m->precision != MPMC_MIXED) return MPMC_INVALID_ARG;
   if (m->recon < MPMC_RECON_WENO5Z || m->recon > MPMC_RECON_TENO6) return MPMC_INVALID_ARG;
   if (m->recon != MPMC_RECON_WENO5Z && m->precision != MPMC_FP64) return MPMC_INVALID_ARG;
+  if (m->viscous && (m->precision != MPMC_FP64 || !(m->prandtl > 0.0) || !(m->lambda_liquid >= 0.0)))
+    return MPMC_INVALID_ARG;
   for (int d = 0; d < 3; ++d) {
     if (d < g->dim && g->n[d] < 3) return MPMC_INVALID_ARG;
     if (d >= g->dim && g->n[d] != 1) return MPMC_INVALID_ARG;
@@ -85,6 +87,9 @@ inline int build_params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_mode
   P.diffusion = m->diffusion ? 1 : 0;
   P.pos_limiter = m->pos_limiter ? 1 : 0;
   P.recon = m->recon;
+  P.viscous = m->viscous ? 1 : 0;
+  P.prandtl = m->prandtl;
+  P.lambda_liquid = m->lambda_liquid;
   P.cdi_eps = m->cdi_eps > 0.0 ? m->cdi_eps : g->dx;
   P.cdi_gamma = m->cdi_gamma;
   P.phi_min = m->phi_min;
@@ -115,6 +120,10 @@ inline int build_params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_mode
     f += ns;
     P.wB = f;
     f += ns;
+  }
+  if (P.viscous) {
+    P.wMu = f++;
+    P.wLam = f++;
   }
   P.nW = f;
   P.wstride = P.ncell + 1;

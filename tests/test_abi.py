@@ -47,7 +47,7 @@ int main(void) {{
   printf("%zu %zu %zu %zu %zu\\n", sizeof(mpmc_grid), sizeof(mpmc_eos), sizeof(mpmc_model),
          sizeof(mpmc_stage), sizeof(mpmc_stats));
   printf("%zu %zu %zu %zu %zu\\n", offsetof(mpmc_grid, inflow), offsetof(mpmc_eos, Sc),
-         offsetof(mpmc_model, precision), offsetof(mpmc_model, recon), offsetof(mpmc_stage, Gamma));
+         offsetof(mpmc_model, precision), offsetof(mpmc_model, lambda_liquid), offsetof(mpmc_stage, Gamma));
   return 0;
 }}
 """)
@@ -57,8 +57,8 @@ int main(void) {{
     sizes = [int(x) for x in out[:5]]
     offs = [int(x) for x in out[5:]]
     assert sizes == [ctypes.sizeof(t) for t in (b.Grid, b.Eos, b.ModelC, b.StageC, b.StatsC)]
-    assert offs == [b.Grid.inflow.offset, b.Eos.Sc.offset, b.ModelC.precision.offset, b.ModelC.recon.offset,
-                    b.StageC.Gamma.offset]
+    assert offs == [b.Grid.inflow.offset, b.Eos.Sc.offset, b.ModelC.precision.offset,
+                    b.ModelC.lambda_liquid.offset, b.StageC.Gamma.offset]
 
 
 def test_invalid_arguments_are_rejected_without_a_gpu(lib):
@@ -85,5 +85,10 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     m.recon = 4
     assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
     m.recon, m.precision = 3, b.MIXED
+    assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
+    # viscosity: mixed precision, or a non-positive Prandtl number
+    m.recon, m.viscous, m.prandtl = 0, 1, 0.72
+    assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
+    m.precision, m.prandtl = b.FP64, 0.0
     assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
     assert h.value is None

@@ -1,0 +1,95 @@
+"""Viscous stress and heat conduction (Eq. DiffusionTerms; row f2) on the
+FP64 GPU path, through the C ABI: the stage right-hand side against the
+oracle with walls (mirrored tangential gradients), periodic and 3D
+boundaries (same bound as the inviscid parity tests), 100 steps, and the
+shear wave's decay against the exact SSP-RK3 factor of the discrete
+Laplacian; the mixed path and the adjoint refuse it."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2504_14063_gb300 import workloads as W
+from tests.test_gpu_parity import _steps_parity, rhs_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mp():
+    from paper_2504_14063_gb300 import binding
+    return binding
+
+
+def _viscous(p, mu_scale=1.0):
+    p.model.viscous = 1
+    if mu_scale != 1.0:
+        p.model.mu_liquid *= mu_scale
+        p.model.lambda_liquid *= mu_scale
+        for s in p.species:
+            s.mu *= mu_scale
+    return p
+
+
+CASES = {
+    # the viscous terms scaled up so that they are a visible part of L
+    "slab_1d": (lambda: _viscous(W.interface_advection_1d(n=400, cdi=1), 1e4), 3),
+    "shock_bubble_2d_walls": (lambda: _viscous(W.shock_bubble_2d(nx=100, ny=52, seed=1), 1e3), 60),
+    "periodic_cdi_diffusion_2d": (lambda: _viscous(W.random_smooth_2d(41, 35, seed=5, cdi=1, diffusion=1), 1e3), 2),
+    "droplet_field_3d": (lambda: _viscous(W.droplet_field_3d(n=22, ndrops=4, seed=2, rmin=3.0, rmax=5.0), 1e2), 2),
+    "shock_droplet_3d": (lambda: _viscous(W.shock_droplet_3d(n=24, seed=4), 1e2), 2),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_rhs_parity_viscous(mp, case):
+    make, pre = CASES[case]
+    rhs_parity(mp, make(), pre_steps=pre)
+
+
+def test_100_steps_shock_bubble_viscous(mp):
+    p = _viscous(W.shock_bubble_2d(nx=72, ny=40, seed=0, liquid_cols=24), 1e3)
+    _steps_parity(mp, p, 100, conditioned=False)
+
+
+def test_shear_wave_decay_on_gpu(mp):
+    """u_y = A sin(kx), gas at rest, periodic: after n steps of length dt
+    the amplitude is A (1 - z + z^2/2 - z^3/6)^n, z = nu (2 - 2 cos k dx)
+    dt / dx^2 (the three-point Laplacian that the face gradients make)."""
+    nx, A, dx = 16, 1e-3, 1e-7
+    prim = np.zeros((5, 1, 4, nx))
+    x = (np.arange(nx) + 0.5) * dx
+    prim[0] = 1.0
+    prim[2] = A * np.sin(2 * np.pi * x / (nx * dx))[None, None, :]
+    prim[3] = 1e5
+    prim[4] = 300.0
+    p = W.Problem("shear", 2, (nx, 4, 1), dx, [W.AIR], W.Model(), prim,
+                  bc_lo=(W.BC_PERIODIC,) * 3, bc_hi=(W.BC_PERIODIC,) * 3)
+    p.model.viscous = 1
+    ctx = mp.Context(p)
+    U = ctx.init_state(torch.from_numpy(prim))
+    rho = float(U[0].mean())
+    nu = W.AIR.mu / rho
+    a = np.sqrt(W.AIR.gamma * (W.AIR.gamma - 1) * W.AIR.cv * 300.0)
+    dt = min(0.4 * dx / a, 0.1 * dx * dx / nu)
+    n = 40
+    for _ in range(n):
+        ctx.rk_step(U, dt)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    z = nu * (2 - 2 * np.cos(2 * np.pi / nx)) * dt / dx ** 2
+    factor = (1 - z + z * z / 2 - z ** 3 / 6) ** n
+    uy = (U[2] / U[0]).cpu().numpy()[0, 0]
+    s = np.sin(2 * np.pi * (np.arange(nx) + 0.5) / nx)
+    amp = (uy * s).sum() / (s * s).sum()
+    print(f"GPU shear wave after {n} steps: amplitude ratio {amp / A:.12f}, discrete factor {factor:.12f}")
+    assert amp / A == pytest.approx(factor, rel=1e-9)
+
+
+def test_viscous_needs_the_fp64_forward_path(mp):
+    p = _viscous(W.random_smooth_2d(16, 12, seed=1))
+    with pytest.raises(mp.MpmcError):
+        mp.Context(p, precision=mp.MIXED)
+    ctx = mp.Context(p)
+    U = ctx.init_state(torch.from_numpy(p.prim))
+    with pytest.raises(mp.MpmcError):
+        ctx.rk_step_adjoint(U, torch.zeros_like(U), dt=1e-9)
