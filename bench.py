@@ -405,12 +405,16 @@ def main():
     # ---- Sec. 4.1's other ENO-type interpolations: the same FP64 step ------
     recon = None
     if not args.no_recon:
-        recon = {"note": "the FP64 SSP-RK3 step of the same workload with each interpolation, "
+        recon = {"note": "the FP64 SSP-RK3 step of the same workload with each other interpolation "
+                         "(WENO5-JS, TENO5, TENO6) and with viscous stress and heat conduction on, "
                          "same timing (CUDA events per step, L2 flushed between steps)"}
         from paper_2504_14063_gb300 import workloads as W
-        for rname, rkind in (("WENO5JS", W.RECON_WENO5JS), ("TENO5", W.RECON_TENO5), ("TENO6", W.RECON_TENO6)):
+        variants = (("WENO5JS", dict(recon=W.RECON_WENO5JS)), ("TENO5", dict(recon=W.RECON_TENO5)),
+                    ("TENO6", dict(recon=W.RECON_TENO6)), ("viscous", dict(viscous=1)))
+        for rname, fields in variants:
             pr_ = workload()
-            pr_.model.recon = rkind
+            for f_, v_ in fields.items():
+                setattr(pr_.model, f_, v_)
             ctxr = mp.Context(pr_)
             Ur = ctxr.init_state(torch.from_numpy(pr_.prim))
             for _ in range(args.warmup):
@@ -434,7 +438,7 @@ def main():
                 tr = float(t.item())
             vr = world * pr_.ncells * args.recon_steps / tr
             recon[rname] = {"value": vr, "unit": UNIT, "ms_per_step": 1e3 * tr / args.recon_steps,
-                            "vs_weno5z": vr / value, "steps": args.recon_steps,
+                            "vs_base_step": vr / value, "steps": args.recon_steps,
                             "face_ms_per_step": rprof["face"][0] / args.recon_steps, "status": ctxr.status()}
             del ctxr, Ur
 
@@ -476,7 +480,7 @@ def main():
         if mixed is not None:
             line["mixed"] = mixed
         if recon is not None:
-            line["interpolations"] = recon
+            line["variants"] = recon
         if adjoint is not None:
             line["adjoint"] = adjoint
         if world == 1 and not args.no_cpu_baseline:

@@ -57,7 +57,7 @@ struct KParams {
   struct Consts32 {
     float cv[MAXS], gam[MAXS], q[MAXS], b[MAXS], pinf[MAXS], Rk[MAXS], cp[MAXS];
     float W[MAXS], mu[MAXS], Sc[MAXS], wilke[MAXS][MAXS];
-    float inv_dx, cdi_eps, sharp0, mu_liquid;
+    float inv_dx, cdi_eps, sharp0, mu_liquid, prandtl, lambda_liquid;
   } f32;
 };
 
@@ -80,6 +80,8 @@ inline void round_consts32(KParams& P) {
   P.f32.cdi_eps = (float)P.cdi_eps;
   P.f32.sharp0 = (float)P.sharp0;
   P.f32.mu_liquid = (float)P.mu_liquid;
+  P.f32.prandtl = (float)P.prandtl;
+  P.f32.lambda_liquid = (float)P.lambda_liquid;
 }
 
 // (x, y, z) of the linear index l of an n0 x n1 x n2 box, in 32-bit unsigned

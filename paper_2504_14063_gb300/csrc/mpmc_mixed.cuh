@@ -324,9 +324,9 @@ __global__ void __launch_bounds__(CELL_THREADS)
       Wc[(P.nW + v) * ws + c] = (float)Uc[v];
       if (red) P.unf[v * ws + c] = (float)Uc[v];
     }
-    float mu = 0.f;
+    float mu = 0.f, lam = 0.f;
     const float rhof = (float)rho;
-    if (P.cdi || P.diffusion) {
+    if (P.cdi || P.diffusion || P.viscous) {
       float phi[2], Yp[2];
 #pragma unroll
       for (int ph = 0; ph < 2; ++ph) {
@@ -356,9 +356,8 @@ __global__ void __launch_bounds__(CELL_THREADS)
         Wc[P.wPhi0 * ws + c] = phi[0];
         Wc[P.wPsi * ws + c] = P.f32.cdi_eps * __logf((phi[0] + DELTA32) / (phi[1] + DELTA32));
       }
-      if (P.diffusion) {
-        float mup[2];
-        mup[0] = P.f32.mu_liquid;
+      float mup[2] = {P.f32.mu_liquid, 0.f};
+      if (P.diffusion || P.viscous) {
         float num = 0.f;
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -371,6 +370,18 @@ __global__ void __launch_bounds__(CELL_THREADS)
         }
         mup[1] = Yp[1] > 0.f ? num : 0.f;
         mu = phi[0] * mup[0] + phi[1] * mup[1];
+      }
+      if (P.viscous) {
+        float cpY = 0.f;
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+          if (P.phase[k] == 1) cpY += Yf[k] * sp[k].cp;
+        const float lam_g = Yp[1] > 0.f ? mup[1] / P.f32.prandtl * (cpY / Yp[1]) : 0.f;
+        lam = phi[0] * P.f32.lambda_liquid + phi[1] * lam_g;
+        Wc[P.wMu * ws + c] = mu;
+        Wc[P.wLam * ws + c] = lam;
+      }
+      if (P.diffusion) {
 #pragma unroll
         for (int ph = 0; ph < 2; ++ph) {
           float sY = 0.f;
@@ -403,7 +414,13 @@ __global__ void __launch_bounds__(CELL_THREADS)
         smax = fmaxf(smax, (ud + a) * idx);
         gmax = fmaxf(gmax, ud);
       }
-      if (P.diffusion) smax = fmaxf(smax, 4.f * mu / rhof * (idx * idx));
+      if (P.diffusion || P.viscous) smax = fmaxf(smax, 4.f * mu / rhof * (idx * idx));
+      if (P.viscous) {
+        float cv = 0.f;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) cv += Yf[k] * sp[k].cv;
+        smax = fmaxf(smax, 4.f * lam / (rhof * cv) * (idx * idx));
+      }
     }
   }
   if (red) block_max2f(smax, gmax, red);
@@ -794,6 +811,55 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
   }
 
 #pragma unroll
+  // viscous stress and heat conduction in FP32, as the FP64 face kernel's
+  // (second-order central; uniform u and T give exactly zero)
+  if (P.viscous) {
+    const float idx = P.f32.inv_dx;
+    float gu[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) gu[i][j] = 0.f;
+    float ui[3] = {0.f, 0.f, 0.f}, uj[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      ui[i] = wgetf(P, Wc, P.wU + i, ri) * sgnf(ri.flip, i);
+      uj[i] = wgetf(P, Wc, P.wU + i, rj) * sgnf(rj.flip, i);
+      gu[i][d] = (uj[i] - ui[i]) * idx;
+    }
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      if (t == d) continue;
+      int a0[3] = {ci[0], ci[1], ci[2]}, a1[3] = {ci[0], ci[1], ci[2]};
+      a0[t] += 1;
+      a1[t] -= 1;
+      int b0[3] = {a0[0], a0[1], a0[2]}, b1[3] = {a1[0], a1[1], a1[2]};
+      b0[d] += 1;
+      b1[d] += 1;
+      const CRef ip = map_cell(P, a0[0], a0[1], a0[2]), im = map_cell(P, a1[0], a1[1], a1[2]);
+      const CRef jp = map_cell(P, b0[0], b0[1], b0[2]), jm = map_cell(P, b1[0], b1[1], b1[2]);
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const float dip = wgetf(P, Wc, P.wU + i, ip) * sgnf(ip.flip, i) - wgetf(P, Wc, P.wU + i, im) * sgnf(im.flip, i);
+        const float djp = wgetf(P, Wc, P.wU + i, jp) * sgnf(jp.flip, i) - wgetf(P, Wc, P.wU + i, jm) * sgnf(jm.flip, i);
+        gu[i][t] = 0.25f * idx * (dip + djp);
+      }
+    }
+    float div = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) div += gu[k][k];
+    const float mub = 0.5f * (wgetf(P, Wc, P.wMu, ri) + wgetf(P, Wc, P.wMu, rj));
+    const float lamb = 0.5f * (wgetf(P, Wc, P.wLam, ri) + wgetf(P, Wc, P.wLam, rj));
+    float work = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float tau = mub * (gu[i][d] + gu[d][i] - (i == d ? (2.f / 3.f) * div : 0.f));
+      Fx[NS + i] -= tau;
+      work += 0.5f * (ui[i] + uj[i]) * tau;
+    }
+    Fx[NS + D] -= work + lamb * (Tj - Ti) * idx;
+  }
+
   // stored widened to FP64 (exact): the update then takes every flux with
   // the same FP64 value in its two cells, and the widening happens once per
   // face, here, where the FP64 pipe is otherwise idle

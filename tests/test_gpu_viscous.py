@@ -3,13 +3,15 @@ FP64 GPU path, through the C ABI: the stage right-hand side against the
 oracle with walls (mirrored tangential gradients), periodic and 3D
 boundaries (same bound as the inviscid parity tests), 100 steps, and the
 shear wave's decay against the exact SSP-RK3 factor of the discrete
-Laplacian; the mixed path and the adjoint refuse it."""
+Laplacian; the mixed path's FP32 viscous fluxes within the mixed-precision
+bound; the adjoint refuses it."""
 import numpy as np
 import pytest
 import torch
 
+from oracle import Oracle
 from paper_2504_14063_gb300 import workloads as W
-from tests.test_gpu_parity import _steps_parity, rhs_parity
+from tests.test_gpu_parity import NTH, _cuda, _gross, _steps_parity, rhs_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -85,10 +87,39 @@ def test_shear_wave_decay_on_gpu(mp):
     assert amp / A == pytest.approx(factor, rel=1e-9)
 
 
-def test_viscous_needs_the_fp64_forward_path(mp):
+@pytest.mark.parametrize("case", ["shock_bubble_2d_walls", "periodic_cdi_diffusion_2d", "shock_droplet_3d"])
+def test_mixed_rhs_viscous_close_to_oracle(mp, case):
+    """The mixed path's FP32 viscous fluxes: the stage right-hand side within
+    the mixed-precision bound of tests/test_gpu_mixed.py (1e-4 of the
+    oracle's L1 + 1e-7 of the gross flux + 10 x the oracle's own change
+    under a 2^-24 perturbation of its input)."""
+    make, pre = CASES[case]
+    p = make()
+    o = Oracle(p, nthreads=NTH)
+    Un = o.run(o.init_state(), pre)[0]
+    dt, G, _ = o.dt_gamma(Un)
+    Uk = o.stage(Un, Un, (1.0, 0.0, 1.0), dt, G)[0]
+    rk = (0.75, 0.25, 0.25)
+    _, Lo, _, st = o.stage(Un, Uk, rk, dt, G)
+    assert st == 0
+    F, _ = o.face_fluxes(Un, Uk, rk, dt, G)
+    ctx = mp.Context(p, precision=mp.MIXED)
+    Lg = ctx.rhs(_cuda(Uk), stage=dict(U_n=_cuda(Un), rk=rk, dt=dt, Gamma=G)).cpu().numpy()
+    assert ctx.status() == 0
+    rng = np.random.default_rng(1)
+    jit = lambda A: A * (1.0 + 2.0 ** -24 * rng.standard_normal(A.shape))
+    _, Lt, _, _ = o.stage(jit(Un), jit(Uk), rk, dt, G)
+    T32 = np.abs(Lt - Lo).sum(axis=(1, 2, 3))
+    num = np.abs(Lg - Lo).sum(axis=(1, 2, 3))
+    ref = np.abs(Lo).sum(axis=(1, 2, 3))
+    bound = 1e-4 * ref + 1e-7 * _gross(p, F) + 10.0 * T32
+    print(f"mixed viscous rhs {case}: rel err {np.array2string(num / ref, precision=2)}, err/bound "
+          f"{np.array2string(num / bound, precision=2)}")
+    assert np.all(num <= bound)
+
+
+def test_viscous_adjoint_is_refused(mp):
     p = _viscous(W.random_smooth_2d(16, 12, seed=1))
-    with pytest.raises(mp.MpmcError):
-        mp.Context(p, precision=mp.MIXED)
     ctx = mp.Context(p)
     U = ctx.init_state(torch.from_numpy(p.prim))
     with pytest.raises(mp.MpmcError):
