@@ -192,9 +192,9 @@ extern "C" int mpmc_create(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_m
     case 2: c->aops = adj_ops_d2(ns); break;
     default: c->aops = adj_ops_d3(ns); break;
   }
-  if (P.recon == MPMC_RECON_WENO5JS) c->ops.face = face_fp64_weno5js(D, ns);
-  else if (P.recon == MPMC_RECON_TENO5) c->ops.face = face_fp64_teno5(D, ns);
-  else if (P.recon == MPMC_RECON_TENO6) c->ops.face = face_fp64_teno6(D, ns);
+  if (P.recon == MPMC_RECON_WENO5JS) c->ops.face = mixed ? face_mixed_weno5js(D, ns) : face_fp64_weno5js(D, ns);
+  else if (P.recon == MPMC_RECON_TENO5) c->ops.face = mixed ? face_mixed_teno5(D, ns) : face_fp64_teno5(D, ns);
+  else if (P.recon == MPMC_RECON_TENO6) c->ops.face = mixed ? face_mixed_teno6(D, ns) : face_fp64_teno6(D, ns);
   if (!c->ops.face || !c->aops.face) {
     delete c;
     return MPMC_INVALID_ARG;

@@ -140,6 +140,95 @@ __device__ __forceinline__ float weno5z_f(float v0, float v1, float v2, float v3
   return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
 }
 
+// Sec. 4.1's other ENO-type interpolations in FP32 (as the FP64 ones in
+// mpmc_device.cuh; the mixed face kernel feeds them deviations from the left
+// cell).  Ratios tau / (beta + eps) are clamped at 1e30 as in weno5z_f.
+struct Eno3f {
+  float ql, qc, qr, bl, bc, br;
+};
+
+__device__ __forceinline__ Eno3f eno3_f(float v0, float v1, float v2, float v3, float v4) {
+  Eno3f e;
+  e.ql = (2.f * v0 - 7.f * v1 + 11.f * v2) * (1.f / 6.f);
+  e.qc = (-v1 + 5.f * v2 + 2.f * v3) * (1.f / 6.f);
+  e.qr = (2.f * v2 + 5.f * v3 - v4) * (1.f / 6.f);
+  float t = v0 - 2.f * v1 + v2, s = v0 - 4.f * v1 + 3.f * v2;
+  e.bl = (13.f / 12.f) * t * t + 0.25f * s * s;
+  t = v1 - 2.f * v2 + v3;
+  s = v1 - v3;
+  e.bc = (13.f / 12.f) * t * t + 0.25f * s * s;
+  t = v2 - 2.f * v3 + v4;
+  s = 3.f * v2 - 4.f * v3 + v4;
+  e.br = (13.f / 12.f) * t * t + 0.25f * s * s;
+  return e;
+}
+
+// WENO5-JS: alpha_k = d_k / (eps + beta_k)^2, eps = 1e-6
+__device__ __forceinline__ float weno5js_f(float v0, float v1, float v2, float v3, float v4) {
+  const Eno3f e = eno3_f(v0, v1, v2, v3, v4);
+  // 1/(eps + beta)^2 stays a normal FP32 number for indicators below 1e18
+  const float il = __frcp_rn(1e-6f + e.bl), ic = __frcp_rn(1e-6f + e.bc), ir = __frcp_rn(1e-6f + e.br);
+  const float al = 0.1f * il * il, ac = 0.6f * ic * ic, ar = 0.3f * ir * ir;
+  return (al * e.ql + ac * e.qc + ar * e.qr) / (al + ac + ar);
+}
+
+template <int K>
+__device__ __forceinline__ float teno_select_f(const float* q, const float* b, const float* dk, float tau, float CT) {
+  float r[K], rmax = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    r[k] = 1.f + fminf(__fdividef(tau, b[k] + WENO_EPS32), 1e30f);
+    rmax = fmaxf(rmax, r[k]);
+  }
+  const float irm = __frcp_rn(rmax);
+  float g[K], gs = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float x = r[k] * irm, x2 = x * x;
+    g[k] = x2 * x2 * x2;
+    gs += g[k];
+  }
+  float num = 0.f, den = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (!(g[k] < CT * gs)) {
+      num += dk[k] * q[k];
+      den += dk[k];
+    }
+  return num / den;
+}
+
+__device__ __forceinline__ float teno5_f(float v0, float v1, float v2, float v3, float v4) {
+  const Eno3f e = eno3_f(v0, v1, v2, v3, v4);
+  const float q[3] = {e.qc, e.ql, e.qr}, b[3] = {e.bc, e.bl, e.br}, dk[3] = {0.6f, 0.1f, 0.3f};
+  return teno_select_f<3>(q, b, dk, fabsf(e.bl - e.br), 1e-5f);
+}
+
+__device__ __forceinline__ float teno6_f(float v0, float v1, float v2, float v3, float v4, float v5) {
+  const Eno3f e = eno3_f(v0, v1, v2, v3, v4);
+  const float q4 = (3.f * v2 + 13.f * v3 - 5.f * v4 + v5) * (1.f / 12.f);
+  const float e0 = v0 - v2, e1 = v1 - v2, e3 = v3 - v2, e4 = v4 - v2, e5 = v5 - v2;
+  const float s = 18.f * e3 - 9.f * e4 + 2.f * e5, t = -5.f * e3 + 4.f * e4 - e5, u = 3.f * e3 - 3.f * e4 + e5;
+  const float b4 = (1.f / 36.f) * s * s + (13.f / 12.f) * t * t + (781.f / 720.f) * u * u;
+  const float c1 = 3.f * e0 - 30.f * e1 + 60.f * e3 - 15.f * e4 + 2.f * e5;
+  const float c2 = -11.f * e0 + 174.f * e1 + 174.f * e3 - 11.f * e4;
+  const float c3 = -16315.f * e0 - 16831.f * e1 - 230474.f * e3 + 115237.f * e4 - 16487.f * e5;
+  const float c4 = e0 - 4.f * e1 - 4.f * e3 + e4;
+  const float c5 = -e0 + 5.f * e1 + 10.f * e3 - 5.f * e4 + e5;
+  const float b6 = (1.f / 3600.f) * c1 * c1 + (1.f / 15600.f) * c2 * c2 + (1.f / 3967729920.f) * c3 * c3 +
+                   (1421461.f / 1310400.f) * c4 * c4 + (21520059541.f / 19838649600.f) * c5 * c5;
+  const float q[4] = {e.qc, e.ql, e.qr, q4}, b[4] = {e.bc, e.bl, e.br, b4}, dk[4] = {0.45f, 0.05f, 0.3f, 0.2f};
+  return teno_select_f<4>(q, b, dk, fabsf(b6 - (e.bl + e.br + 4.f * e.bc) * (1.f / 6.f)), 1e-7f);
+}
+
+template <int RC>
+__device__ __forceinline__ float recon_f(float v0, float v1, float v2, float v3, float v4, float v5) {
+  if constexpr (RC == RC_WENO5JS) return weno5js_f(v0, v1, v2, v3, v4);
+  else if constexpr (RC == RC_TENO5) return teno5_f(v0, v1, v2, v3, v4);
+  else if constexpr (RC == RC_TENO6) return teno6_f(v0, v1, v2, v3, v4, v5);
+  else return weno5z_f(v0, v1, v2, v3, v4);
+}
+
 template <int NS>
 struct StateF {
   float rho, rhoY[NS], u[3], m[3], p, E, a;
@@ -485,7 +574,8 @@ __device__ __forceinline__ int admissible_f(const KParams& P, const float* Unf, 
 // by it is indexed by a constant (registers, not the stack).  Five blocks per
 // SM (<= 96 registers, a small spill) hide more of the cache loads' latency
 // than four with 126 registers: 6 % less time for this kernel on GB300.
-template <int NS, int D, int DIR>
+// RC: the ENO-type interpolation (RC_WENO5Z or one of Sec. 4.1's others).
+template <int NS, int D, int DIR, int RC>
 __global__ void __launch_bounds__(FACE_THREADS, 5)
     k_face(const KParams P, const float* __restrict__ Wc, const double* __restrict__ Un,
            const double* __restrict__ Uk, const double* __restrict__ Uin, const double* __restrict__ scal,
@@ -579,12 +669,12 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
       w5[j] = (0.5f * c) * du + 0.5f * dp;
       w6[j] = (-0.5f * c) * du + 0.5f * dp;
     }
-    const float w1L = weno5z_f(w1[0], w1[1], w1[2], w1[3], w1[4]);
-    const float w1R = weno5z_f(w1[5], w1[4], w1[3], w1[2], w1[1]);
-    const float w5L = weno5z_f(w5[0], w5[1], w5[2], w5[3], w5[4]);
-    const float w5R = weno5z_f(w5[5], w5[4], w5[3], w5[2], w5[1]);
-    const float w6L = weno5z_f(w6[0], w6[1], w6[2], w6[3], w6[4]);
-    const float w6R = weno5z_f(w6[5], w6[4], w6[3], w6[2], w6[1]);
+    const float w1L = recon_f<RC>(w1[0], w1[1], w1[2], w1[3], w1[4], w1[5]);
+    const float w1R = recon_f<RC>(w1[5], w1[4], w1[3], w1[2], w1[1], w1[0]);
+    const float w5L = recon_f<RC>(w5[0], w5[1], w5[2], w5[3], w5[4], w5[5]);
+    const float w5R = recon_f<RC>(w5[5], w5[4], w5[3], w5[2], w5[1], w5[0]);
+    const float w6L = recon_f<RC>(w6[0], w6[1], w6[2], w6[3], w6[4], w6[5]);
+    const float w6R = recon_f<RC>(w6[5], w6[4], w6[3], w6[2], w6[1], w6[0]);
     TL = Ti + (w1L + X * (w5L + w6L));
     TR = Ti + (w1R + X * (w5R + w6R));
     uL[d] = uni + ic * (w5L - w6L);
@@ -600,8 +690,8 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
     float y[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) y[j] = wgetf(P, Wc, P.wY + k, cr[j]) - Yi[k];
-    YL[k] = Yi[k] + weno5z_f(y[0], y[1], y[2], y[3], y[4]);
-    YR[k] = Yi[k] + weno5z_f(y[5], y[4], y[3], y[2], y[1]);
+    YL[k] = Yi[k] + recon_f<RC>(y[0], y[1], y[2], y[3], y[4], y[5]);
+    YR[k] = Yi[k] + recon_f<RC>(y[5], y[4], y[3], y[2], y[1], y[0]);
   }
 #pragma unroll
   for (int t = 0; t < D; ++t) {
@@ -610,8 +700,8 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
     float y[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) y[j] = wgetf(P, Wc, P.wU + t, cr[j]) * sgnf(cr[j].flip, t) - ut;
-    uL[t] = ut + weno5z_f(y[0], y[1], y[2], y[3], y[4]);
-    uR[t] = ut + weno5z_f(y[5], y[4], y[3], y[2], y[1]);
+    uL[t] = ut + recon_f<RC>(y[0], y[1], y[2], y[3], y[4], y[5]);
+    uR[t] = ut + recon_f<RC>(y[5], y[4], y[3], y[2], y[1], y[0]);
   }
 
   if (P.pos_limiter) {
@@ -888,6 +978,47 @@ __global__ void __launch_bounds__(CELL_THREADS)
 
 inline unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// the mixed face pass of one direction with interpolation RC
+template <int NS, int D, int RC>
+struct FaceImpl {
+  static void face(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* Un, const double* Uk,
+                   const double* Uin, const double* scal, double rk0, double rk1, double rk2, double* F,
+                   uint32_t* flags, unsigned long long* stats) {
+    long long nf = 1;
+    for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
+    const unsigned nb = nblocks(nf, FACE_THREADS);
+    const float* W = reinterpret_cast<const float*>(Wc);
+    if (d == 0)
+      k_face<NS, D, 0, RC><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags, stats);
+    else if (d == 1)
+      k_face<NS, D, (D > 1 ? 1 : 0), RC><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, F,
+                                                                     flags, stats);
+    else
+      k_face<NS, D, (D > 2 ? 2 : 0), RC><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, F,
+                                                                     flags, stats);
+  }
+};
+
+// the mixed face pass of interpolation RC for (dimension, species count)
+template <int RC>
+FaceFn face_mixed(int dim, int ns) {
+  switch (dim * 8 + ns) {
+    case 9: return &FaceImpl<1, 1, RC>::face;
+    case 10: return &FaceImpl<2, 1, RC>::face;
+    case 11: return &FaceImpl<3, 1, RC>::face;
+    case 12: return &FaceImpl<4, 1, RC>::face;
+    case 17: return &FaceImpl<1, 2, RC>::face;
+    case 18: return &FaceImpl<2, 2, RC>::face;
+    case 19: return &FaceImpl<3, 2, RC>::face;
+    case 20: return &FaceImpl<4, 2, RC>::face;
+    case 25: return &FaceImpl<1, 3, RC>::face;
+    case 26: return &FaceImpl<2, 3, RC>::face;
+    case 27: return &FaceImpl<3, 3, RC>::face;
+    case 28: return &FaceImpl<4, 3, RC>::face;
+    default: return nullptr;
+  }
+}
+
 template <int NS, int D>
 struct Impl {
   static void prim(const KParams& P, cudaStream_t s, const double* U, const double* Uin, double* Wc,
@@ -898,18 +1029,7 @@ struct Impl {
   static void face(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* Un, const double* Uk,
                    const double* Uin, const double* scal, double rk0, double rk1, double rk2, double* F,
                    uint32_t* flags, unsigned long long* stats) {
-    long long nf = 1;
-    for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
-    const unsigned nb = nblocks(nf, FACE_THREADS);
-    const float* W = reinterpret_cast<const float*>(Wc);
-    if (d == 0)
-      k_face<NS, D, 0><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags, stats);
-    else if (d == 1)
-      k_face<NS, D, (D > 1 ? 1 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags,
-                                                                 stats);
-    else
-      k_face<NS, D, (D > 2 ? 2 : 0)><<<nb, FACE_THREADS, 0, s>>>(P, W, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags,
-                                                                 stats);
+    FaceImpl<NS, D, RC_WENO5Z>::face(P, s, d, Wc, Un, Uk, Uin, scal, rk0, rk1, rk2, F, flags, stats);
   }
   static void update(const KParams& P, cudaStream_t s, const double* Un, const double* Uk, double* const* F,
                      const double* scal, double rk0, double rk1, double rk2, double* Uout, double* dUdt,

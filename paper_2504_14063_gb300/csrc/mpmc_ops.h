@@ -39,6 +39,10 @@ using FaceFn = decltype(Ops::face);
 FaceFn face_fp64_weno5js(int dim, int ns);
 FaceFn face_fp64_teno5(int dim, int ns);
 FaceFn face_fp64_teno6(int dim, int ns);
+// the same for mixed-precision contexts: mpmc_mixed_recon_{weno5js,teno5,teno6}.cu
+FaceFn face_mixed_weno5js(int dim, int ns);
+FaceFn face_mixed_teno5(int dim, int ns);
+FaceFn face_mixed_teno6(int dim, int ns);
 
 // per-dimension tables, defined in mpmc_kernels_d{1,2,3}.cu (FP64) and
 // mpmc_mixed_d{1,2,3}.cu (mixed precision; init is the FP64 one)

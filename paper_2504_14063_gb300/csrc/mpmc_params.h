@@ -20,7 +20,6 @@ inline int build_params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_mode
     return MPMC_INVALID_ARG;
   if (m->precision != MPMC_FP64 && m->precision != MPMC_MIXED) return MPMC_INVALID_ARG;
   if (m->recon < MPMC_RECON_WENO5Z || m->recon > MPMC_RECON_TENO6) return MPMC_INVALID_ARG;
-  if (m->recon != MPMC_RECON_WENO5Z && m->precision != MPMC_FP64) return MPMC_INVALID_ARG;
   if (m->viscous && (!(m->prandtl > 0.0) || !(m->lambda_liquid >= 0.0))) return MPMC_INVALID_ARG;
   for (int d = 0; d < 3; ++d) {
     if (d < g->dim && g->n[d] < 3) return MPMC_INVALID_ARG;

@@ -80,11 +80,9 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     g.n[0] = 2 ** 31 - 2     # 2^31 - 2 cells + the inflow slot, 2^31 - 1 faces
     assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
     assert h.value is None
-    # interpolations: an unknown kind; TENO6 on a mixed-precision context
+    # an unknown interpolation
     g.n[0] = 16
     m.recon = 4
-    assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
-    m.recon, m.precision = 3, b.MIXED
     assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
     # viscosity with a non-positive Prandtl number
     m.recon, m.viscous, m.precision, m.prandtl = 0, 1, b.FP64, 0.0

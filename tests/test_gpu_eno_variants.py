@@ -3,7 +3,8 @@ FP64 GPU path, through the C ABI, against the oracle: the right-hand side of
 one stage on 1D / 2D / 3D configurations (same bound as the WENO5-Z parity
 tests), 100 SSP-RK3 steps, one step of the benchmarked workload at full
 size, and Table DropAdvectionIECResults after one flow-through; the mixed
-path and the adjoint refuse them."""
+path's FP32 versions within the mixed-precision bound; the adjoint refuses
+them."""
 import json
 import os
 
@@ -13,7 +14,7 @@ import torch
 
 from oracle import Oracle
 from paper_2504_14063_gb300 import workloads as W
-from tests.test_gpu_parity import L1_TOL, NTH, _cuda, _steps_parity, rhs_parity, scaled_l1
+from tests.test_gpu_parity import L1_TOL, NTH, _cuda, _gross, _steps_parity, rhs_parity, scaled_l1
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -101,10 +102,40 @@ def test_paper_droplet_advection_golden_on_gpu(mp, name):
         assert errs[k] <= 5 * ref[k]
 
 
-def test_other_interpolations_need_the_fp64_forward_path(mp):
+@pytest.mark.parametrize("case", ["slab_1d_cdi", "shock_bubble_2d", "shock_droplet_3d"])
+@pytest.mark.parametrize("name", list(KINDS))
+def test_mixed_rhs_close_to_oracle(mp, name, case):
+    """The mixed path's FP32 interpolation: the stage right-hand side within
+    the mixed-precision bound of tests/test_gpu_mixed.py (1e-4 of the
+    oracle's L1 + 1e-7 of the gross flux + 10 x the oracle's own change
+    under a 2^-24 perturbation of its input)."""
+    make, pre = CASES[case]
+    p = _with(make(), name)
+    o = Oracle(p, nthreads=NTH)
+    Un = o.run(o.init_state(), pre)[0]
+    dt, G, _ = o.dt_gamma(Un)
+    Uk = o.stage(Un, Un, (1.0, 0.0, 1.0), dt, G)[0]
+    rk = (0.75, 0.25, 0.25)
+    _, Lo, _, st = o.stage(Un, Uk, rk, dt, G)
+    assert st == 0
+    F, _ = o.face_fluxes(Un, Uk, rk, dt, G)
+    ctx = mp.Context(p, precision=mp.MIXED)
+    Lg = ctx.rhs(_cuda(Uk), stage=dict(U_n=_cuda(Un), rk=rk, dt=dt, Gamma=G)).cpu().numpy()
+    assert ctx.status() == 0
+    rng = np.random.default_rng(1)
+    jit = lambda A: A * (1.0 + 2.0 ** -24 * rng.standard_normal(A.shape))
+    _, Lt, _, _ = o.stage(jit(Un), jit(Uk), rk, dt, G)
+    T32 = np.abs(Lt - Lo).sum(axis=(1, 2, 3))
+    num = np.abs(Lg - Lo).sum(axis=(1, 2, 3))
+    ref = np.abs(Lo).sum(axis=(1, 2, 3))
+    bound = 1e-4 * ref + 1e-7 * _gross(p, F) + 10.0 * T32
+    print(f"mixed {name} rhs {case}: rel err {np.array2string(num / ref, precision=2)}, err/bound "
+          f"{np.array2string(num / bound, precision=2)}")
+    assert np.all(num <= bound)
+
+
+def test_other_interpolations_refused_by_the_adjoint(mp):
     p = _with(W.random_smooth_2d(16, 12, seed=1), "TENO6")
-    with pytest.raises(mp.MpmcError):
-        mp.Context(p, precision=mp.MIXED)
     ctx = mp.Context(p)
     U = ctx.init_state(torch.from_numpy(p.prim))
     with pytest.raises(mp.MpmcError):
