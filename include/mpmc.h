@@ -64,7 +64,8 @@ extern "C" {
 /* ENO-type interpolation of the face states (Sec. 3.1.3; Sec. 4.1 runs all
  * four).  WENO5-Z (Borges et al. 2008) is the method's; the others follow
  * their cited definitions (Jiang & Shu 1996; Fu, Hu & Adams 2016), on FP64
- * and mixed contexts (FP32 there), not in the adjoint. */
+ * and mixed contexts (FP32 there) and in the adjoint (TENO differentiated
+ * with its candidate selection replayed). */
 #define MPMC_RECON_WENO5Z 0
 #define MPMC_RECON_WENO5JS 1 /* eps 1e-6, exponent 2 */
 #define MPMC_RECON_TENO5 2   /* C = 1, q = 6, CT = 1e-5 */
@@ -119,8 +120,7 @@ typedef struct {
   double mu_liquid; /* liquid-phase viscosity [Pa s] */
   int precision;    /* MPMC_FP64 or MPMC_MIXED */
   int recon;        /* MPMC_RECON_*; 0 (WENO5-Z) is the default.  Another value
-                       is refused by mpmc_rhs_noalloc and by the adjoint
-                       entries (MPMC_INVALID_ARG) */
+                       is refused by mpmc_rhs_noalloc (MPMC_INVALID_ARG) */
   int viscous;      /* viscous stress and heat conduction (Eq. DiffusionTerms:
                        tau = mu (grad u + grad u^T - 2/3 div u I),
                        q = -lambda grad T + sum J h), second-order central on

@@ -113,6 +113,106 @@ __device__ __forceinline__ double weno_val_grad(double v0, double v1, double v2,
   return out;
 }
 
+// gradient of the three-cell candidates and indicators: given the adjoints
+// lq[k] of the candidate values and lb[k] of the indicators (k = left,
+// central, right), adds d/dv0..v4 to g
+__device__ __forceinline__ void eno3_rev(double v0, double v1, double v2, double v3, double v4, const double* lq,
+                                         const double* lb, double* g) {
+  const double t0 = v0 - 2.0 * v1 + v2, s0 = v0 - 4.0 * v1 + 3.0 * v2;
+  const double t1 = v1 - 2.0 * v2 + v3, s1 = v1 - v3;
+  const double t2 = v2 - 2.0 * v3 + v4, s2 = 3.0 * v2 - 4.0 * v3 + v4;
+  const double lt0 = lb[0] * (13.0 / 6.0) * t0, ls0 = lb[0] * 0.5 * s0;
+  const double lt1 = lb[1] * (13.0 / 6.0) * t1, ls1 = lb[1] * 0.5 * s1;
+  const double lt2 = lb[2] * (13.0 / 6.0) * t2, ls2 = lb[2] * 0.5 * s2;
+  g[0] += lt0 + ls0 + lq[0] * (2.0 / 6.0);
+  g[1] += -2.0 * lt0 - 4.0 * ls0 + lt1 + ls1 - lq[0] * (7.0 / 6.0) - lq[1] * (1.0 / 6.0);
+  g[2] += lt0 + 3.0 * ls0 - 2.0 * lt1 + lt2 + 3.0 * ls2 + lq[0] * (11.0 / 6.0) + lq[1] * (5.0 / 6.0) +
+          lq[2] * (2.0 / 6.0);
+  g[3] += lt1 - ls1 - 2.0 * lt2 - 4.0 * ls2 + lq[1] * (2.0 / 6.0) + lq[2] * (5.0 / 6.0);
+  g[4] += lt2 + ls2 - lq[2] * (1.0 / 6.0);
+}
+
+// WENO5-JS (alpha_k = d_k / (eps + beta_k)^2, eps = 1e-6): value and
+// gradient w.r.t. v0..v4 (g[5] = 0)
+__device__ __forceinline__ double weno5js_val_grad(double v0, double v1, double v2, double v3, double v4, double* g) {
+  const Eno3 e = eno3(v0, v1, v2, v3, v4);
+  constexpr double eps = 1e-6;
+  const double il = 1.0 / (eps + e.bl), ic = 1.0 / (eps + e.bc), ir = 1.0 / (eps + e.br);
+  const double A[3] = {0.1 * il * il, 0.6 * ic * ic, 0.3 * ir * ir};
+  const double q[3] = {e.ql, e.qc, e.qr}, ib[3] = {il, ic, ir};
+  const double S = A[0] + A[1] + A[2];
+  const double out = (A[0] * q[0] + A[1] * q[1] + A[2] * q[2]) / S;
+  // out = sum A_k q_k / S: dA_k -> (q_k - out) / S; dq_k -> A_k / S;
+  // dA_k / dbeta_k = -2 A_k / (eps + beta_k)
+  double lq[3], lb[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lq[k] = A[k] / S;
+    lb[k] = (q[k] - out) / S * (-2.0 * A[k] * ib[k]);
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) g[j] = 0.0;
+  eno3_rev(v0, v1, v2, v3, v4, lq, lb, g);
+  return out;
+}
+
+// TENO5 / TENO6: with the kept candidates fixed by the forward values (the
+// replayed decision) the value is linear in v; its gradient is the kept
+// candidates' coefficients with their renormalized optimal weights
+template <int RC>
+__device__ __forceinline__ double teno_val_grad(double v0, double v1, double v2, double v3, double v4, double v5,
+                                                double* g) {
+  const Eno3 e = eno3(v0, v1, v2, v3, v4);
+  constexpr int K = RC == RC_TENO6 ? 4 : 3;
+  // candidate coefficients on v0..v5: central, left, right, right four-cell
+  const double cf[4][6] = {{0.0, -1.0 / 6.0, 5.0 / 6.0, 2.0 / 6.0, 0.0, 0.0},
+                           {2.0 / 6.0, -7.0 / 6.0, 11.0 / 6.0, 0.0, 0.0, 0.0},
+                           {0.0, 0.0, 2.0 / 6.0, 5.0 / 6.0, -1.0 / 6.0, 0.0},
+                           {0.0, 0.0, 3.0 / 12.0, 13.0 / 12.0, -5.0 / 12.0, 1.0 / 12.0}};
+  unsigned kept;
+  double q[4] = {e.qc, e.ql, e.qr, 0.0};
+  const double* dk;
+  if constexpr (RC == RC_TENO6) {
+    kept = teno6_kept(e, v0, v1, v2, v3, v4, v5);
+    q[3] = (3.0 * v2 + 13.0 * v3 - 5.0 * v4 + v5) * (1.0 / 12.0);
+    dk = TENO6_D;
+  } else {
+    kept = teno5_kept(e);
+    dk = TENO5_D;
+  }
+  const double out = teno_combine<K>(q, dk, kept);
+  double den = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (kept & (1u << k)) den += dk[k];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) g[j] = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (kept & (1u << k)) {
+      const double w = dk[k] / den;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) g[j] += w * cf[k][j];
+    }
+  return out;
+}
+
+// value and gradient w.r.t. the six stencil values of the interpolation RC
+// (left side: cells i-2..i+3; right side: the same cells mirrored)
+template <int RC>
+__device__ __forceinline__ double recon_val_grad(double v0, double v1, double v2, double v3, double v4, double v5,
+                                                 double eps, double* g) {
+  if constexpr (RC == RC_WENO5JS) {
+    return weno5js_val_grad(v0, v1, v2, v3, v4, g);
+  } else if constexpr (RC == RC_TENO5 || RC == RC_TENO6) {
+    return teno_val_grad<RC>(v0, v1, v2, v3, v4, v5, g);
+  } else {
+    const double out = weno_val_grad(v0, v1, v2, v3, v4, eps, g);
+    g[5] = 0.0;
+    return out;
+  }
+}
+
 // adds d(out)/d(v) * lam to gv[0..4]
 __device__ __forceinline__ void weno_rev(const Weno& w, double lam, double* gv) {
   if (w.flat) {

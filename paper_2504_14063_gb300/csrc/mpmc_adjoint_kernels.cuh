@@ -165,8 +165,9 @@ __device__ __forceinline__ void face_avg_rev(const KParams& P, const FaceAvg<NS,
 }
 
 // DIR: the face direction, a template parameter so that every array indexed
-// by it is indexed by a constant
-template <int NS, int D, int DIR>
+// by it is indexed by a constant.  RC: the interpolation (RC_WENO5Z or one of
+// Sec. 4.1's others)
+template <int NS, int D, int DIR, int RC>
 __global__ void __launch_bounds__(VJP_THREADS)
     k_face_adj(const KParams P, const double* __restrict__ Wc, const double* __restrict__ Uk,
                const double* __restrict__ Uin, const double* __restrict__ scal, const uint32_t* __restrict__ tape,
@@ -224,8 +225,10 @@ __global__ void __launch_bounds__(VJP_THREADS)
   const double X = fa.X, c = fa.c, ic = 1.0 / c;
   // reconstruction values with their gradients w.r.t. the stencil values
   double TL, TR, PL, PR, uL[3] = {0.0, 0.0, 0.0}, uR[3] = {0.0, 0.0, 0.0};
-  double g1L[5], g1R[5], g5L[5], g5R[5], g6L[5], g6R[5], w5L, w5R, w6L, w6R;
-  double gYL[NS][5], gYR[NS][5], gtL[2][5], gtR[2][5];
+  // gradients over the six stencil cells (the last entry zero for the
+  // five-cell interpolations); the right side's gradient index runs mirrored
+  double g1L[6], g1R[6], g5L[6], g5R[6], g6L[6], g6R[6], w5L, w5R, w6L, w6R;
+  double gYL[NS][6], gYR[NS][6], gtL[2][6], gtR[2][6];
   {
     double w1[6], w5[6], w6[6];
 #pragma unroll
@@ -236,12 +239,12 @@ __global__ void __launch_bounds__(VJP_THREADS)
       w5[j] = (0.5 * c) * un + 0.5 * Pj_;
       w6[j] = (-0.5 * c) * un + 0.5 * Pj_;
     }
-    const double w1L = weno_val_grad(w1[0], w1[1], w1[2], w1[3], w1[4], eps, g1L);
-    const double w1R = weno_val_grad(w1[5], w1[4], w1[3], w1[2], w1[1], eps, g1R);
-    w5L = weno_val_grad(w5[0], w5[1], w5[2], w5[3], w5[4], eps, g5L);
-    w5R = weno_val_grad(w5[5], w5[4], w5[3], w5[2], w5[1], eps, g5R);
-    w6L = weno_val_grad(w6[0], w6[1], w6[2], w6[3], w6[4], eps, g6L);
-    w6R = weno_val_grad(w6[5], w6[4], w6[3], w6[2], w6[1], eps, g6R);
+    const double w1L = recon_val_grad<RC>(w1[0], w1[1], w1[2], w1[3], w1[4], w1[5], eps, g1L);
+    const double w1R = recon_val_grad<RC>(w1[5], w1[4], w1[3], w1[2], w1[1], w1[0], eps, g1R);
+    w5L = recon_val_grad<RC>(w5[0], w5[1], w5[2], w5[3], w5[4], w5[5], eps, g5L);
+    w5R = recon_val_grad<RC>(w5[5], w5[4], w5[3], w5[2], w5[1], w5[0], eps, g5R);
+    w6L = recon_val_grad<RC>(w6[0], w6[1], w6[2], w6[3], w6[4], w6[5], eps, g6L);
+    w6R = recon_val_grad<RC>(w6[5], w6[4], w6[3], w6[2], w6[1], w6[0], eps, g6R);
     TL = w1L + X * w5L + X * w6L;
     TR = w1R + X * w5R + X * w6R;
     uL[d] = ic * w5L + (-ic) * w6L;
@@ -254,8 +257,8 @@ __global__ void __launch_bounds__(VJP_THREADS)
   for (int k = 0; k < NS; ++k) {
     double y[6];
     stencil(P.wY + k, -1, y);
-    YLp[k] = weno_val_grad(y[0], y[1], y[2], y[3], y[4], eps, gYL[k]);
-    YRp[k] = weno_val_grad(y[5], y[4], y[3], y[2], y[1], eps, gYR[k]);
+    YLp[k] = recon_val_grad<RC>(y[0], y[1], y[2], y[3], y[4], y[5], eps, gYL[k]);
+    YRp[k] = recon_val_grad<RC>(y[5], y[4], y[3], y[2], y[1], y[0], eps, gYR[k]);
   }
   {
     int tt = 0;
@@ -264,8 +267,8 @@ __global__ void __launch_bounds__(VJP_THREADS)
       if (t == d) continue;
       double y[6];
       stencil(P.wU + t, t, y);
-      uL[t] = weno_val_grad(y[0], y[1], y[2], y[3], y[4], eps, gtL[tt]);
-      uR[t] = weno_val_grad(y[5], y[4], y[3], y[2], y[1], eps, gtR[tt]);
+      uL[t] = recon_val_grad<RC>(y[0], y[1], y[2], y[3], y[4], y[5], eps, gtL[tt]);
+      uR[t] = recon_val_grad<RC>(y[5], y[4], y[3], y[2], y[1], y[0], eps, gtR[tt]);
       ++tt;
     }
   }
@@ -645,10 +648,8 @@ __global__ void __launch_bounds__(VJP_THREADS)
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     double gj[6];
-    gj[0] = lYL[k] * gYL[k][0];
-    gj[5] = lYR[k] * gYR[k][0];
 #pragma unroll
-    for (int j = 1; j < 5; ++j) gj[j] = lYL[k] * gYL[k][j] + lYR[k] * gYR[k][5 - j];
+    for (int j = 0; j < 6; ++j) gj[j] = lYL[k] * gYL[k][j] + lYR[k] * gYR[k][5 - j];
     gj[2] += aY[0][k];
     gj[3] += aY[1][k];
 #pragma unroll
@@ -660,10 +661,8 @@ __global__ void __launch_bounds__(VJP_THREADS)
     for (int t = 0; t < D; ++t) {
       if (t == d) continue;
       double gj[6];
-      gj[0] = luL[t] * gtL[tt][0];
-      gj[5] = luR[t] * gtR[tt][0];
 #pragma unroll
-      for (int j = 1; j < 5; ++j) gj[j] = luL[t] * gtL[tt][j] + luR[t] * gtR[tt][5 - j];
+      for (int j = 0; j < 6; ++j) gj[j] = luL[t] * gtL[tt][j] + luR[t] * gtR[tt][5 - j];
       gj[2] += aU3[0][t];
       gj[3] += aU3[1][t];
 #pragma unroll
@@ -684,10 +683,10 @@ __global__ void __launch_bounds__(VJP_THREADS)
     lc = -lic * ic * ic;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      // left stencil v = w[0..4], right stencil v = w[5..1]
-      const double lw1 = (j < 5 ? l1L * g1L[j] : 0.0) + (j > 0 ? l1R * g1R[5 - j] : 0.0);
-      const double lw5 = (j < 5 ? l5L * g5L[j] : 0.0) + (j > 0 ? l5R * g5R[5 - j] : 0.0);
-      const double lw6 = (j < 5 ? l6L * g6L[j] : 0.0) + (j > 0 ? l6R * g6R[5 - j] : 0.0);
+      // left stencil v = w[0..5], right stencil v = w[5..0]
+      const double lw1 = l1L * g1L[j] + l1R * g1R[5 - j];
+      const double lw5 = l5L * g5L[j] + l5R * g5R[5 - j];
+      const double lw6 = l6L * g6L[j] + l6R * g6R[5 - j];
       const double Pj_ = wget(P, Wc, P.wP, cr[j]);
       const double un = wget(P, Wc, P.wU + d, cr[j]) * sgn_flip(cr[j].flip, d);
       double gT_ = lw1;
@@ -1143,9 +1142,9 @@ __global__ void __launch_bounds__(CELL_THREADS)
   lprim[(long long)(NS + D + 1) * n + c] = lT;
 }
 
-template <int NS, int D>
-struct AdjImpl {
-  static int slots(const KParams& P) { return Lay<NS, D>(P.cdi, P.diffusion).total; }
+// the adjoint face pass of one direction with interpolation RC
+template <int NS, int D, int RC>
+struct AdjFaceImpl {
   static void face(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* Uk, const double* Uin,
                    const double* scal, const uint32_t* tape, const double* lamL, double coef, int mul_dt,
                    double* C) {
@@ -1153,11 +1152,43 @@ struct AdjImpl {
     for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
     const unsigned nb = nblocks(nf, VJP_THREADS);
     if (d == 0)
-      k_face_adj<NS, D, 0><<<nb, VJP_THREADS, 0, s>>>(P, Wc, Uk, Uin, scal, tape, lamL, coef, mul_dt, C);
+      k_face_adj<NS, D, 0, RC><<<nb, VJP_THREADS, 0, s>>>(P, Wc, Uk, Uin, scal, tape, lamL, coef, mul_dt, C);
     else if (d == 1)
-      k_face_adj<NS, D, (D > 1 ? 1 : 0)><<<nb, VJP_THREADS, 0, s>>>(P, Wc, Uk, Uin, scal, tape, lamL, coef, mul_dt, C);
+      k_face_adj<NS, D, (D > 1 ? 1 : 0), RC><<<nb, VJP_THREADS, 0, s>>>(P, Wc, Uk, Uin, scal, tape, lamL, coef,
+                                                                        mul_dt, C);
     else
-      k_face_adj<NS, D, (D > 2 ? 2 : 0)><<<nb, VJP_THREADS, 0, s>>>(P, Wc, Uk, Uin, scal, tape, lamL, coef, mul_dt, C);
+      k_face_adj<NS, D, (D > 2 ? 2 : 0), RC><<<nb, VJP_THREADS, 0, s>>>(P, Wc, Uk, Uin, scal, tape, lamL, coef,
+                                                                        mul_dt, C);
+  }
+};
+
+// the adjoint face pass of interpolation RC for (dimension, species count)
+template <int RC>
+AdjFaceFn adj_face(int dim, int ns) {
+  switch (dim * 8 + ns) {
+    case 9: return &AdjFaceImpl<1, 1, RC>::face;
+    case 10: return &AdjFaceImpl<2, 1, RC>::face;
+    case 11: return &AdjFaceImpl<3, 1, RC>::face;
+    case 12: return &AdjFaceImpl<4, 1, RC>::face;
+    case 17: return &AdjFaceImpl<1, 2, RC>::face;
+    case 18: return &AdjFaceImpl<2, 2, RC>::face;
+    case 19: return &AdjFaceImpl<3, 2, RC>::face;
+    case 20: return &AdjFaceImpl<4, 2, RC>::face;
+    case 25: return &AdjFaceImpl<1, 3, RC>::face;
+    case 26: return &AdjFaceImpl<2, 3, RC>::face;
+    case 27: return &AdjFaceImpl<3, 3, RC>::face;
+    case 28: return &AdjFaceImpl<4, 3, RC>::face;
+    default: return nullptr;
+  }
+}
+
+template <int NS, int D>
+struct AdjImpl {
+  static int slots(const KParams& P) { return Lay<NS, D>(P.cdi, P.diffusion).total; }
+  static void face(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* Uk, const double* Uin,
+                   const double* scal, const uint32_t* tape, const double* lamL, double coef, int mul_dt,
+                   double* C) {
+    AdjFaceImpl<NS, D, RC_WENO5Z>::face(P, s, d, Wc, Uk, Uin, scal, tape, lamL, coef, mul_dt, C);
   }
   static void gather(const KParams& P, cudaStream_t s, int d, const double* C, int first, double* gW, double* gU) {
     const unsigned nb = nblocks(P.ncell, CELL_THREADS);

@@ -192,9 +192,16 @@ extern "C" int mpmc_create(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_m
     case 2: c->aops = adj_ops_d2(ns); break;
     default: c->aops = adj_ops_d3(ns); break;
   }
-  if (P.recon == MPMC_RECON_WENO5JS) c->ops.face = mixed ? face_mixed_weno5js(D, ns) : face_fp64_weno5js(D, ns);
-  else if (P.recon == MPMC_RECON_TENO5) c->ops.face = mixed ? face_mixed_teno5(D, ns) : face_fp64_teno5(D, ns);
-  else if (P.recon == MPMC_RECON_TENO6) c->ops.face = mixed ? face_mixed_teno6(D, ns) : face_fp64_teno6(D, ns);
+  if (P.recon == MPMC_RECON_WENO5JS) {
+    c->ops.face = mixed ? face_mixed_weno5js(D, ns) : face_fp64_weno5js(D, ns);
+    c->aops.face = adj_face_weno5js(D, ns);
+  } else if (P.recon == MPMC_RECON_TENO5) {
+    c->ops.face = mixed ? face_mixed_teno5(D, ns) : face_fp64_teno5(D, ns);
+    c->aops.face = adj_face_teno5(D, ns);
+  } else if (P.recon == MPMC_RECON_TENO6) {
+    c->ops.face = mixed ? face_mixed_teno6(D, ns) : face_fp64_teno6(D, ns);
+    c->aops.face = adj_face_teno6(D, ns);
+  }
   if (!c->ops.face || !c->aops.face) {
     delete c;
     return MPMC_INVALID_ARG;
@@ -424,8 +431,6 @@ extern "C" int mpmc_dt_gamma(mpmc_ctx* c, const double* U, double* out_dev) {
 // discrete adjoint (FP64 contexts)
 static int ensure_adjoint(mpmc_ctx* c) {
   if (c->precision != MPMC_FP64) return fail(c, MPMC_INVALID_ARG, "adjoint: needs an FP64 context");
-  if (c->P.recon != MPMC_RECON_WENO5Z)
-    return fail(c, MPMC_INVALID_ARG, "adjoint: the reverse kernels differentiate WENO5-Z only");
   if (c->P.viscous) return fail(c, MPMC_INVALID_ARG, "adjoint: viscous stress and conduction are not reversed");
   const KParams& P = c->P;
   int rc = MPMC_OK;

@@ -505,10 +505,9 @@ __device__ __forceinline__ double weno5js(double v0, double v1, double v2, doubl
 
 // TENO selection: r_k = C + tau / (beta_k + eps); chi_k = r_k^q / sum r^q,
 // formed from r_k / max r (r_k^6 overflows beside a large jump); candidates
-// with chi_k < CT are cut off, the rest combine with their optimal weights
+// with chi_k < CT are cut off (bit k of the result clear)
 template <int K>
-__device__ __forceinline__ double teno_select(const double* q, const double* b, const double* dk, double tau,
-                                              double CT) {
+__device__ __forceinline__ unsigned teno_kept(const double* b, double tau, double CT) {
   double r[K], rmax = 0.0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -523,10 +522,20 @@ __device__ __forceinline__ double teno_select(const double* q, const double* b, 
     g[k] = x2 * x2 * x2;
     gs += g[k];
   }
+  unsigned kept = 0u;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (!(g[k] < CT * gs)) kept |= 1u << k;
+  return kept;
+}
+
+// the kept candidates with their optimal weights renormalized
+template <int K>
+__device__ __forceinline__ double teno_combine(const double* q, const double* dk, unsigned kept) {
   double num = 0.0, den = 0.0;
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    if (!(g[k] < CT * gs)) {
+    if (kept & (1u << k)) {
       num += dk[k] * q[k];
       den += dk[k];
     }
@@ -535,10 +544,18 @@ __device__ __forceinline__ double teno_select(const double* q, const double* b, 
 
 // TENO5: optimal weights (3/5, 1/10, 3/10) for (central, left, right),
 // tau5 = |beta_left - beta_right|
+__device__ constexpr double TENO5_D[3] = {0.6, 0.1, 0.3};
+__device__ constexpr double TENO6_D[4] = {0.45, 0.05, 0.3, 0.2};
+
+__device__ __forceinline__ unsigned teno5_kept(const Eno3& e) {
+  const double b[3] = {e.bc, e.bl, e.br};
+  return teno_kept<3>(b, fabs(e.bl - e.br), 1e-5);
+}
+
 __device__ __forceinline__ double teno5(double v0, double v1, double v2, double v3, double v4) {
   const Eno3 e = eno3(v0, v1, v2, v3, v4);
-  const double q[3] = {e.qc, e.ql, e.qr}, b[3] = {e.bc, e.bl, e.br}, dk[3] = {0.6, 0.1, 0.3};
-  return teno_select<3>(q, b, dk, fabs(e.bl - e.br), 1e-5);
+  const double q[3] = {e.qc, e.ql, e.qr};
+  return teno_combine<3>(q, TENO5_D, teno5_kept(e));
 }
 
 // TENO6: adds the four-cell candidate i..i+3; optimal weights
@@ -547,11 +564,10 @@ __device__ __forceinline__ double teno5(double v0, double v1, double v2, double 
 // and six-cell Jiang-Shu indicators are written as positive multiples of
 // squared zero-sum combinations (exact rational coefficients), evaluated on
 // deviations from cell i.
-__device__ __forceinline__ double teno6(double v0, double v1, double v2, double v3, double v4, double v5) {
-  const Eno3 e = eno3(v0, v1, v2, v3, v4);
-  const double q4 = (3.0 * v2 + 13.0 * v3 - 5.0 * v4 + v5) * (1.0 / 12.0);
+__device__ __forceinline__ unsigned teno6_kept(const Eno3& e, double v0, double v1, double v2, double v3, double v4,
+                                               double v5) {
   const double e0 = v0 - v2, e1 = v1 - v2, e3 = v3 - v2, e4 = v4 - v2, e5 = v5 - v2;
-  double s = 18.0 * e3 - 9.0 * e4 + 2.0 * e5, t = -5.0 * e3 + 4.0 * e4 - e5, u = 3.0 * e3 - 3.0 * e4 + e5;
+  const double s = 18.0 * e3 - 9.0 * e4 + 2.0 * e5, t = -5.0 * e3 + 4.0 * e4 - e5, u = 3.0 * e3 - 3.0 * e4 + e5;
   const double b4 = (1.0 / 36.0) * s * s + (13.0 / 12.0) * t * t + (781.0 / 720.0) * u * u;
   const double c1 = 3.0 * e0 - 30.0 * e1 + 60.0 * e3 - 15.0 * e4 + 2.0 * e5;
   const double c2 = -11.0 * e0 + 174.0 * e1 + 174.0 * e3 - 11.0 * e4;
@@ -560,8 +576,14 @@ __device__ __forceinline__ double teno6(double v0, double v1, double v2, double 
   const double c5 = -e0 + 5.0 * e1 + 10.0 * e3 - 5.0 * e4 + e5;
   const double b6 = (1.0 / 3600.0) * c1 * c1 + (1.0 / 15600.0) * c2 * c2 + (1.0 / 3967729920.0) * c3 * c3 +
                     (1421461.0 / 1310400.0) * c4 * c4 + (21520059541.0 / 19838649600.0) * c5 * c5;
-  const double q[4] = {e.qc, e.ql, e.qr, q4}, b[4] = {e.bc, e.bl, e.br, b4}, dk[4] = {0.45, 0.05, 0.3, 0.2};
-  return teno_select<4>(q, b, dk, fabs(b6 - (e.bl + e.br + 4.0 * e.bc) * (1.0 / 6.0)), 1e-7);
+  const double b[4] = {e.bc, e.bl, e.br, b4};
+  return teno_kept<4>(b, fabs(b6 - (e.bl + e.br + 4.0 * e.bc) * (1.0 / 6.0)), 1e-7);
+}
+
+__device__ __forceinline__ double teno6(double v0, double v1, double v2, double v3, double v4, double v5) {
+  const Eno3 e = eno3(v0, v1, v2, v3, v4);
+  const double q[4] = {e.qc, e.ql, e.qr, (3.0 * v2 + 13.0 * v3 - 5.0 * v4 + v5) * (1.0 / 12.0)};
+  return teno_combine<4>(q, TENO6_D, teno6_kept(e, v0, v1, v2, v3, v4, v5));
 }
 
 // the interpolation of kind RC on the stencil v0..v5 (left side: cells

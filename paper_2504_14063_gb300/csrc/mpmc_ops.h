@@ -44,6 +44,13 @@ FaceFn face_mixed_weno5js(int dim, int ns);
 FaceFn face_mixed_teno5(int dim, int ns);
 FaceFn face_mixed_teno6(int dim, int ns);
 
+using AdjFaceFn = decltype(AdjOps::face);
+// adjoint face passes with Sec. 4.1's other interpolations:
+// mpmc_adjoint_recon_{weno5js,teno5,teno6}.cu
+AdjFaceFn adj_face_weno5js(int dim, int ns);
+AdjFaceFn adj_face_teno5(int dim, int ns);
+AdjFaceFn adj_face_teno6(int dim, int ns);
+
 // per-dimension tables, defined in mpmc_kernels_d{1,2,3}.cu (FP64) and
 // mpmc_mixed_d{1,2,3}.cu (mixed precision; init is the FP64 one)
 Ops ops_fp64_d1(int ns);

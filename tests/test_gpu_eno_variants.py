@@ -3,8 +3,8 @@ FP64 GPU path, through the C ABI, against the oracle: the right-hand side of
 one stage on 1D / 2D / 3D configurations (same bound as the WENO5-Z parity
 tests), 100 SSP-RK3 steps, one step of the benchmarked workload at full
 size, and Table DropAdvectionIECResults after one flow-through; the mixed
-path's FP32 versions within the mixed-precision bound; the adjoint refuses
-them."""
+path's FP32 versions within the mixed-precision bound; the discrete adjoint
+of each (dot products against the oracle's forward-mode tangent)."""
 import json
 import os
 
@@ -14,7 +14,9 @@ import torch
 
 from oracle import Oracle
 from paper_2504_14063_gb300 import workloads as W
+from tests.test_gpu_adjoint import _dot_check
 from tests.test_gpu_parity import L1_TOL, NTH, _cuda, _gross, _steps_parity, rhs_parity, scaled_l1
+from tests.test_oracle_jvp import _modulated, _state_and_dir
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -134,9 +136,44 @@ def test_mixed_rhs_close_to_oracle(mp, name, case):
     assert np.all(num <= bound)
 
 
-def test_other_interpolations_refused_by_the_adjoint(mp):
-    p = _with(W.random_smooth_2d(16, 12, seed=1), "TENO6")
+ADJ_CASES = {
+    "smooth_2d_cdi_diff": lambda: W.random_smooth_2d(24, 20, seed=3, cdi=1, diffusion=1),
+    "shock_bubble_2d": lambda: _modulated(W.shock_bubble_2d(nx=48, ny=28, seed=1)),
+    "droplet_3d": lambda: _modulated(W.droplet_field_3d(n=14, ndrops=2, seed=2, rmin=2.5, rmax=3.5)),
+}
+
+
+@pytest.mark.parametrize("case", list(ADJ_CASES))
+@pytest.mark.parametrize("name", list(KINDS))
+def test_rhs_adjoint_dot_product(mp, name, case):
+    """<lam, J dU> from the oracle's forward-mode tangent (TENO's candidate
+    selection held at the point, WENO5-JS differentiated through its weights)
+    = <J^T lam, dU> from the GPU adjoint, within 1e-9 of the gross sum."""
+    p = _with(ADJ_CASES[case](), name)
+    o = Oracle(p, nthreads=NTH)
+    U, dU = _state_and_dir(o, p, np.random.default_rng(5))
+    dt, G, _ = o.dt_gamma(U)
+    rk = (0.75, 0.25, 0.25)
+    Un = o.rk_step(U, 0.3 * dt)[0]
+    _, dL, st = o.stage_jvp(Un, U, dU, rk, dt, G)
+    assert st == 0
+    lam = np.random.default_rng(9).standard_normal(U.shape)
     ctx = mp.Context(p)
-    U = ctx.init_state(torch.from_numpy(p.prim))
-    with pytest.raises(mp.MpmcError):
-        ctx.rk_step_adjoint(U, torch.zeros_like(U), dt=1e-9)
+    lamU = ctx.rhs_adjoint(_cuda(U), dict(U_n=_cuda(Un), rk=rk, dt=dt, Gamma=G), None, _cuda(lam)).cpu().numpy()
+    assert ctx.status() == 0
+    _dot_check((lam * dL).sum(), (lamU * dU).sum(), np.abs(lam * dL).sum(), f"rhs {name} {case}")
+
+
+@pytest.mark.parametrize("name", list(KINDS))
+def test_rk_step_adjoint_dot_product(mp, name):
+    p = _with(_modulated(W.shock_bubble_2d(nx=48, ny=28, seed=1)), name)
+    o = Oracle(p, nthreads=NTH)
+    U, dU = _state_and_dir(o, p, np.random.default_rng(6))
+    ctx = mp.Context(p)
+    dt, G = (float(x) for x in ctx.dt_gamma(_cuda(U)).cpu())
+    _, dU1, st = o.rk_step_jvp(U, dU, dt, G)
+    assert st == 0
+    lam = np.random.default_rng(10).standard_normal(U.shape)
+    lam_n = ctx.rk_step_adjoint(_cuda(U), _cuda(lam), dt=dt).cpu().numpy()
+    assert ctx.status() == 0
+    _dot_check((lam * dU1).sum(), (lam_n * dU).sum(), np.abs(lam * dU1).sum(), f"rk step {name}")

@@ -227,3 +227,27 @@ def test_teno_keeps_equilibrium_even_in_the_five_equation_basis(name):
     eP, eT, eu = _iec_errors(o, U)
     print(f"{name} [rhoY, u, P] basis after 2000 steps: P {eP:.2e} T {eT:.2e} u {eu:.2e}")
     assert max(eP, eT, eu) < 1e-10
+
+
+@pytest.mark.parametrize("name", list(KINDS))
+def test_stage_tangent_matches_central_differences(name):
+    """The oracle's forward-mode tangent of a stage with this interpolation
+    (the reference gradient of the GPU adjoint): central differences along a
+    smooth primitive-space direction, TENO's candidate selection unchanged
+    within +-h on this state."""
+    from tests.test_oracle_jvp import _modulated, _state_and_dir
+    p = _modulated(W.shock_bubble_2d(nx=48, ny=28, seed=1))
+    p.model.recon = KINDS[name]
+    o = Oracle(p, nthreads=8)
+    U, dU = _state_and_dir(o, p, np.random.default_rng(5))
+    dt, G, _ = o.dt_gamma(U)
+    rk = (0.75, 0.25, 0.25)
+    Un = o.rk_step(U, 0.3 * dt)[0]
+    _, dL, st = o.stage_jvp(Un, U, dU, rk, dt, G)
+    assert st == 0
+    h = 1e-7
+    Lp = o.stage(Un, U + h * dU, rk, dt, G)[1]
+    Lm = o.stage(Un, U - h * dU, rk, dt, G)[1]
+    err = np.abs((Lp - Lm) / (2 * h) - dL).sum() / np.abs(dL).sum()
+    print(f"{name}: tangent vs central differences {err:.2e}")
+    assert err < 1e-6
