@@ -557,6 +557,23 @@ R teno_select(int K, const R* q, const R* beta, const double* d, const R& tau, d
   return num / den;
 }
 
+/* reading (derivative only, as for WENO5-Z): on a stencil flat to rounding
+ * (every indicator below (WENO_FLAT max|v|)^2) the candidates TENO keeps are
+ * chosen by rounding noise while every candidate is the value to rounding;
+ * the tangent there is that of the linear scheme (all candidates kept) */
+template <class R>
+R teno_flat_tangent(const R* v, int nv, int K, const R* q, const R* beta, const double* d, const R& out) {
+  if (!is_dual<R>::value) return out;
+  double M = 0.0;
+  for (int j = 0; j < nv; ++j) M = std::max(M, std::fabs(val(v[j])));
+  const double tol = (WENO_FLAT * M) * (WENO_FLAT * M);
+  for (int k = 0; k < K; ++k)
+    if (val(beta[k]) > tol) return out;
+  R lin(0.0);
+  for (int k = 0; k < K; ++k) lin = lin + d[k] * q[k];
+  return with_value(lin, val(out));
+}
+
 /* TENO5: candidates central (i-1..i+1), left (i-2..i), right (i..i+2) with
  * optimal weights (3/5, 1/10, 3/10); tau5 = |beta_left - beta_right|;
  * reading: CT = 1e-5 */
@@ -575,7 +592,8 @@ R teno5(const R* v) {
   const R br = (13.0 / 12.0) * t * t + 0.25 * s * s;
   const R q[3] = {qc, ql, qr}, beta[3] = {bc, bl, br};
   const double d[3] = {0.6, 0.1, 0.3};
-  return teno_select(3, q, beta, d, fabs(bl - br), 1e-5);
+  const R out = teno_select(3, q, beta, d, fabs(bl - br), 1e-5);
+  return teno_flat_tangent(v, 5, 3, q, beta, d, out);
 }
 
 /* TENO6: TENO5's three candidates plus the four-cell right candidate
@@ -605,7 +623,8 @@ R teno6(const R* v) {
   const R b6 = jiang_shu_beta(a6, 6);
   const R q[4] = {qc, ql, qr, q4}, beta[4] = {bc, bl, br, b4};
   const double d[4] = {0.45, 0.05, 0.3, 0.2};
-  return teno_select(4, q, beta, d, fabs(b6 - (bl + br + 4.0 * bc) / 6.0), 1e-7);
+  const R out = teno_select(4, q, beta, d, fabs(b6 - (bl + br + 4.0 * bc) / 6.0), 1e-7);
+  return teno_flat_tangent(v, 6, 4, q, beta, d, out);
 }
 
 /* the interpolation the model selects (ORC_RECON_*) */

@@ -181,6 +181,22 @@ __device__ __forceinline__ double teno_val_grad(double v0, double v1, double v2,
     dk = TENO5_D;
   }
   const double out = teno_combine<K>(q, dk, kept);
+  // on a stencil flat to rounding the selection is rounding noise: the
+  // derivative is the linear scheme's (every candidate kept), as the
+  // oracle's tangent takes it
+  {
+    double M = fmax(fmax(fabs(v0), fabs(v1)), fmax(fmax(fabs(v2), fabs(v3)), fabs(v4)));
+    if constexpr (RC == RC_TENO6) M = fmax(M, fabs(v5));
+    const double tol = (WENO_FLAT * M) * (WENO_FLAT * M);
+    bool flat = e.bl <= tol && e.bc <= tol && e.br <= tol;
+    if constexpr (RC == RC_TENO6) {
+      const double e3 = v3 - v2, e4 = v4 - v2, e5 = v5 - v2;
+      const double s = 18.0 * e3 - 9.0 * e4 + 2.0 * e5, t = -5.0 * e3 + 4.0 * e4 - e5, u = 3.0 * e3 - 3.0 * e4 + e5;
+      const double b4 = (1.0 / 36.0) * s * s + (13.0 / 12.0) * t * t + (781.0 / 720.0) * u * u;
+      flat = flat && b4 <= tol;
+    }
+    if (flat) kept = (1u << K) - 1u;
+  }
   double den = 0.0;
 #pragma unroll
   for (int k = 0; k < K; ++k)

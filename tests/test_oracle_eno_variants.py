@@ -233,8 +233,9 @@ def test_teno_keeps_equilibrium_even_in_the_five_equation_basis(name):
 def test_stage_tangent_matches_central_differences(name):
     """The oracle's forward-mode tangent of a stage with this interpolation
     (the reference gradient of the GPU adjoint): central differences along a
-    smooth primitive-space direction, TENO's candidate selection unchanged
-    within +-h on this state."""
+    smooth primitive-space direction on the shock-bubble state (as the
+    WENO5-Z tangent pins; the stiff multi-liquid droplet field is covered by
+    the GPU dot products against this tangent)."""
     from tests.test_oracle_jvp import _modulated, _state_and_dir
     p = _modulated(W.shock_bubble_2d(nx=48, ny=28, seed=1))
     p.model.recon = KINDS[name]
