@@ -13,54 +13,13 @@ namespace mpmc {
 namespace adj {
 
 // ---------------------------------------------------------------------------
-// WENO5-Z (the kernel's form with one common denominator) and its reverse
-struct Weno {
-  double v[5], q[3], t[3], s[3], c[3], A[3], tau, S, out;
-  int sg;
-  bool flat;
-};
-
 // relative stencil variation below which the weights are noise: the
 // derivative there is taken with the ideal weights (the value is each
 // candidate to rounding, and the weights' own derivative grows like 1/eps)
 constexpr double WENO_FLAT = 1e-10;
 
-__device__ __forceinline__ double weno_fwd(Weno& w, double v0, double v1, double v2, double v3, double v4,
-                                           double eps) {
-  w.v[0] = v0; w.v[1] = v1; w.v[2] = v2; w.v[3] = v3; w.v[4] = v4;
-  w.q[0] = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
-  w.q[1] = (-v1 + 5.0 * v2 + 2.0 * v3) * (1.0 / 6.0);
-  w.q[2] = (2.0 * v2 + 5.0 * v3 - v4) * (1.0 / 6.0);
-  w.t[0] = v0 - 2.0 * v1 + v2;
-  w.s[0] = v0 - 4.0 * v1 + 3.0 * v2;
-  w.t[1] = v1 - 2.0 * v2 + v3;
-  w.s[1] = v1 - v3;
-  w.t[2] = v2 - 2.0 * v3 + v4;
-  w.s[2] = 3.0 * v2 - 4.0 * v3 + v4;
-  double b[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) b[k] = (13.0 / 12.0) * w.t[k] * w.t[k] + 0.25 * w.s[k] * w.s[k];
-  {
-    double M = 0.0;
-#pragma unroll
-    for (int j = 0; j < 5; ++j) M = fmax(M, fabs(w.v[j]));
-    const double tol = (WENO_FLAT * M) * (WENO_FLAT * M);
-    w.flat = b[0] <= tol && b[1] <= tol && b[2] <= tol;
-  }
-  w.sg = (b[0] - b[2]) >= 0.0 ? 1 : -1;
-  w.tau = fabs(b[0] - b[2]);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) w.c[k] = b[k] + eps;
-  w.A[0] = 0.1 * (w.c[0] + w.tau) * w.c[1] * w.c[2];
-  w.A[1] = 0.6 * (w.c[1] + w.tau) * w.c[0] * w.c[2];
-  w.A[2] = 0.3 * (w.c[2] + w.tau) * w.c[0] * w.c[1];
-  w.S = w.A[0] + w.A[1] + w.A[2];
-  w.out = (w.A[0] * w.q[0] + w.A[1] * w.q[1] + w.A[2] * w.q[2]) / w.S;
-  return w.out;
-}
-
-// WENO5-Z value and its gradient g[j] = d(out)/d(v_j) in one pass (the
-// same arithmetic as weno_fwd followed by weno_rev with a unit seed)
+// WENO5-Z (the kernel's form with one common denominator): its value and
+// gradient g[j] = d(out)/d(v_j) in one pass
 __device__ __forceinline__ double weno_val_grad(double v0, double v1, double v2, double v3, double v4, double eps,
                                                 double* g) {
   const double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
@@ -227,49 +186,6 @@ __device__ __forceinline__ double recon_val_grad(double v0, double v1, double v2
     g[5] = 0.0;
     return out;
   }
-}
-
-// adds d(out)/d(v) * lam to gv[0..4]
-__device__ __forceinline__ void weno_rev(const Weno& w, double lam, double* gv) {
-  if (w.flat) {
-    // ideal weights 1/10, 6/10, 3/10 on the three candidates
-    gv[0] += lam * (1.0 / 30.0);
-    gv[1] += lam * (-13.0 / 60.0);
-    gv[2] += lam * (47.0 / 60.0);
-    gv[3] += lam * (9.0 / 20.0);
-    gv[4] += lam * (-1.0 / 20.0);
-    return;
-  }
-  const double lN = lam / w.S, lS = -lam * w.out / w.S;
-  double lA[3], lc[3] = {0.0, 0.0, 0.0}, ltau = 0.0, lq[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    lA[k] = lN * w.q[k] + lS;
-    lq[k] = lN * w.A[k];
-  }
-  const double* c = w.c;
-  const double tau = w.tau;
-  double a = lA[0] * 0.1;
-  lc[0] += a * c[1] * c[2]; ltau += a * c[1] * c[2]; lc[1] += a * (c[0] + tau) * c[2]; lc[2] += a * (c[0] + tau) * c[1];
-  a = lA[1] * 0.6;
-  lc[1] += a * c[0] * c[2]; ltau += a * c[0] * c[2]; lc[0] += a * (c[1] + tau) * c[2]; lc[2] += a * (c[1] + tau) * c[0];
-  a = lA[2] * 0.3;
-  lc[2] += a * c[0] * c[1]; ltau += a * c[0] * c[1]; lc[0] += a * (c[2] + tau) * c[1]; lc[1] += a * (c[2] + tau) * c[0];
-  double lb[3] = {lc[0], lc[1], lc[2]};
-  lb[0] += w.sg * ltau;
-  lb[2] -= w.sg * ltau;
-  double lt[3], ls[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    lt[k] = lb[k] * (13.0 / 6.0) * w.t[k];
-    ls[k] = lb[k] * 0.5 * w.s[k];
-  }
-  gv[0] += lt[0] + ls[0] + lq[0] * (2.0 / 6.0);
-  gv[1] += -2.0 * lt[0] - 4.0 * ls[0] + lt[1] + ls[1] - lq[0] * (7.0 / 6.0) - lq[1] * (1.0 / 6.0);
-  gv[2] += lt[0] + 3.0 * ls[0] - 2.0 * lt[1] + lt[2] + 3.0 * ls[2] + lq[0] * (11.0 / 6.0) + lq[1] * (5.0 / 6.0) +
-           lq[2] * (2.0 / 6.0);
-  gv[3] += lt[1] - ls[1] - 2.0 * lt[2] - 4.0 * ls[2] + lq[1] * (2.0 / 6.0) + lq[2] * (5.0 / 6.0);
-  gv[4] += lt[2] + ls[2] - lq[2] * (1.0 / 6.0);
 }
 
 // ---------------------------------------------------------------------------
