@@ -124,7 +124,8 @@ typedef struct {
   int viscous;      /* viscous stress and heat conduction (Eq. DiffusionTerms:
                        tau = mu (grad u + grad u^T - 2/3 div u I),
                        q = -lambda grad T + sum J h), second-order central on
-                       the faces (FP32 on mixed contexts); not in the adjoint */
+                       the faces (FP32 on mixed contexts); reversed by the
+                       adjoint entries too */
   double prandtl;   /* gas-phase Prandtl number: lambda_g = mu_g cp_g / Pr
                        (> 0 when viscous) */
   double lambda_liquid; /* liquid-phase heat conductivity [W/(m K)] (>= 0) */

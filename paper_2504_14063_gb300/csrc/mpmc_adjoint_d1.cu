@@ -9,7 +9,7 @@ AdjOps adj_ops_d1(int ns) {
     case 2: return adj::AdjImpl<2, 1>::ops();
     case 3: return adj::AdjImpl<3, 1>::ops();
     case 4: return adj::AdjImpl<4, 1>::ops();
-    default: return AdjOps{nullptr, nullptr, nullptr, nullptr, nullptr};
+    default: return AdjOps{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   }
 }
 

@@ -9,7 +9,7 @@ AdjOps adj_ops_d2(int ns) {
     case 2: return adj::AdjImpl<2, 2>::ops();
     case 3: return adj::AdjImpl<3, 2>::ops();
     case 4: return adj::AdjImpl<4, 2>::ops();
-    default: return AdjOps{nullptr, nullptr, nullptr, nullptr, nullptr};
+    default: return AdjOps{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   }
 }
 

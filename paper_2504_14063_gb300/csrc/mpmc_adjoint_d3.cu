@@ -9,7 +9,7 @@ AdjOps adj_ops_d3(int ns) {
     case 2: return adj::AdjImpl<2, 3>::ops();
     case 3: return adj::AdjImpl<3, 3>::ops();
     case 4: return adj::AdjImpl<4, 3>::ops();
-    default: return AdjOps{nullptr, nullptr, nullptr, nullptr, nullptr};
+    default: return AdjOps{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   }
 }
 

@@ -28,16 +28,19 @@ constexpr int VJP_THREADS = 128;
 //     [diffusion: X^c/X_p x NS, W^c D^c_p/W_p x NS], U x NV
 //   CDI: psi of the four tangential neighbours per tangential direction
 //     (i + e_t, i - e_t, i + e_d + e_t, i + e_d - e_t)
+//   viscous: mu, lambda in the neighbour slots, and the D velocity
+//     components of the same four tangential neighbours per tangential
+//     direction
 // Values are adjoints of the quantities as the face sees them (wall-mirrored
 // velocity components with their sign); the gather applies the mirror sign.
 template <int NS, int D>
 struct Lay {
   static constexpr int NV = NS + D + 1;
   static constexpr int NL = 2 + NS + D;
-  int nb, qYr, qHr, qPhi, qPsi, qXr, qB, qU, psi0, total;
-  __host__ __device__ Lay(int cdi, int diff) {
+  int nb, qYr, qHr, qPhi, qPsi, qXr, qB, qMu, qLam, qU, psi0, vel0, total;
+  __host__ __device__ Lay(int cdi, int diff, int visc = 0) {
     int q = 2;
-    qYr = qHr = qPhi = qPsi = qXr = qB = -1;
+    qYr = qHr = qPhi = qPsi = qXr = qB = qMu = qLam = -1;
     if (cdi) {
       qYr = q; q += NS;
       qHr = q; q += 2;
@@ -48,12 +51,20 @@ struct Lay {
       qXr = q; q += NS;
       qB = q; q += NS;
     }
+    if (visc) {
+      qMu = q++;
+      qLam = q++;
+    }
     qU = q;
     q += NV;
     nb = q;
     psi0 = 6 * NL + 2 * nb;
-    total = psi0 + (cdi ? 4 * (D - 1) : 0);
+    vel0 = psi0 + (cdi ? 4 * (D - 1) : 0);
+    total = vel0 + (visc ? 4 * (D - 1) * D : 0);
   }
+  // velocity component i of tangential neighbour q (0..3) of tangential
+  // direction number tt
+  __host__ __device__ int vel(int tt, int q, int i) const { return vel0 + (tt * 4 + q) * D + i; }
   __host__ __device__ int line(int j, int q) const { return j * NL + q; }
   __host__ __device__ int nbq(int s, int q) const { return 6 * NL + s * nb + q; }
 };
@@ -178,7 +189,7 @@ __global__ void __launch_bounds__(VJP_THREADS)
   const long long nf = (long long)f0 * f1 * f2;
   const long long fid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (fid >= nf) return;
-  const Lay<NS, D> L(P.cdi, P.diffusion);
+  const Lay<NS, D> L(P.cdi, P.diffusion, P.viscous);
   auto put = [&](int q, double v) { C[(long long)q * nf + fid] = v; };
   int fc[3];
   unflatten(fid, f0, f1, fc);
@@ -764,6 +775,159 @@ __device__ __forceinline__ Pre preimages(int c, int n, int lo, int hi) {
   return p;
 }
 
+// Per face of direction DIR, after k_face_adj: the reverse of the viscous
+// stress and heat-conduction flux (Eq. DiffusionTerms, second-order central,
+// as k_face): adds to the T and velocity line slots of the two face cells and
+// writes the mu, lambda slots and the tangential neighbours' velocity slots.
+template <int NS, int D, int DIR>
+__global__ void __launch_bounds__(VJP_THREADS)
+    k_face_visc_adj(const KParams P, const double* __restrict__ Wc, const double* __restrict__ scal,
+                    const double* __restrict__ lamL, const double coef, const int mul_dt, double* __restrict__ C) {
+  constexpr int NV = NS + D + 1;
+  constexpr int d = DIR;
+  const int f0 = P.n[0] + (d == 0), f1 = P.n[1] + (d == 1), f2 = P.n[2] + (d == 2);
+  const long long nf = (long long)f0 * f1 * f2;
+  const long long fid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (fid >= nf) return;
+  const Lay<NS, D> L(P.cdi, P.diffusion, P.viscous);
+  int fc[3];
+  unflatten(fid, f0, f1, fc);
+  int ci[3] = {fc[0], fc[1], fc[2]};
+  ci[d] -= 1;
+  const CRef ri = map_cell(P, ci[0], ci[1], ci[2]);
+  int cj3[3] = {ci[0], ci[1], ci[2]};
+  cj3[d] += 1;
+  const CRef rj = map_cell(P, cj3[0], cj3[1], cj3[2]);
+  const double sc = (mul_dt ? coef * scal[0] : coef) * P.inv_dx;
+  const bool real_i = ci[d] >= 0, real_j = ci[d] + 1 <= P.n[d] - 1;
+  double nu[NV];
+  bool any = false;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double a = real_j ? lamL[(long long)v * P.ncell + rj.idx] : 0.0;
+    const double b = real_i ? lamL[(long long)v * P.ncell + ri.idx] : 0.0;
+    nu[v] = (a - b) * sc;
+    any = any || nu[v] != 0.0;
+  }
+  // (k_face_adj has zeroed every slot of a face whose flux adjoint is zero)
+  if (!any) return;
+  auto put = [&](int q, double v) { C[(long long)q * nf + fid] = v; };
+  auto add = [&](int q, double v) { C[(long long)q * nf + fid] += v; };
+
+  // forward values
+  double gu[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gu[i][j] = 0.0;
+  double ui[3] = {0.0, 0.0, 0.0}, uj[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    ui[i] = wget(P, Wc, P.wU + i, ri) * sgn_flip(ri.flip, i);
+    uj[i] = wget(P, Wc, P.wU + i, rj) * sgn_flip(rj.flip, i);
+    gu[i][d] = (uj[i] - ui[i]) * P.inv_dx;
+  }
+  CRef tn[3][4];  // tangential neighbours: i + e_t, i - e_t, j + e_t, j - e_t
+#pragma unroll
+  for (int t = 0; t < D; ++t) {
+    if (t == d) continue;
+    int a0[3] = {ci[0], ci[1], ci[2]}, a1[3] = {ci[0], ci[1], ci[2]};
+    a0[t] += 1;
+    a1[t] -= 1;
+    int b0[3] = {a0[0], a0[1], a0[2]}, b1[3] = {a1[0], a1[1], a1[2]};
+    b0[d] += 1;
+    b1[d] += 1;
+    tn[t][0] = map_cell(P, a0[0], a0[1], a0[2]);
+    tn[t][1] = map_cell(P, a1[0], a1[1], a1[2]);
+    tn[t][2] = map_cell(P, b0[0], b0[1], b0[2]);
+    tn[t][3] = map_cell(P, b1[0], b1[1], b1[2]);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const double dip = wget(P, Wc, P.wU + i, tn[t][0]) * sgn_flip(tn[t][0].flip, i) -
+                         wget(P, Wc, P.wU + i, tn[t][1]) * sgn_flip(tn[t][1].flip, i);
+      const double djp = wget(P, Wc, P.wU + i, tn[t][2]) * sgn_flip(tn[t][2].flip, i) -
+                         wget(P, Wc, P.wU + i, tn[t][3]) * sgn_flip(tn[t][3].flip, i);
+      gu[i][t] = 0.25 * P.inv_dx * (dip + djp);
+    }
+  }
+  double div = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) div += gu[k][k];
+  const double mub = 0.5 * (wget(P, Wc, P.wMu, ri) + wget(P, Wc, P.wMu, rj));
+  const double lamb = 0.5 * (wget(P, Wc, P.wLam, ri) + wget(P, Wc, P.wLam, rj));
+  const double Ti = wget(P, Wc, P.wT, ri), Tj = wget(P, Wc, P.wT, rj);
+  double tau[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < D; ++i) tau[i] = mub * (gu[i][d] + gu[d][i] - (i == d ? (2.0 / 3.0) * div : 0.0));
+
+  // reverse: F_{NS+i} -= tau_i; F_E -= sum ub_i tau_i + lamb (Tj - Ti) / dx
+  const double lE = nu[NS + D];
+  double lgu[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) lgu[i][j] = 0.0;
+  double lmub = 0.0, lui[3] = {0.0, 0.0, 0.0}, luj[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const double ub = 0.5 * (ui[i] + uj[i]);
+    const double ltau = -nu[NS + i] - lE * ub;
+    const double lub = -lE * tau[i];
+    lui[i] += 0.5 * lub;
+    luj[i] += 0.5 * lub;
+    lmub += ltau * (gu[i][d] + gu[d][i] - (i == d ? (2.0 / 3.0) * div : 0.0));
+    lgu[i][d] += ltau * mub;
+    lgu[d][i] += ltau * mub;
+    if (i == d) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) lgu[k][k] -= (2.0 / 3.0) * ltau * mub;
+    }
+  }
+  const double llamb = -lE * (Tj - Ti) * P.inv_dx;
+  const double lTj = -lE * lamb * P.inv_dx, lTi = lE * lamb * P.inv_dx;
+  // normal derivatives
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    lui[i] -= lgu[i][d] * P.inv_dx;
+    luj[i] += lgu[i][d] * P.inv_dx;
+  }
+  // line slots of the two face cells (j = 2: cell i, 3: cell i+1)
+  add(L.line(2, 0), lTi);
+  add(L.line(3, 0), lTj);
+  {
+    int tt = 0;
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      const int q = t == d ? 2 : 3 + NS + tt;
+      if (t != d) ++tt;
+      add(L.line(2, q), lui[t]);
+      add(L.line(3, q), luj[t]);
+    }
+  }
+  // mu, lambda of the two cells
+  put(L.nbq(0, L.qMu), 0.5 * lmub);
+  put(L.nbq(1, L.qMu), 0.5 * lmub);
+  put(L.nbq(0, L.qLam), 0.5 * llamb);
+  put(L.nbq(1, L.qLam), 0.5 * llamb);
+  // tangential derivatives: gu[i][t] = (u_{i+t} - u_{i-t} + u_{j+t} - u_{j-t}) / (4 dx)
+  {
+    int tt = 0;
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      if (t == d) continue;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const double g = 0.25 * P.inv_dx * lgu[i][t];
+        put(L.vel(tt, 0, i), g);
+        put(L.vel(tt, 1, i), -g);
+        put(L.vel(tt, 2, i), g);
+        put(L.vel(tt, 3, i), -g);
+      }
+      ++tt;
+    }
+  }
+}
+
 // Per cell: sums, in a fixed order, the contributions of the faces of
 // direction d whose stencils reach the cell; first != 0 writes, otherwise
 // adds.  gW: cache adjoint [nW][wstride]; gU: U adjoint [NV][ncell].
@@ -775,7 +939,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
   constexpr int d = DIR;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= P.ncell) return;
-  const Lay<NS, D> L(P.cdi, P.diffusion);
+  const Lay<NS, D> L(P.cdi, P.diffusion, P.viscous);
   int cc[3];
   unflatten(c, P.n[0], P.n[1], cc);
   const int f0 = P.n[0] + (d == 0), f1 = P.n[1] + (d == 1), f2 = P.n[2] + (d == 2);
@@ -787,6 +951,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
 
   double aT = 0.0, aP = 0.0, aUn = 0.0, aY[NS], aUt[3] = {0.0, 0.0, 0.0}, aRho = 0.0, aA = 0.0;
   double aYr[NS], aHr[2] = {0.0, 0.0}, aPhi = 0.0, aPsi = 0.0, aXr[NS], aB[NS], aU[NV];
+  double aMu = 0.0, aLam = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) { aY[k] = 0.0; aYr[k] = 0.0; aXr[k] = 0.0; aB[k] = 0.0; }
 #pragma unroll
@@ -837,6 +1002,10 @@ __global__ void __launch_bounds__(CELL_THREADS)
           aB[k] += get(L.nbq(s2, L.qB + k), f);
         }
       }
+      if (P.viscous) {
+        aMu += get(L.nbq(s2, L.qMu), f);
+        aLam += get(L.nbq(s2, L.qLam), f);
+      }
 #pragma unroll
       for (int v = 0; v < NV; ++v) aU[v] += (v == NS + d ? sg : 1.0) * get(L.nbq(s2, L.qU + v), f);
     }
@@ -864,6 +1033,42 @@ __global__ void __launch_bounds__(CELL_THREADS)
             fc[d] = fi;
             fc[t] = cit;
             aPsi += get(L.psi0 + 4 * tt + q, face(fc));
+          }
+        }
+      }
+      ++tt;
+    }
+  }
+
+  // velocity components of the tangential neighbours of a face (viscous
+  // stress), with the wall-mirror sign of the mapping that reached the cell
+  if (P.viscous && D > 1) {
+    int tt = 0;
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      if (t == d) continue;
+      const Pre pt = preimages(cc[t], P.n[t], P.bc_lo[t], P.bc_hi[t]);
+      for (int e = 0; e < pd.n; ++e) {
+        const int gd = pd.g[e];
+        for (int h = 0; h < pt.n; ++h) {
+          const int gt = pt.g[h];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int cid = q < 2 ? gd : gd - 1;
+            const int cit = (q & 1) ? gt + 1 : gt - 1;
+            const int fi = cid + 1;
+            if (fi < 0 || fi > n || cit < 0 || cit >= P.n[t]) continue;
+            int fc[3] = {cc[0], cc[1], cc[2]};
+            fc[d] = fi;
+            fc[t] = cit;
+            const long long f = face(fc);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+              const double sgn = i == d ? pd.s[e] : (i == t ? pt.s[h] : 1.0);
+              const double v = sgn * get(L.vel(tt, q, i), f);
+              if (i == d) aUn += v;
+              else aUt[i < d ? i : i - 1] += v;
+            }
           }
         }
       }
@@ -901,6 +1106,10 @@ __global__ void __launch_bounds__(CELL_THREADS)
       out(P.wXr + k, aXr[k]);
       out(P.wB + k, aB[k]);
     }
+  }
+  if (P.viscous) {
+    out(P.wMu, aMu);
+    out(P.wLam, aLam);
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -958,7 +1167,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
 #pragma unroll
   for (int v = 0; v < NV; ++v) lU[v] = 0.0;
 
-  if (P.cdi || P.diffusion) {
+  if (P.cdi || P.diffusion || P.viscous) {
     double phi[2] = {0.0, 0.0}, hr[2] = {0.0, 0.0}, Yp[2] = {0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
@@ -992,7 +1201,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
         lphi[ph] -= lq * iphi * iphi;
       }
     }
-    if (P.diffusion) {
+    if (P.diffusion || P.viscous) {
       // gas viscosity (Wilke) and its dependence on the gas mass fractions
       double mup[2], den[NS], lmu[2] = {0.0, 0.0};
       mup[0] = P.mu_liquid;
@@ -1007,8 +1216,31 @@ __global__ void __launch_bounds__(CELL_THREADS)
         if (den[i] > 0.0) num += Y[i] * P.mu[i] / den[i];
       }
       mup[1] = Yp[1] >= ABSENT ? num : 0.0;
+      if (P.viscous) {
+        // mu = phi_0 mu_l + phi_1 mu_g; lambda = phi_0 lambda_l + phi_1 lambda_g,
+        // lambda_g = (mu_g / Pr) cpY / Y_g, cpY = sum_{gas} Y_k cp_k
+        const double lMu = gW[P.wMu * ws + c], lLam = gW[P.wLam * ws + c];
+        double cpY = 0.0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+          if (P.phase[k] == 1) cpY += Y[k] * P.cp[k];
+        const double lam_g = Yp[1] >= ABSENT ? mup[1] / P.prandtl * (cpY / Yp[1]) : 0.0;
+        lphi[0] += lMu * mup[0] + lLam * P.lambda_liquid;
+        lphi[1] += lMu * mup[1] + lLam * lam_g;
+        lmu[1] += lMu * phi[1];
+        if (Yp[1] >= ABSENT) {
+          const double llg = lLam * phi[1];
+          lmu[1] += llg * cpY / (P.prandtl * Yp[1]);
+          const double lcpY = llg * mup[1] / (P.prandtl * Yp[1]);
+          const double lYg = -llg * mup[1] * cpY / (P.prandtl * Yp[1] * Yp[1]);
+#pragma unroll
+          for (int k = 0; k < NS; ++k)
+            if (P.phase[k] == 1) lY[k] += lcpY * P.cp[k] + lYg;
+        }
+      }
 #pragma unroll
       for (int ph = 0; ph < 2; ++ph) {
+        if (!P.diffusion) break;
         double sY = 0.0;
 #pragma unroll
         for (int j = 0; j < NS; ++j)
@@ -1184,11 +1416,23 @@ AdjFaceFn adj_face(int dim, int ns) {
 
 template <int NS, int D>
 struct AdjImpl {
-  static int slots(const KParams& P) { return Lay<NS, D>(P.cdi, P.diffusion).total; }
+  static int slots(const KParams& P) { return Lay<NS, D>(P.cdi, P.diffusion, P.viscous).total; }
   static void face(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* Uk, const double* Uin,
                    const double* scal, const uint32_t* tape, const double* lamL, double coef, int mul_dt,
                    double* C) {
     AdjFaceImpl<NS, D, RC_WENO5Z>::face(P, s, d, Wc, Uk, Uin, scal, tape, lamL, coef, mul_dt, C);
+  }
+  static void face_visc(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* scal,
+                        const double* lamL, double coef, int mul_dt, double* C) {
+    long long nf = 1;
+    for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
+    const unsigned nb = nblocks(nf, VJP_THREADS);
+    if (d == 0)
+      k_face_visc_adj<NS, D, 0><<<nb, VJP_THREADS, 0, s>>>(P, Wc, scal, lamL, coef, mul_dt, C);
+    else if (d == 1)
+      k_face_visc_adj<NS, D, (D > 1 ? 1 : 0)><<<nb, VJP_THREADS, 0, s>>>(P, Wc, scal, lamL, coef, mul_dt, C);
+    else
+      k_face_visc_adj<NS, D, (D > 2 ? 2 : 0)><<<nb, VJP_THREADS, 0, s>>>(P, Wc, scal, lamL, coef, mul_dt, C);
   }
   static void gather(const KParams& P, cudaStream_t s, int d, const double* C, int first, double* gW, double* gU) {
     const unsigned nb = nblocks(P.ncell, CELL_THREADS);
@@ -1211,6 +1455,7 @@ struct AdjImpl {
     AdjOps o;
     o.slots = &slots;
     o.face = &face;
+    o.face_visc = &face_visc;
     o.gather = &gather;
     o.cell = &cell;
     o.init = &init;

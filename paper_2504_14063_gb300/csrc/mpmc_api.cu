@@ -431,7 +431,6 @@ extern "C" int mpmc_dt_gamma(mpmc_ctx* c, const double* U, double* out_dev) {
 // discrete adjoint (FP64 contexts)
 static int ensure_adjoint(mpmc_ctx* c) {
   if (c->precision != MPMC_FP64) return fail(c, MPMC_INVALID_ARG, "adjoint: needs an FP64 context");
-  if (c->P.viscous) return fail(c, MPMC_INVALID_ARG, "adjoint: viscous stress and conduction are not reversed");
   const KParams& P = c->P;
   int rc = MPMC_OK;
   const size_t st_bytes = (size_t)P.nv * P.ncell * sizeof(double);
@@ -469,6 +468,7 @@ static void stage_vjp(mpmc_ctx* c, cudaStream_t s, const double* U, const uint32
     {
       ProfScope ps(c, FAM_ADJ_FACE, s);
       c->aops.face(P, s, d, c->Wc, U, c->Uin, c->scal, tape + off, lamL, coef, mul_dt, c->Cslots);
+      if (P.viscous) c->aops.face_visc(P, s, d, c->Wc, c->scal, lamL, coef, mul_dt, c->Cslots);
     }
     ProfScope ps(c, FAM_ADJ_PRIM, s);
     c->aops.gather(P, s, d, c->Cslots, d == 0, c->gW, c->gU);

@@ -4,14 +4,17 @@ oracle with walls (mirrored tangential gradients), periodic and 3D
 boundaries (same bound as the inviscid parity tests), 100 steps, and the
 shear wave's decay against the exact SSP-RK3 factor of the discrete
 Laplacian; the mixed path's FP32 viscous fluxes within the mixed-precision
-bound; the adjoint refuses it."""
+bound; the discrete adjoint with its viscous reverse (dot products against
+the oracle's forward-mode tangent)."""
 import numpy as np
 import pytest
 import torch
 
 from oracle import Oracle
 from paper_2504_14063_gb300 import workloads as W
+from tests.test_gpu_adjoint import _dot_check
 from tests.test_gpu_parity import NTH, _cuda, _gross, _steps_parity, rhs_parity
+from tests.test_oracle_jvp import _modulated, _state_and_dir
 
 pytestmark = pytest.mark.gpu
 
@@ -118,9 +121,43 @@ def test_mixed_rhs_viscous_close_to_oracle(mp, case):
     assert np.all(num <= bound)
 
 
-def test_viscous_adjoint_is_refused(mp):
-    p = _viscous(W.random_smooth_2d(16, 12, seed=1))
+ADJ_CASES = {
+    "smooth_2d_cdi_diff": lambda: _viscous(W.random_smooth_2d(24, 20, seed=3, cdi=1, diffusion=1), 1e3),
+    "shock_bubble_2d_walls": lambda: _viscous(_modulated(W.shock_bubble_2d(nx=48, ny=28, seed=1)), 1e3),
+    "droplet_3d": lambda: _viscous(_modulated(W.droplet_field_3d(n=14, ndrops=2, seed=2, rmin=2.5, rmax=3.5)),
+                                   1e2),
+}
+
+
+@pytest.mark.parametrize("case", list(ADJ_CASES))
+def test_viscous_rhs_adjoint_dot_product(mp, case):
+    """<lam, J dU> (oracle forward-mode tangent through the viscous terms) =
+    <J^T lam, dU> (GPU adjoint with its viscous reverse kernel), within 1e-9
+    of the gross sum."""
+    p = ADJ_CASES[case]()
+    o = Oracle(p, nthreads=NTH)
+    U, dU = _state_and_dir(o, p, np.random.default_rng(5))
+    dt, G, _ = o.dt_gamma(U)
+    rk = (0.75, 0.25, 0.25)
+    Un = o.rk_step(U, 0.3 * dt)[0]
+    _, dL, st = o.stage_jvp(Un, U, dU, rk, dt, G)
+    assert st == 0
+    lam = np.random.default_rng(9).standard_normal(U.shape)
     ctx = mp.Context(p)
-    U = ctx.init_state(torch.from_numpy(p.prim))
-    with pytest.raises(mp.MpmcError):
-        ctx.rk_step_adjoint(U, torch.zeros_like(U), dt=1e-9)
+    lamU = ctx.rhs_adjoint(_cuda(U), dict(U_n=_cuda(Un), rk=rk, dt=dt, Gamma=G), None, _cuda(lam)).cpu().numpy()
+    assert ctx.status() == 0
+    _dot_check((lam * dL).sum(), (lamU * dU).sum(), np.abs(lam * dL).sum(), f"viscous rhs {case}")
+
+
+def test_viscous_rk_step_adjoint_dot_product(mp):
+    p = ADJ_CASES["shock_bubble_2d_walls"]()
+    o = Oracle(p, nthreads=NTH)
+    U, dU = _state_and_dir(o, p, np.random.default_rng(6))
+    ctx = mp.Context(p)
+    dt, G = (float(x) for x in ctx.dt_gamma(_cuda(U)).cpu())
+    _, dU1, st = o.rk_step_jvp(U, dU, dt, G)
+    assert st == 0
+    lam = np.random.default_rng(10).standard_normal(U.shape)
+    lam_n = ctx.rk_step_adjoint(_cuda(U), _cuda(lam), dt=dt).cpu().numpy()
+    assert ctx.status() == 0
+    _dot_check((lam * dU1).sum(), (lam_n * dU).sum(), np.abs(lam * dU1).sum(), "viscous rk step")

@@ -181,3 +181,29 @@ def test_conservation_with_viscosity_and_conduction():
     for v in range(U.shape[0]):
         scale = np.abs(U0[v]).sum() + 1e-300
         assert abs(U[v].sum() - U0[v].sum()) <= 1e-13 * scale, v
+
+
+def test_viscous_stage_tangent_matches_central_differences():
+    """The oracle's forward-mode tangent through the viscous terms (the
+    reference gradient of the GPU adjoint) against central differences along
+    a smooth primitive-space direction."""
+    from tests.test_oracle_jvp import _state_and_dir
+    p = W.random_smooth_2d(16, 12, seed=3, cdi=1, diffusion=1)
+    p.model.viscous = 1
+    p.model.mu_liquid *= 1e3
+    p.model.lambda_liquid *= 1e3
+    for s in p.species:
+        s.mu *= 1e3
+    o = Oracle(p, nthreads=2)
+    U, dU = _state_and_dir(o, p, np.random.default_rng(5))
+    dt, G, _ = o.dt_gamma(U)
+    rk = (0.75, 0.25, 0.25)
+    Un = o.rk_step(U, 0.3 * dt)[0]
+    _, dL, st = o.stage_jvp(Un, U, dU, rk, dt, G)
+    assert st == 0
+    h = 1e-6
+    Lp = o.stage(Un, U + h * dU, rk, dt, G)[1]
+    Lm = o.stage(Un, U - h * dU, rk, dt, G)[1]
+    err = np.abs((Lp - Lm) / (2 * h) - dL).sum() / np.abs(dL).sum()
+    print(f"viscous stage tangent vs central differences {err:.2e}")
+    assert err < 1e-6
