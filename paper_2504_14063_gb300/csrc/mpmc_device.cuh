@@ -508,17 +508,32 @@ __device__ __forceinline__ double weno5js(double v0, double v1, double v2, doubl
 // with chi_k < CT are cut off (bit k of the result clear)
 template <int K>
 __device__ __forceinline__ unsigned teno_kept(const double* b, double tau, double CT) {
+  // 1 / (beta_k + eps) from one reciprocal of their product (each factor lies
+  // in [1e-40, ~1e20], the product of four within range), then r_k
+  double cfac[K], pre[K], suf[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) cfac[k] = b[k] + 1e-40;
+  pre[0] = 1.0;
+#pragma unroll
+  for (int k = 1; k < K; ++k) pre[k] = pre[k - 1] * cfac[k - 1];
+  suf[K - 1] = 1.0;
+#pragma unroll
+  for (int k = K - 2; k >= 0; --k) suf[k] = suf[k + 1] * cfac[k + 1];
+  const double iprod = 1.0 / (pre[K - 1] * cfac[K - 1]);
   double r[K], rmax = 0.0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    r[k] = 1.0 + tau / (b[k] + 1e-40);
+    r[k] = 1.0 + tau * (iprod * pre[k] * suf[k]);
     rmax = fmax(rmax, r[k]);
   }
-  const double irm = 1.0 / rmax;
+  // scale by the power of two 2^-floor(log2 rmax) (exact; r_k^6 would
+  // overflow beside a large jump): chi_k is unchanged by a common factor
+  const int ex = min((__double2hiint(rmax) >> 20) & 0x7ff, 2045);  // rmax >= 1, finite
+  const double scale = __hiloint2double((2046 - ex) << 20, 0);
   double g[K], gs = 0.0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const double x = r[k] * irm, x2 = x * x;
+    const double x = r[k] * scale, x2 = x * x;
     g[k] = x2 * x2 * x2;
     gs += g[k];
   }
