@@ -10,6 +10,7 @@
 #pragma once
 #include "mpmc_device.cuh"
 #include "mpmc_ops.h"
+#include "mpmc_narrow.h"
 #include "mpmc_update.cuh"
 
 namespace mpmc {
@@ -394,27 +395,28 @@ __global__ void __launch_bounds__(CELL_THREADS)
     load_species<NS>(P, sp);
     float Yf[NS];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) Yf[k] = (float)Y[k];
-    const float p = (float)pd, T = (float)Td;
+    for (int k = 0; k < NS; ++k) Yf[k] = narrow(Y[k]);
+    const float p = narrow(pd), T = narrow(Td);
     float r2, e2, a;
     eos_forward_f<NS>(sp, Yf, p, T, r2, e2, a);
     Wc[P.wT * ws + c] = T;
     Wc[P.wP * ws + c] = p;
-    Wc[P.wRho * ws + c] = (float)rho;
+    Wc[P.wRho * ws + c] = narrow(rho);
     Wc[P.wA * ws + c] = a;
 #pragma unroll
     for (int k = 0; k < NS; ++k) Wc[(P.wY + k) * ws + c] = Yf[k];
 #pragma unroll
-    for (int d = 0; d < D; ++d) Wc[(P.wU + d) * ws + c] = (float)u[d];
+    for (int d = 0; d < D; ++d) Wc[(P.wU + d) * ws + c] = narrow(u[d]);
     // FP32 copies of U for the limiter's first (FP32) admissibility test;
     // the pass that computes dt and Gamma (red != null) runs on U^n
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      Wc[(P.nW + v) * ws + c] = (float)Uc[v];
-      if (red) P.unf[v * ws + c] = (float)Uc[v];
+      const float uf = narrow(Uc[v]);
+      Wc[(P.nW + v) * ws + c] = uf;
+      if (red) P.unf[v * ws + c] = uf;
     }
     float mu = 0.f, lam = 0.f;
-    const float rhof = (float)rho;
+    const float rhof = narrow(rho);
     if (P.cdi || P.diffusion || P.viscous) {
       float phi[2], Yp[2];
 #pragma unroll
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
         for (int k = 0; k < NS; ++k)
           if (P.phase[k] == ph) {
             yp += Yf[k];
-            const float ry = (float)Uc[k];
+            const float ry = narrow(Uc[k]);
             if (ry != 0.f) {
               f += ry * (sp[k].Rk * T / (p + sp[k].pinf) + sp[k].b);
               hr += ry * (sp[k].cp * T + sp[k].b * p + sp[k].q);
@@ -499,7 +501,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
       const float idx = P.f32.inv_dx;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        const float ud = fabsf((float)u[d]);
+        const float ud = fabsf(narrow(u[d]));
         smax = fmaxf(smax, (ud + a) * idx);
         gmax = fmaxf(gmax, ud);
       }
