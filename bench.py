@@ -160,6 +160,24 @@ def cpu_baseline(p, seconds=12.0):
                               "sample": f"1 SSP-RK3 step of the same workload ({el1:.1f} s)"}}
 
 
+def max_over_ranks(x, device):
+    """The largest x over the ranks of the initialised process group (the
+    slowest replica's time); x itself on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, cells, steps, seconds):
+    """cell-updates/s of all ranks together: each rank advances its own replica
+    of `cells` cells by `steps` steps, the job takes the slowest rank's time"""
+    return world * cells * steps / seconds
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -337,13 +355,10 @@ def main():
     status = ctx.status()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(total_s, "cuda")
     prof = ctx.profile(reset=True)
     stats = ctx.stats(reset=True)
-    value = world * p.ncells * args.steps / total_s
+    value = whole_job_value(world, p.ncells, args.steps, total_s)
 
     # roofline of the face-flux kernel (dominant): algorithmic FP64 flops
     face_ms, face_n = prof["face"]
@@ -373,11 +388,7 @@ def main():
         ctxm.set_profiling(False)
         mstat = ctxm.status()
         mprof = ctxm.profile(reset=True)
-        tm = sum(a.elapsed_time(b) for a, b in evm) / 1e3
-        if world > 1:
-            t = torch.tensor([tm], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tm = float(t.item())
+        tm = max_over_ranks(sum(a.elapsed_time(b) for a, b in evm) / 1e3, "cuda")
         # accuracy: 100 steps from the initial state, FP64 path vs mixed path
         A = ctx.init_state(torch.from_numpy(p.prim))
         B = ctxm.init_state(torch.from_numpy(p.prim))
@@ -393,8 +404,9 @@ def main():
             si = rhoi if v < ns else (rhoi * 1000.0 if v < ns + D else np.abs(Ah[v]).max())
             l1[names[v]] = float(np.abs(Bh[v] - Ah[v]).sum() / s1)
             li[names[v]] = float(np.abs(Bh[v] - Ah[v]).max() / si)
-        mixed = {"value": world * p.ncells * args.steps / tm, "unit": UNIT, "ms_per_step": 1e3 * tm / args.steps,
-                 "speedup_vs_fp64": (world * p.ncells * args.steps / tm) / value,
+        vm = whole_job_value(world, p.ncells, args.steps, tm)
+        mixed = {"value": vm, "unit": UNIT, "ms_per_step": 1e3 * tm / args.steps,
+                 "speedup_vs_fp64": vm / value,
                  "kernel_ms_per_step": {k: v[0] / args.steps for k, v in mprof.items()},
                  "error_vs_fp64": {"steps": args.compare_steps,
                                    "norm": "state-scaled (partial densities by rho, momenta by rho*1000 m/s, "
@@ -431,12 +443,8 @@ def main():
             torch.cuda.synchronize()
             ctxr.set_profiling(False)
             rprof = ctxr.profile(reset=True)
-            tr = sum(a.elapsed_time(b) for a, b in evr) / 1e3
-            if world > 1:
-                t = torch.tensor([tr], device="cuda", dtype=torch.float64)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                tr = float(t.item())
-            vr = world * pr_.ncells * args.recon_steps / tr
+            tr = max_over_ranks(sum(a.elapsed_time(b) for a, b in evr) / 1e3, "cuda")
+            vr = whole_job_value(world, pr_.ncells, args.recon_steps, tr)
             recon[rname] = {"value": vr, "unit": UNIT, "ms_per_step": 1e3 * tr / args.recon_steps,
                             "vs_base_step": vr / value, "steps": args.recon_steps,
                             "face_ms_per_step": rprof["face"][0] / args.recon_steps, "status": ctxr.status()}
@@ -449,10 +457,12 @@ def main():
     # ---- end to end through the host-buffer entry --------------------------
     H = U.cpu().pin_memory()
     ctx.step_n_host(H, 1)
+    if world > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ctx.step_n_host(H, 1)
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
     nbytes = ctx.nv * ctx.ncells * 8
 
     if rank == 0:
@@ -462,7 +472,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(p, {"parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"}),
             "clocks": clk,
-            "e2e": {"value": world * p.ncells * args.steps / e2e_s, "unit": UNIT,
+            "e2e": {"value": whole_job_value(world, p.ncells, args.steps, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "rhs_cell_evaluations_per_s": 3 * value,
             "gpu_launches": launches,
