@@ -37,10 +37,10 @@ L2_BYTES = 129 * 2 ** 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_face launch of this
 # workload from an ncu capture (profiles/k_face_shock_bubble_2d_1024x512_fp64.md),
 # reported while the kernel's sources hash to the captured version
-K_FACE_TRAFFIC_BYTES = 121.61e6
+K_FACE_TRAFFIC_BYTES = 119.46e6
 K_FACE_SOURCES = ("paper_2504_14063_gb300/csrc/mpmc_kernels.cuh", "paper_2504_14063_gb300/csrc/mpmc_device.cuh",
                   "paper_2504_14063_gb300/csrc/mpmc_kernels_d2.cu")
-K_FACE_SOURCES_SHA256 = "842a46a706083e3b7fc5dd80a1a5189951c226a64698d1605b076eba01772287"
+K_FACE_SOURCES_SHA256 = "1e91393309a8601ad1dae8f24100432c1d4f26ff278bea829086fdb04579777e"
 
 
 def k_face_traffic():
@@ -158,6 +158,95 @@ def cpu_baseline(p, seconds=12.0):
                       f"({el:.1f} s, OpenMP threads = {cores})",
             "single_thread": {"value": p.ncells / el1, "unit": UNIT, "cores": 1,
                               "sample": f"1 SSP-RK3 step of the same workload ({el1:.1f} s)"}}
+
+
+def field_errors(A, B, p):
+    """Per-field L1 and Linf of B - A (device states), scaled by the state:
+    partial densities by |rho|, momenta by |rho| x 1000 m/s, energy by |E|
+    (sums for L1, maxima for Linf)."""
+    ns, D = p.ns, p.dim
+    rho = A[:ns].sum(0).abs()
+    rho1, rhoi = float(rho.sum()), float(rho.max())
+    names = [f"rhoY_{s.name}" for s in p.species] + [f"m_{'xyz'[d]}" for d in range(D)] + ["E"]
+    l1, li = {}, {}
+    for v in range(A.shape[0]):
+        s1 = rho1 if v < ns else (rho1 * 1000.0 if v < ns + D else float(A[v].abs().sum()))
+        si = rhoi if v < ns else (rhoi * 1000.0 if v < ns + D else float(A[v].abs().max()))
+        d = (B[v] - A[v]).abs()
+        l1[names[v]] = float(d.sum()) / s1
+        li[names[v]] = float(d.max()) / si
+    return l1, li
+
+
+STUDIES = {
+    # name: (workload, the configuration's step count)
+    "droplet_field_3d": (lambda W: W.droplet_field_3d(n=256), 500),
+    "shock_droplet_3d": (lambda W: W.shock_droplet_3d(n=512), 200),
+}
+
+
+def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=None):
+    """The mixed path against the FP64 path on a 3D workload at full size:
+    both advanced in lockstep from the same initial state with a common
+    step size (the FP64 path's CFL step, so that both reach the same
+    physical times), per-field L1/Linf of the difference every `every`
+    steps; throughput of each path timed separately with CUDA events over
+    `timed_steps` steps (CFL step on the device, after 3 warm-up steps).
+    The states exceed L2 many times over, so no flush is needed."""
+    steps = max(int(steps), 1)
+    prim = torch.from_numpy(p.prim)
+    out = {"study": name, "metric": "mixed vs FP64: per-field L1/Linf of the state difference; cell-updates/s",
+           "unit": UNIT, "grid": list(p.n[:p.dim]), "cells": p.ncells, "species": p.ns,
+           "cdi": bool(p.model.cdi), "diffusion": bool(p.model.diffusion), "steps": steps,
+           "workload_build_s": t_build}
+    perf = {}
+    for label, prec in (("fp64", mp.FP64), ("mixed", mp.MIXED)):
+        ctx = mp.Context(p, precision=prec)
+        U = ctx.init_state(prim)
+        for _ in range(3):
+            ctx.rk_step(U)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(timed_steps)]
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        ctx.set_profiling(True)
+        for k in range(timed_steps):
+            ev[k][0].record()
+            ctx.rk_step(U)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        ctx.set_profiling(False)
+        clk = clocks.stop()
+        ts = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        prof = ctx.profile(reset=True)
+        perf[label] = {"value": p.ncells * timed_steps / ts, "ms_per_step": 1e3 * ts / timed_steps,
+                       "kernel_ms_per_step": {k: v[0] / timed_steps for k, v in prof.items()},
+                       "timed_steps": timed_steps, "clocks": clk, "status": ctx.status()}
+        del ctx, U
+        torch.cuda.empty_cache()
+    perf["mixed"]["speedup_vs_fp64"] = perf["mixed"]["value"] / perf["fp64"]["value"]
+    out.update(perf)
+
+    c64, cmx = mp.Context(p), mp.Context(p, precision=mp.MIXED)
+    A, B = c64.init_state(prim), cmx.init_state(prim)
+    hist, t_phys = [], 0.0
+    t0 = time.perf_counter()
+    for n in range(1, steps + 1):
+        dt = float(c64.dt_gamma(A)[0])
+        c64.rk_step(A, dt)
+        cmx.rk_step(B, dt)
+        t_phys += dt
+        if n % every == 0 or n == steps:
+            l1, li = field_errors(A, B, p)
+            hist.append({"step": n, "t": t_phys, "l1_max": max(l1.values()), "linf_max": max(li.values())})
+    torch.cuda.synchronize()
+    out["lockstep_s"] = time.perf_counter() - t0
+    out["error_vs_fp64"] = {"steps": steps, "t_end": t_phys, "dt": "common: the FP64 path's CFL step each step",
+                            "norm": "state-scaled (partial densities by rho, momenta by rho*1000 m/s, energy by E)",
+                            "l1": l1, "linf": li, "history": hist}
+    out["status"] = {"fp64": c64.status(), "mixed": cmx.status()}
+    return out
 
 
 def max_over_ranks(x, device):
@@ -308,6 +397,10 @@ def main():
     ap.add_argument("--no-recon", action="store_true")
     ap.add_argument("--recon-steps", type=int, default=5)
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--study", choices=sorted(STUDIES), action="append",
+                    help="instead of the benchmark line: the mixed-vs-FP64 precision study of a 3D workload "
+                         "(one JSON line each)")
+    ap.add_argument("--study-steps", type=int, default=None)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -320,6 +413,20 @@ def main():
     import torch
     import torch.distributed as dist
     torch.cuda.set_device(local)
+    if args.study:
+        if rank != 0:
+            return 0
+        from paper_2504_14063_gb300 import binding as mp
+        from paper_2504_14063_gb300 import workloads as W
+        for name in args.study:
+            make, nsteps = STUDIES[name]
+            t0 = time.perf_counter()
+            p = make(W)
+            t_build = time.perf_counter() - t0
+            line = precision_study(mp, torch, name, p, args.study_steps or nsteps, t_build=t_build)
+            print(json.dumps(line), flush=True)
+            del p
+        return 0
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
@@ -394,16 +501,7 @@ def main():
         B = ctxm.init_state(torch.from_numpy(p.prim))
         ctx.step_n(A, args.compare_steps)
         ctxm.step_n(B, args.compare_steps)
-        Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
-        ns, D = p.ns, p.dim
-        rho1, rhoi = np.abs(Ah[:ns].sum(0)).sum(), np.abs(Ah[:ns].sum(0)).max()
-        names = [f"rhoY_{s.name}" for s in p.species] + [f"m_{'xyz'[d]}" for d in range(D)] + ["E"]
-        l1, li = {}, {}
-        for v in range(Ah.shape[0]):
-            s1 = rho1 if v < ns else (rho1 * 1000.0 if v < ns + D else np.abs(Ah[v]).sum())
-            si = rhoi if v < ns else (rhoi * 1000.0 if v < ns + D else np.abs(Ah[v]).max())
-            l1[names[v]] = float(np.abs(Bh[v] - Ah[v]).sum() / s1)
-            li[names[v]] = float(np.abs(Bh[v] - Ah[v]).max() / si)
+        l1, li = field_errors(A, B, p)
         vm = whole_job_value(world, p.ncells, args.steps, tm)
         mixed = {"value": vm, "unit": UNIT, "ms_per_step": 1e3 * tm / args.steps,
                  "speedup_vs_fp64": vm / value,

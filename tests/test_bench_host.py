@@ -1,0 +1,43 @@
+"""Host-side helpers of bench.py on the CPU: the state-scaled per-field
+error norms that the mixed-vs-FP64 comparisons report."""
+import os
+import sys
+
+import pytest
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+from paper_2504_14063_gb300 import workloads as W  # noqa: E402
+
+
+def test_field_errors_scaling():
+    p = W.random_smooth_2d(8, 6, seed=0)
+    ns, D = p.ns, p.dim
+    g = torch.Generator().manual_seed(0)
+    A = torch.rand((ns + D + 1,) + tuple(p.n[::-1]), generator=g, dtype=torch.float64) + 0.5
+    rho = A[:ns].sum(0)
+    B = A.clone()
+    # one perturbation per kind of field, each at its own cell
+    B[1, 0, 2, 3] += 1e-3
+    B[ns + 1, 0, 4, 1] -= 2e-2
+    B[ns + D, 0, 0, 0] += 5e-4
+    B[ns + D, 0, 1, 0] -= 1e-4
+    l1, li = bench.field_errors(A, B, p)
+    names = [f"rhoY_{s.name}" for s in p.species] + ["m_x", "m_y", "E"]
+    assert list(l1) == names and list(li) == names
+    sp = names[1]
+    assert l1[sp] == pytest.approx(1e-3 / float(rho.sum()), rel=1e-9)
+    assert li[sp] == pytest.approx(1e-3 / float(rho.max()), rel=1e-9)
+    assert l1["m_y"] == pytest.approx(2e-2 / (1000.0 * float(rho.sum())), rel=1e-9)
+    assert li["m_y"] == pytest.approx(2e-2 / (1000.0 * float(rho.max())), rel=1e-9)
+    assert l1["E"] == pytest.approx(6e-4 / float(A[ns + D].sum()), rel=1e-9)
+    assert li["E"] == pytest.approx(5e-4 / float(A[ns + D].max()), rel=1e-9)
+    for k in (names[0], names[2], "m_x"):
+        assert l1[k] == 0.0 and li[k] == 0.0
+
+
+def test_studies_are_the_3d_configurations():
+    assert bench.STUDIES["droplet_field_3d"][1] == 500
+    assert bench.STUDIES["shock_droplet_3d"][1] == 200

@@ -144,3 +144,32 @@ def test_mixed_full_size_shock_bubble_stays_admissible(mp):
     ctx.step_n(U, 200)
     torch.cuda.synchronize()
     assert ctx.status() == 0
+
+
+def test_precision_study_small_3d(mp):
+    """bench.py's mixed-vs-FP64 study (the 3D configurations' report) on a
+    small droplet field: both paths in lockstep with the FP64 path's step
+    size, the study's per-field L1 against an independent host computation
+    of the same norm, and the n-step mixed-precision bound above."""
+    import bench
+    p = W.droplet_field_3d(n=24, ndrops=4, seed=2, rmin=3.0, rmax=5.0)
+    out = bench.precision_study(mp, torch, "droplet_field_3d_24", p, 6, timed_steps=2, every=3)
+    assert out["status"] == {"fp64": 0, "mixed": 0}
+    assert out["fp64"]["status"] == 0 and out["mixed"]["status"] == 0
+    assert [h["step"] for h in out["error_vs_fp64"]["history"]] == [3, 6]
+    # the same lockstep on the host side of the check
+    c64, cmx = mp.Context(p), mp.Context(p, precision=mp.MIXED)
+    A, B = c64.init_state(torch.from_numpy(p.prim)), cmx.init_state(torch.from_numpy(p.prim))
+    t = 0.0
+    for _ in range(6):
+        dt = float(c64.dt_gamma(A)[0])
+        c64.rk_step(A, dt)
+        cmx.rk_step(B, dt)
+        t += dt
+    assert t == pytest.approx(out["error_vs_fp64"]["t_end"], rel=1e-15)
+    Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
+    err = scaled_l1(Bh, Ah, p.ns, p.dim)
+    got = np.array(list(out["error_vs_fp64"]["l1"].values()))
+    print(f"study 24^3, 6 steps: L1 {np.array2string(got, precision=2)}")
+    assert np.allclose(got, err, rtol=1e-6, atol=0)
+    assert got.max() <= 6 * 10 * 2 ** -24 * 20
