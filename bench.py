@@ -378,7 +378,7 @@ def adjoint_section(mp, torch, nsteps=200, every=20, n=512):
             "backward_kernel_ms": {k: v[0] for k, v in prof.items() if v[1]},
             "memory_mb": {"state": state_mb, "checkpoints": state_mb * len(range(0, nsteps, every)),
                           "segment_states": state_mb * (every + 1)},
-            "J": float(J), "grad_norm": float(grad.norm()), "status": ctx.status(),
+            "J": float(J.detach()), "grad_norm": float(grad.detach().norm()), "status": ctx.status(),
             "note": "backward = per segment one forward replay step per step (stage states and flags "
                     "recorded) + per step the reverse of SSP-RK3"}
 
