@@ -582,7 +582,7 @@ def main():
                          "peak_source": "nominal GB300 FP64 rate (recipe table); FP64 pipe, not HBM, binds"},
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "limiter_activity": {k: stats[k] / max(stats["faces"], 1) for k in
-                                 ("hllc_fallback", "cdi_dropped", "theta_p", "theta_t", "ylim")},
+                                 ("hllc_fallback", "cdi_dropped", "theta_p", "theta_t", "ylim", "diff_dropped")},
             "status": status,
         }
         if mixed is not None:

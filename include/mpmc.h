@@ -85,6 +85,8 @@ extern "C" {
 #define MPMC_F_CDI_DROPPED (1u << 5)   /* regularization flux not added (Sec. 3.3.2, last paragraph) */
 #define MPMC_F_YLIM_L (1u << 6)        /* mass-fraction limiter changed the left state */
 #define MPMC_F_YLIM_R (1u << 7)
+#define MPMC_F_DIFF_DROPPED (1u << 8) /* diffusive flux (species diffusion, viscous stress, conduction) not
+                                         added: the regularization flux's limiter applied to it */
 
 /* Grid (Sec. 3.1: isotropic Cartesian cells). n[d] = 1 for inactive
  * directions; active directions need n[d] >= 3. */
@@ -144,6 +146,7 @@ typedef struct {
   uint64_t hllc_fallback;  /* faces that took the first-order flux */
   uint64_t cdi_dropped;    /* faces whose regularization flux was dropped */
   uint64_t theta_p, theta_t, ylim; /* interpolation-limiter activations (face sides) */
+  uint64_t diff_dropped;   /* faces whose diffusive flux was dropped (MPMC_F_DIFF_DROPPED) */
 } mpmc_stats;
 
 typedef struct mpmc_ctx mpmc_ctx;

@@ -1229,8 +1229,15 @@ struct Solver {
       }
     }
 
-    /* species diffusion, not limited (reading); energy carries
-     * sum_c J^c h^c (reading: without the extra Y^c/Y_p factor) */
+    /* diffusive flux F_nu: species diffusion (energy carries sum_c J^c h^c;
+     * reading: without the extra Y^c/Y_p factor), viscous stress and heat
+     * conduction.  Reading: it passes the same flux limiter as the
+     * regularization flux (Sec. 3.3.2, last paragraph) -- added to the
+     * admissible flux when the pseudo-update stays admissible, else not
+     * added at this face -- so that the next state is admissible with
+     * every flux in */
+    R Fnu[MAXV];
+    for (int v = 0; v < nv; ++v) Fnu[v] = R(0.0);
     if (p.diffusion) {
       R rb = 0.5 * (ci.rho + cj.rho);
       R Jh(0.0);
@@ -1248,11 +1255,11 @@ struct Solver {
           if (p.phase[k] != ph) continue;
           R Yk = 0.5 * (ci.Y[k] + cj.Y[k]);
           R J = -rb * (Yp * Bf[k] * Gf[k] - Yk * Ssum);
-          F[k] = F[k] + J;
+          Fnu[k] = J;
           Jh = Jh + J * 0.5 * (ci.h[k] + cj.h[k]);
         }
       }
-      F[ns + D] = F[ns + D] + Jh;
+      Fnu[ns + D] = Jh;
     }
 
     /* viscous stress and heat conduction (Eq. DiffusionTerms and the stress
@@ -1283,10 +1290,19 @@ struct Solver {
       R work(0.0);
       for (int i = 0; i < D; ++i) {
         R tau = mub * (gu[i][d] + gu[d][i] - (i == d ? (2.0 / 3.0) * div : R(0.0)));
-        F[ns + i] = F[ns + i] - tau;
+        Fnu[ns + i] = -tau;
         work = work + 0.5 * (ci.u[i] + cj.u[i]) * tau;
       }
-      F[ns + D] = F[ns + D] - work - lamb * (cj.T - ci.T) / p.dx;
+      Fnu[ns + D] = Fnu[ns + D] - work - lamb * (cj.T - ci.T) / p.dx;
+    }
+    if (p.diffusion || p.viscous) {
+      R Ft[MAXV];
+      for (int v = 0; v < nv; ++v) Ft[v] = F[v] + Fnu[v];
+      if (p.pos_limiter && !passes(Ft)) {
+        flags |= ORC_F_DIFF_DROPPED;
+      } else {
+        for (int v = 0; v < nv; ++v) F[v] = Ft[v];
+      }
     }
     return flags;
   }

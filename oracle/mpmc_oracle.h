@@ -42,6 +42,7 @@ extern "C" {
 #define ORC_F_CDI_DROPPED (1u << 5)
 #define ORC_F_YLIM_L (1u << 6)
 #define ORC_F_YLIM_R (1u << 7)
+#define ORC_F_DIFF_DROPPED (1u << 8)
 
 typedef struct {
   /* grid */

@@ -20,7 +20,7 @@ MAXS = 4
 OK, INVALID_ARG, CUDA_ERROR, INADMISSIBLE, EOS_NO_CONVERGE, OUT_OF_MEMORY = 0, 1, 2, 3, 4, 5
 FP64, MIXED = 0, 1
 F_THETA_T_L, F_THETA_T_R, F_THETA_P_L, F_THETA_P_R = 1, 2, 4, 8
-F_HLLC_FALLBACK, F_CDI_DROPPED, F_YLIM_L, F_YLIM_R = 16, 32, 64, 128
+F_HLLC_FALLBACK, F_CDI_DROPPED, F_YLIM_L, F_YLIM_R, F_DIFF_DROPPED = 16, 32, 64, 128, 256
 
 
 class MpmcError(RuntimeError):
@@ -54,7 +54,8 @@ class StageC(ctypes.Structure):
 
 
 class StatsC(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_uint64) for f in ("faces", "hllc_fallback", "cdi_dropped", "theta_p", "theta_t", "ylim")]
+    _fields_ = [(f, ctypes.c_uint64) for f in ("faces", "hllc_fallback", "cdi_dropped", "theta_p", "theta_t", "ylim",
+                                                     "diff_dropped")]
 
 
 def _load():

@@ -325,7 +325,9 @@ __global__ void __launch_bounds__(VJP_THREADS)
   }
 
   // ---- species diffusion (Eq. SpeciesMassDiffusion), stores its cache slots
+  // (zeros where the forward pass dropped the diffusive flux)
   if (P.diffusion) {
+    const bool dropped = (fl & F_DIFF_DROPPED) != 0;
     const double rbar = 0.5 * (wget(P, Wc, P.wRho, ri) + wget(P, Wc, P.wRho, rj));
     double lrb = 0.0;
 #pragma unroll
@@ -350,8 +352,8 @@ __global__ void __launch_bounds__(VJP_THREADS)
         const double Ybk = 0.5 * (Yi[k] + Yj[k]);
         const double J = -rbar * (Yp * Bf[k] * G[k] - Ybk * S);
         const double hi = h_k(P, k, Pi, Ti), hj = h_k(P, k, Pj, Tj);
-        const double lJ = nu[k] + nu[NS + D] * 0.5 * (hi + hj);
-        const double lh = nu[NS + D] * J * 0.5;
+        const double lJ = dropped ? 0.0 : nu[k] + nu[NS + D] * 0.5 * (hi + hj);
+        const double lh = dropped ? 0.0 : nu[NS + D] * J * 0.5;
         aT[0] += lh * P.cp[k];
         aP[0] += lh * P.b[k];
         aT[1] += lh * P.cp[k];
@@ -778,11 +780,13 @@ __device__ __forceinline__ Pre preimages(int c, int n, int lo, int hi) {
 // Per face of direction DIR, after k_face_adj: the reverse of the viscous
 // stress and heat-conduction flux (Eq. DiffusionTerms, second-order central,
 // as k_face): adds to the T and velocity line slots of the two face cells and
-// writes the mu, lambda slots and the tangential neighbours' velocity slots.
+// writes the mu, lambda slots and the tangential neighbours' velocity slots
+// (zeros where the forward pass dropped the diffusive flux).
 template <int NS, int D, int DIR>
 __global__ void __launch_bounds__(VJP_THREADS)
     k_face_visc_adj(const KParams P, const double* __restrict__ Wc, const double* __restrict__ scal,
-                    const double* __restrict__ lamL, const double coef, const int mul_dt, double* __restrict__ C) {
+                    const uint32_t* __restrict__ tape, const double* __restrict__ lamL, const double coef,
+                    const int mul_dt, double* __restrict__ C) {
   constexpr int NV = NS + D + 1;
   constexpr int d = DIR;
   const int f0 = P.n[0] + (d == 0), f1 = P.n[1] + (d == 1), f2 = P.n[2] + (d == 2);
@@ -811,6 +815,10 @@ __global__ void __launch_bounds__(VJP_THREADS)
   }
   // (k_face_adj has zeroed every slot of a face whose flux adjoint is zero)
   if (!any) return;
+  if (tape[fid] & F_DIFF_DROPPED) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) nu[v] = 0.0;
+  }
   auto put = [&](int q, double v) { C[(long long)q * nf + fid] = v; };
   auto add = [&](int q, double v) { C[(long long)q * nf + fid] += v; };
 
@@ -1423,16 +1431,16 @@ struct AdjImpl {
     AdjFaceImpl<NS, D, RC_WENO5Z>::face(P, s, d, Wc, Uk, Uin, scal, tape, lamL, coef, mul_dt, C);
   }
   static void face_visc(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* scal,
-                        const double* lamL, double coef, int mul_dt, double* C) {
+                        const uint32_t* tape, const double* lamL, double coef, int mul_dt, double* C) {
     long long nf = 1;
     for (int e = 0; e < 3; ++e) nf *= (long long)(P.n[e] + (e == d));
     const unsigned nb = nblocks(nf, VJP_THREADS);
     if (d == 0)
-      k_face_visc_adj<NS, D, 0><<<nb, VJP_THREADS, 0, s>>>(P, Wc, scal, lamL, coef, mul_dt, C);
+      k_face_visc_adj<NS, D, 0><<<nb, VJP_THREADS, 0, s>>>(P, Wc, scal, tape, lamL, coef, mul_dt, C);
     else if (d == 1)
-      k_face_visc_adj<NS, D, (D > 1 ? 1 : 0)><<<nb, VJP_THREADS, 0, s>>>(P, Wc, scal, lamL, coef, mul_dt, C);
+      k_face_visc_adj<NS, D, (D > 1 ? 1 : 0)><<<nb, VJP_THREADS, 0, s>>>(P, Wc, scal, tape, lamL, coef, mul_dt, C);
     else
-      k_face_visc_adj<NS, D, (D > 2 ? 2 : 0)><<<nb, VJP_THREADS, 0, s>>>(P, Wc, scal, lamL, coef, mul_dt, C);
+      k_face_visc_adj<NS, D, (D > 2 ? 2 : 0)><<<nb, VJP_THREADS, 0, s>>>(P, Wc, scal, tape, lamL, coef, mul_dt, C);
   }
   static void gather(const KParams& P, cudaStream_t s, int d, const double* C, int first, double* gW, double* gU) {
     const unsigned nb = nblocks(P.ncell, CELL_THREADS);

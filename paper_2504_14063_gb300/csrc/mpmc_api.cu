@@ -468,7 +468,7 @@ static void stage_vjp(mpmc_ctx* c, cudaStream_t s, const double* U, const uint32
     {
       ProfScope ps(c, FAM_ADJ_FACE, s);
       c->aops.face(P, s, d, c->Wc, U, c->Uin, c->scal, tape + off, lamL, coef, mul_dt, c->Cslots);
-      if (P.viscous) c->aops.face_visc(P, s, d, c->Wc, c->scal, lamL, coef, mul_dt, c->Cslots);
+      if (P.viscous) c->aops.face_visc(P, s, d, c->Wc, c->scal, tape + off, lamL, coef, mul_dt, c->Cslots);
     }
     ProfScope ps(c, FAM_ADJ_PRIM, s);
     c->aops.gather(P, s, d, c->Cslots, d == 0, c->gW, c->gU);
@@ -616,6 +616,7 @@ extern "C" int mpmc_get_stats(mpmc_ctx* c, mpmc_stats* out, int reset) {
   out->theta_p = s[3];
   out->theta_t = s[4];
   out->ylim = s[5];
+  out->diff_dropped = s[6];
   if (reset) {
     cudaMemset(c->stats, 0, sizeof(s));
     c->faces_done = 0;

@@ -22,7 +22,8 @@ enum { BC_PERIODIC = 0, BC_WALL = 1, BC_ZEROGRAD = 2, BC_INFLOW = 3 };
 enum { ST_OK = 0, ST_INADMISSIBLE = 3, ST_EOS_NO_CONVERGE = 4 };
 enum : uint32_t {
   F_THETA_T_L = 1u << 0, F_THETA_T_R = 1u << 1, F_THETA_P_L = 1u << 2, F_THETA_P_R = 1u << 3,
-  F_HLLC_FALLBACK = 1u << 4, F_CDI_DROPPED = 1u << 5, F_YLIM_L = 1u << 6, F_YLIM_R = 1u << 7
+  F_HLLC_FALLBACK = 1u << 4, F_CDI_DROPPED = 1u << 5, F_YLIM_L = 1u << 6, F_YLIM_R = 1u << 7,
+  F_DIFF_DROPPED = 1u << 8
 };
 
 // Everything a kernel needs, passed by value (lives in the constant bank).

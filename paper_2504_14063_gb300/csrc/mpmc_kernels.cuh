@@ -489,7 +489,13 @@ __global__ void __launch_bounds__(FACE_THREADS)
     }
   }
 
-  // species diffusion (Eq. SpeciesMassDiffusion), not limited
+  // diffusive flux F_nu: species diffusion (Eq. SpeciesMassDiffusion),
+  // viscous stress and heat conduction.  It passes the same flux limiter as
+  // the regularization flux: added to the admissible flux when both
+  // pseudo-updates stay admissible, else not added at this face.
+  double Fnu[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Fnu[v] = 0.0;
   if (P.diffusion) {
     const double rb = 0.5 * (wget(P, Wc, P.wRho, ri) + wget(P, Wc, P.wRho, rj));
     double Jh = 0.0;
@@ -510,11 +516,11 @@ __global__ void __launch_bounds__(FACE_THREADS)
       for (int k = 0; k < NS; ++k) {
         if (P.phase[k] != ph) continue;
         const double J = -rb * (Yp * Bf[k] * G[k] - 0.5 * (Yi[k] + Yj[k]) * S);
-        Fx[k] += J;
+        Fnu[k] = J;
         Jh += J * (0.5 * (h_k(P, k, Pi, Ti) + h_k(P, k, Pj, Tj)));
       }
     }
-    Fx[NS + D] += Jh;
+    Fnu[NS + D] = Jh;
   }
 
   // viscous stress and heat conduction (Eq. DiffusionTerms), second-order
@@ -563,10 +569,21 @@ __global__ void __launch_bounds__(FACE_THREADS)
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       const double tau = mub * (gu[i][d] + gu[d][i] - (i == d ? (2.0 / 3.0) * div : 0.0));
-      Fx[NS + i] -= tau;
+      Fnu[NS + i] = -tau;
       work += 0.5 * (ui[i] + uj[i]) * tau;
     }
-    Fx[NS + D] -= work + lamb * (Tj - Ti) * P.inv_dx;
+    Fnu[NS + D] -= work + lamb * (Tj - Ti) * P.inv_dx;
+  }
+  if (P.diffusion || P.viscous) {
+    double Ft[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Ft[v] = Fx[v] + Fnu[v];
+    if (P.pos_limiter && !passes(Ft)) {
+      fl |= F_DIFF_DROPPED;
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fx[v] = Ft[v];
+    }
   }
 
 #pragma unroll
@@ -578,6 +595,7 @@ __global__ void __launch_bounds__(FACE_THREADS)
     if (fl & (F_THETA_P_L | F_THETA_P_R)) atomicAdd(stats + 3, 1ull);
     if (fl & (F_THETA_T_L | F_THETA_T_R)) atomicAdd(stats + 4, 1ull);
     if (fl & (F_YLIM_L | F_YLIM_R)) atomicAdd(stats + 5, 1ull);
+    if (fl & F_DIFF_DROPPED) atomicAdd(stats + 6, 1ull);
   }
 }
 

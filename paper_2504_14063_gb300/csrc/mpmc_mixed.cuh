@@ -872,6 +872,11 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
     }
   }
 
+  // the diffusive flux passes the regularization flux's limiter (as on the
+  // FP64 path; FP32 test, FP64 when too close to call)
+  float Fnu[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Fnu[v] = 0.f;
   if (P.diffusion) {
     const float idx = P.f32.inv_dx;
     const float rb = 0.5f * (wgetf(P, Wc, P.wRho, ri) + wgetf(P, Wc, P.wRho, rj));
@@ -893,16 +898,15 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
       for (int k = 0; k < NS; ++k) {
         if (P.phase[k] != ph) continue;
         const float J = -rb * (Yp * Bf[k] * G[k] - 0.5f * (Yi[k] + Yj[k]) * S);
-        Fx[k] += J;
+        Fnu[k] = J;
         const float hi = sp[k].cp * Ti + sp[k].b * Pi + sp[k].q;
         const float hj = sp[k].cp * Tj + sp[k].b * Pj + sp[k].q;
         Jh += J * (0.5f * (hi + hj));
       }
     }
-    Fx[NS + D] += Jh;
+    Fnu[NS + D] = Jh;
   }
 
-#pragma unroll
   // viscous stress and heat conduction in FP32, as the FP64 face kernel's
   // (second-order central; uniform u and T give exactly zero)
   if (P.viscous) {
@@ -946,10 +950,21 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       const float tau = mub * (gu[i][d] + gu[d][i] - (i == d ? (2.f / 3.f) * div : 0.f));
-      Fx[NS + i] -= tau;
+      Fnu[NS + i] = -tau;
       work += 0.5f * (ui[i] + uj[i]) * tau;
     }
-    Fx[NS + D] -= work + lamb * (Tj - Ti) * idx;
+    Fnu[NS + D] -= work + lamb * (Tj - Ti) * idx;
+  }
+  if (P.diffusion || P.viscous) {
+    float Ft[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Ft[v] = Fx[v] + Fnu[v];
+    if (P.pos_limiter && !passes(Ft)) {
+      fl |= F_DIFF_DROPPED;
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fx[v] = Ft[v];
+    }
   }
 
   // stored widened to FP64 (exact): the update then takes every flux with
@@ -963,6 +978,7 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
     if (fl & (F_THETA_P_L | F_THETA_P_R)) atomicAdd(stats + 3, 1ull);
     if (fl & (F_THETA_T_L | F_THETA_T_R)) atomicAdd(stats + 4, 1ull);
     if (fl & (F_YLIM_L | F_YLIM_R)) atomicAdd(stats + 5, 1ull);
+    if (fl & F_DIFF_DROPPED) atomicAdd(stats + 6, 1ull);
   }
 }
 

@@ -29,7 +29,7 @@ struct AdjOps {
   // the viscous stress and conduction flux of the same faces, reversed (adds
   // to the slots the face pass wrote)
   void (*face_visc)(const KParams&, cudaStream_t, int d, const double* Wc, const double* scal,
-                    const double* lamL, double coef, int mul_dt, double* C);
+                    const uint32_t* tape, const double* lamL, double coef, int mul_dt, double* C);
   void (*gather)(const KParams&, cudaStream_t, int d, const double* C, int first, double* gW, double* gU);
   void (*cell)(const KParams&, cudaStream_t, const double* U, const double* gW, const double* gU, double* out,
                double a, const double* x, double b, const double* y, double cz, const double* z);

@@ -61,6 +61,23 @@ int main(void) {{
                     b.ModelC.lambda_liquid.offset, b.StageC.Gamma.offset]
 
 
+def test_flag_and_status_constants_match_header():
+    """The binding's tape-bit, status, precision and interpolation constants
+    are the header's #define values (MPMC_F_*, MPMC_*)."""
+    from paper_2504_14063_gb300 import binding as b
+    txt = open(HDR).read()
+    defs = {}
+    for name, val in re.findall(r"#define\s+MPMC_([A-Z0-9_]+)\s+\(?([0-9]+u?(?:\s*<<\s*[0-9]+)?)\)?", txt):
+        defs[name] = eval(val.replace("u", ""))
+    flags = {k[2:]: v for k, v in defs.items() if k.startswith("F_")}
+    assert flags["DIFF_DROPPED"] == 256
+    for k, v in flags.items():
+        assert getattr(b, "F_" + k) == v, k
+    for k in ("OK", "INVALID_ARG", "CUDA_ERROR", "INADMISSIBLE", "EOS_NO_CONVERGE", "OUT_OF_MEMORY", "FP64", "MIXED"):
+        assert getattr(b, k) == defs[k], k
+    assert [s for s, _ in b.StatsC._fields_][-1] == "diff_dropped"
+
+
 def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     """Host-side validation happens before any CUDA call."""
     from paper_2504_14063_gb300 import binding as b

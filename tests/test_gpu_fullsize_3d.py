@@ -92,7 +92,7 @@ def _box_parity(mp, p, ctx, U, L, flags, centers, dt, G):
             fidx[d] = np.arange(st_d, st_d + nb[d])
             fidx[d] = fidx[d] % p.n[d] if periodic[d] else fidx[d]
             fg = flags[d][np.ix_(fidx[2], fidx[1], fidx[0])]
-            diff = ((fg ^ fo) & 0x3F) != 0
+            diff = ((fg ^ fo) & 0x13F) != 0
             # faces touching interior cells: box faces RIM .. RIM + 2 HALF along d
             sl = [slice(RIM, RIM + 2 * HALF)] * 3
             for s in (0, 1):

@@ -89,7 +89,7 @@ def _switch_mask(o, fl_a, fl_b, shape):
         n = list(o.problem.n)
         n[d] += 1
         nf = n[0] * n[1] * n[2]
-        ch = ((fl_a[off:off + nf] ^ fl_b[off:off + nf]) & 0x3F).reshape(n[2], n[1], n[0]) != 0
+        ch = ((fl_a[off:off + nf] ^ fl_b[off:off + nf]) & 0x13F).reshape(n[2], n[1], n[0]) != 0
         off += nf
         ax = 2 - d
         low = [slice(None)] * 3

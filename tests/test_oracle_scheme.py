@@ -426,3 +426,67 @@ def test_ssprk3_third_order_in_time():
         e = [np.abs(run(dt0 / 2 ** k)[v] - ref[v]).sum() for k in range(3)]
         orders = [np.log2(e[k] / e[k + 1]) for k in range(2)]
         assert all(2.8 < q < 3.2 for q in orders), (v, e, orders)
+
+
+def test_diffusive_flux_limiter_decisions_brute_force():
+    """Reading of Sec. 3.3.2's last paragraph extended to the diffusive flux
+    F_nu (species diffusion, its enthalpy flux): added to the admissible
+    flux F_a (HLLC and, if kept, the regularization flux) when both
+    pseudo-updates stay admissible, else not added at that face.  Checked
+    face by face on a two-phase field with viscosity x 100 and a
+    forward-Euler stage three times the CFL step: F_nu is the difference of the fluxes with and
+    without diffusion, both unlimited; F_a the limited flux without
+    diffusion.  A face flagged DIFF_DROPPED carries F_a and F_a + F_nu fails
+    a pseudo-update; every other face carries F_a + F_nu and passes."""
+    def make(diffusion, limiter):
+        p = W.random_smooth_2d(24, 20, seed=3, cdi=1, diffusion=diffusion)
+        for s in p.species:
+            s.mu *= 100.0
+        p.model.mu_liquid *= 100.0
+        p.model.pos_limiter = limiter
+        return p
+    p = make(1, 1)
+    o = Oracle(p, nthreads=2)
+    U = o.init_state()
+    dt, G, _ = o.dt_gamma(U)
+    dt *= 3.0
+    rk = (1.0, 0.0, 1.0)
+    _, _, flags, _ = o.stage(U, U, rk, dt, G, flags=True)
+    F, _ = o.face_fluxes(U, U, rk, dt, G)
+    Fa, _ = Oracle(make(0, 1), nthreads=2).face_fluxes(U, U, rk, dt, G)
+    Fon, _ = Oracle(make(1, 0), nthreads=2).face_fluxes(U, U, rk, dt, G)
+    Foff, _ = Oracle(make(0, 0), nthreads=2).face_fluxes(U, U, rk, dt, G)
+    sp = p.species
+    D = p.dim
+    lam = 2 * D * rk[2] * dt / p.dx
+    n_drop = n_keep = 0
+    off = 0
+    for d in range(D):
+        nf = F[d][0].size
+        fl = flags[off:off + nf].reshape(F[d].shape[1:])
+        off += nf
+        axis = 2 - d
+        for f in range(1, F[d].shape[1 + axis] - 1):
+            sf = [slice(None)] * 3
+            sf[axis] = f
+            si = [slice(None)] * 3
+            si[axis] = f - 1
+            at = lambda A, s: A[(slice(None),) + tuple(s)]
+            Fnu = at(Fon[d], sf) - at(Foff[d], sf)
+            base_i = (rk[0] + rk[1]) * at(U, si)
+            base_j = (rk[0] + rk[1]) * at(U, sf)
+            drop = (fl[tuple(sf)] & 256) != 0
+            Fall = at(Fa[d], sf) + Fnu
+            ok_all = _admissible(base_i - lam * Fall, sp) & _admissible(base_j + lam * Fall, sp)
+            got = at(F[d], sf)
+            scale = np.abs(at(Fa[d], sf)).max(axis=0) + np.abs(Fnu).max(axis=0)
+            err_keep = np.abs(got - Fall).max(axis=0) / scale
+            err_drop = np.abs(got - at(Fa[d], sf)).max(axis=0) / scale
+            assert np.all(err_drop[drop] <= 1e-13)
+            assert np.all(err_keep[~drop] <= 1e-13)
+            assert not np.any(ok_all[drop])
+            assert np.all(ok_all[~drop])
+            n_drop += int(drop.sum())
+            n_keep += int((~drop).sum())
+    print(f"diffusive flux dropped at {n_drop} of {n_drop + n_keep} interior faces")
+    assert n_drop > 10 and n_keep > n_drop
