@@ -687,24 +687,30 @@ __device__ __forceinline__ void state_from_primitive(const KParams& P, const dou
 // rhoY_k >= -YTOL rho, rho > 0, 1 - sum rhoY_k b_k > 0,
 // rho E - |m|^2/2 - rho sum rhoY_k q_k > 0
 template <int NS, int D>
-__device__ __forceinline__ bool admissible(const KParams& P, const double* U) {
+__device__ __forceinline__ bool admissible_bq(const double* b, const double* q, bool has_b, bool has_q,
+                                              const double* U) {
   double rho = 0.0, sb = 0.0, sq = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     rho += U[k];
-    if (P.has_b) sb += U[k] * P.b[k];
-    if (P.has_q) sq += U[k] * P.q[k];
+    if (has_b) sb += U[k] * b[k];
+    if (has_q) sq += U[k] * q[k];
   }
   // (without covolumes or reference energies the b and q terms are zero:
   // they are skipped, not evaluated as 1 - 0 and x - 0)
-  bool ok = rho > 0.0 && (!P.has_b || (1.0 - sb) > 0.0);
+  bool ok = rho > 0.0 && (!has_b || (1.0 - sb) > 0.0);
 #pragma unroll
   for (int k = 0; k < NS; ++k) ok = ok && (U[k] >= -YTOL * rho);
   double mm = 0.0;
 #pragma unroll
   for (int d = 0; d < D; ++d) mm += U[NS + d] * U[NS + d];
   const double ei = rho * U[NS + D] - 0.5 * mm;
-  return ok && ((P.has_q ? ei - rho * sq : ei) > 0.0);
+  return ok && ((has_q ? ei - rho * sq : ei) > 0.0);
+}
+
+template <int NS, int D>
+__device__ __forceinline__ bool admissible(const KParams& P, const double* U) {
+  return admissible_bq<NS, D>(P.b, P.q, P.has_b, P.has_q, U);
 }
 
 // mass-fraction limiter of Sec. 3.3.1 on one face side (Yc: cell values)

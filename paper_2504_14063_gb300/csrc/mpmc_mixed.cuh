@@ -570,6 +570,51 @@ __device__ __forceinline__ int admissible_f(const KParams& P, const float* Unf, 
   return undecided ? -1 : 0;
 }
 
+// The FP64 test of one cell's pseudo-update T = rk0 U^n + rk1 U^(k) + s F
+// (Eqs. PositivityReqs1/2, the FP64 path's admissible()), for a flux the
+// FP32 test could not decide.  Streams over the components, reloading each
+// from memory when it is needed again, so that only the running sums are
+// held: the FP64 states of both cells kept in registers at every limiter
+// test made the face kernel spill in the common path.
+template <int NS, int D>
+__device__ __forceinline__ bool admissible_stream(const KParams& P, const double* __restrict__ Un,
+                                                  const double* __restrict__ Uk, const double* __restrict__ Uin,
+                                                  const CRef r, const float* Ft, const double rk0, const double rk1,
+                                                  const double s) {
+  const bool inflow = r.idx == P.ncell;
+  // (a wall's mirror image negates the cell's momentum component d, as
+  // load_U does, before the flux term is added)
+  auto T = [&](int v) {
+    double un = inflow ? Uin[v] : Un[(long long)v * P.ncell + r.idx];
+    double uk = inflow ? Uin[v] : Uk[(long long)v * P.ncell + r.idx];
+    if (v >= NS && v < NS + D) {
+      un *= sgn_flip(r.flip, v - NS);
+      uk *= sgn_flip(r.flip, v - NS);
+    }
+    return rk0 * un + rk1 * uk + s * (double)Ft[v];
+  };
+  double rho = 0.0, sb = 0.0, sq = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const double t = T(k);
+    rho += t;
+    if (P.has_b) sb += t * P.b[k];
+    if (P.has_q) sq += t * P.q[k];
+  }
+  if (!(rho > 0.0) || (P.has_b && !((1.0 - sb) > 0.0))) return false;
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+    if (!(T(k) >= -YTOL * rho)) return false;
+  double mm = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double t = T(NS + d);
+    mm += t * t;
+  }
+  const double ei = rho * T(NS + D) - 0.5 * mm;
+  return (P.has_q ? ei - rho * sq : ei) > 0.0;
+}
+
 // per face: FP32 pipeline; the limiter's decisions from FP32 copies of the
 // states with a margin, in FP64 when a state is too close to call
 // DIR: the face direction, a template parameter so that every array indexed
@@ -749,18 +794,8 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
     const int b = admissible_f<NS, D>(P, Unj, Ukj, Ft, r0, r1, lf);
     if (b == 0) return false;
     if (a == 1 && b == 1) return true;
-    double Uni_[NV], Unj_[NV], Uki_[NV], Ukj_[NV], Ti_[NV], Tj_[NV];
-    load_U<NS, D>(P, Un, Uin, ri, Uni_);
-    load_U<NS, D>(P, Un, Uin, rj, Unj_);
-    load_U<NS, D>(P, Uk, Uin, ri, Uki_);
-    load_U<NS, D>(P, Uk, Uin, rj, Ukj_);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const double f = (double)Ft[v];
-      Ti_[v] = rk0 * Uni_[v] + rk1 * Uki_[v] - lam * f;
-      Tj_[v] = rk0 * Unj_[v] + rk1 * Ukj_[v] + lam * f;
-    }
-    return admissible<NS, D>(P, Ti_) && admissible<NS, D>(P, Tj_);
+    return admissible_stream<NS, D>(P, Un, Uk, Uin, ri, Ft, rk0, rk1, -lam) &&
+           admissible_stream<NS, D>(P, Un, Uk, Uin, rj, Ft, rk0, rk1, lam);
   };
   if (P.pos_limiter && !passes(Fx)) {
     StateF<NS> si, sj;
