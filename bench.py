@@ -37,10 +37,10 @@ L2_BYTES = 129 * 2 ** 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_face launch of this
 # workload from an ncu capture (profiles/k_face_shock_bubble_2d_1024x512_fp64.md),
 # reported while the kernel's sources hash to the captured version
-K_FACE_TRAFFIC_BYTES = 119.46e6
+K_FACE_TRAFFIC_BYTES = 119.78e6
 K_FACE_SOURCES = ("paper_2504_14063_gb300/csrc/mpmc_kernels.cuh", "paper_2504_14063_gb300/csrc/mpmc_device.cuh",
                   "paper_2504_14063_gb300/csrc/mpmc_kernels_d2.cu")
-K_FACE_SOURCES_SHA256 = "1e91393309a8601ad1dae8f24100432c1d4f26ff278bea829086fdb04579777e"
+K_FACE_SOURCES_SHA256 = "54412546803647e03e3d752381c390cf4f9faf9da355cf77ae95d764d0359eb8"
 
 
 def k_face_traffic():
