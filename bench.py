@@ -240,6 +240,8 @@ def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=
         if n % every == 0 or n == steps:
             l1, li = field_errors(A, B, p)
             hist.append({"step": n, "t": t_phys, "l1_max": max(l1.values()), "linf_max": max(li.values())})
+            print(json.dumps({"study": name, **hist[-1], "elapsed_s": time.perf_counter() - t0}),
+                  file=sys.stderr, flush=True)
     torch.cuda.synchronize()
     out["lockstep_s"] = time.perf_counter() - t0
     out["error_vs_fp64"] = {"steps": steps, "t_end": t_phys, "dt": "common: the FP64 path's CFL step each step",
