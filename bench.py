@@ -185,14 +185,19 @@ STUDIES = {
 }
 
 
-def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=None):
+def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=None, twin=False):
     """The mixed path against the FP64 path on a 3D workload at full size:
     both advanced in lockstep from the same initial state with a common
     step size (the FP64 path's CFL step, so that both reach the same
     physical times), per-field L1/Linf of the difference every `every`
     steps; throughput of each path timed separately with CUDA events over
     `timed_steps` steps (CFL step on the device, after 3 warm-up steps).
-    The states exceed L2 many times over, so no flush is needed."""
+    The states exceed L2 many times over, so no flush is needed.
+    twin: a third context, FP64, started from the initial state with a
+    relative perturbation 2^-24 xi (xi standard normal, seed 7) and
+    advanced with the same steps: its distance to the FP64 path is the
+    problem's own response to rounding at FP32 level, the scale against
+    which the mixed path's error is read."""
     steps = max(int(steps), 1)
     prim = torch.from_numpy(p.prim)
     out = {"study": name, "metric": "mixed vs FP64: per-field L1/Linf of the state difference; cell-updates/s",
@@ -230,16 +235,25 @@ def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=
 
     c64, cmx = mp.Context(p), mp.Context(p, precision=mp.MIXED)
     A, B = c64.init_state(prim), cmx.init_state(prim)
+    if twin:
+        ctw = mp.Context(p)
+        g = torch.Generator(device=A.device).manual_seed(7)
+        C = A * (1.0 + 2.0 ** -24 * torch.randn(A.shape, generator=g, device=A.device, dtype=A.dtype))
     hist, t_phys = [], 0.0
     t0 = time.perf_counter()
     for n in range(1, steps + 1):
         dt = float(c64.dt_gamma(A)[0])
         c64.rk_step(A, dt)
         cmx.rk_step(B, dt)
+        if twin:
+            ctw.rk_step(C, dt)
         t_phys += dt
         if n % every == 0 or n == steps:
             l1, li = field_errors(A, B, p)
             hist.append({"step": n, "t": t_phys, "l1_max": max(l1.values()), "linf_max": max(li.values())})
+            if twin:
+                t1, ti = field_errors(A, C, p)
+                hist[-1].update(twin_l1_max=max(t1.values()), twin_linf_max=max(ti.values()))
             print(json.dumps({"study": name, **hist[-1], "elapsed_s": time.perf_counter() - t0}),
                   file=sys.stderr, flush=True)
     torch.cuda.synchronize()
@@ -248,6 +262,10 @@ def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=
                             "norm": "state-scaled (partial densities by rho, momenta by rho*1000 m/s, energy by E)",
                             "l1": l1, "linf": li, "history": hist}
     out["status"] = {"fp64": c64.status(), "mixed": cmx.status()}
+    if twin:
+        out["error_vs_fp64"]["twin"] = {"perturbation": "U0 (1 + 2^-24 xi), xi standard normal, seed 7",
+                                        "l1": t1, "linf": ti}
+        out["status"]["fp64_twin"] = ctw.status()
     return out
 
 
@@ -403,6 +421,8 @@ def main():
                     help="instead of the benchmark line: the mixed-vs-FP64 precision study of a 3D workload "
                          "(one JSON line each)")
     ap.add_argument("--study-steps", type=int, default=None)
+    ap.add_argument("--twin", action="store_true",
+                    help="with --study: also an FP64 run from a 2^-24-perturbed initial state")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -425,7 +445,8 @@ def main():
             t0 = time.perf_counter()
             p = make(W)
             t_build = time.perf_counter() - t0
-            line = precision_study(mp, torch, name, p, args.study_steps or nsteps, t_build=t_build)
+            line = precision_study(mp, torch, name, p, args.study_steps or nsteps, t_build=t_build,
+                                   twin=args.twin)
             print(json.dumps(line), flush=True)
             del p
         return 0
