@@ -76,6 +76,8 @@ def flops_per_face(ns, D, cdi, diffusion, pos_limiter=True):
             f += 2 * (3 * nv) + 2 * (4 * ns + 2 * D + 6)
     if diffusion:
         f += 3 + ns * 10 + 6 * ns + 2
+        if pos_limiter:
+            f += 2 * (3 * nv) + 2 * (4 * ns + 2 * D + 6)       # the diffusive flux's pseudo-updates
     return f
 
 

@@ -41,3 +41,15 @@ def test_field_errors_scaling():
 def test_studies_are_the_3d_configurations():
     assert bench.STUDIES["droplet_field_3d"][1] == 500
     assert bench.STUDIES["shock_droplet_3d"][1] == 200
+
+
+def test_flops_per_face_of_the_benchmark_workload():
+    """The algorithmic count behind roofline.achieved: 1592 FP64 operations
+    per face for 3 species in 2D with CDI and the positivity limiter; with
+    diffusion on, the flux itself and its pseudo-update test add to it."""
+    assert bench.flops_per_face(3, 2, 1, 0) == 1592
+    nv = 3 + 2 + 1
+    extra_flux = 3 + 3 * 10 + 6 * 3 + 2
+    extra_test = 2 * (3 * nv) + 2 * (4 * 3 + 2 * 2 + 6)
+    assert bench.flops_per_face(3, 2, 1, 1) == 1592 + extra_flux + extra_test
+    assert bench.flops_per_face(3, 2, 1, 1, pos_limiter=False) < bench.flops_per_face(3, 2, 1, 1)
