@@ -983,10 +983,12 @@ struct Solver {
     return true;
   }
 
-  /* numerical flux through the face between padded cells c0 and c1 = c0 +
-   * stride(d).  Un/Uk: padded U^n and U^(k).  Returns flag bits. */
-  uint32_t face_flux(int d, size_t c0, double rk0, double rk1, double rk2, double dt,
-                     const R& Gamma, R* F) const {
+  /* face states of the face between padded cells c0 and c1 = c0 +
+   * stride(d) (Sec. 3.1.3 steps 1-3 and the interpolation limiters of
+   * Sec. 3.3.1): mass fractions, velocity, pressure and temperature of each
+   * side.  Returns the interpolation-limiter flag bits. */
+  uint32_t face_states(int d, size_t c0, R* YL, R* YR, R* uL, R* uR, R& PL, R& PR, R& TL,
+                       R& TR) const {
     const long st = G.stride(d);
     uint32_t flags = 0;
     const Cell<R>* cc[6];
@@ -995,7 +997,6 @@ struct Solver {
     const Cell<R>& cj = *cc[3];
     const size_t c1 = (size_t)((long)c0 + st);
 
-    R YL[MAXS], YR[MAXS], uL[3], uR[3], PL, PR, TL, TR;
     if (p.recon_basis == 0) {
       /* step 1: averaged state on the face, its EOS and the matrices */
       R Ui[MAXV], Uj[MAXV], Ub[MAXV];
@@ -1117,6 +1118,19 @@ struct Solver {
       if (!p_admissible(YL, PL)) { PL = ci.P; flags |= ORC_F_THETA_P_L; }
       if (!p_admissible(YR, PR)) { PR = cj.P; flags |= ORC_F_THETA_P_R; }
     }
+    return flags;
+  }
+
+  /* numerical flux through the face between padded cells c0 and c1 = c0 +
+   * stride(d).  Un/Uk: padded U^n and U^(k).  Returns flag bits. */
+  uint32_t face_flux(int d, size_t c0, double rk0, double rk1, double rk2, double dt,
+                     const R& Gamma, R* F) const {
+    const long st = G.stride(d);
+    const Cell<R>& ci = cells[c0];
+    const Cell<R>& cj = cells[(size_t)((long)c0 + st)];
+    const size_t c1 = (size_t)((long)c0 + st);
+    R YL[MAXS], YR[MAXS], uL[3], uR[3], PL, PR, TL, TR;
+    uint32_t flags = face_states(d, c0, YL, YR, uL, uR, PL, PR, TL, TR);
 
     /* steps 4-6: face density from the EOS, conserved face states, HLLC */
     State<R> sLf, sRf;
@@ -1557,6 +1571,43 @@ void orc_candidate(const double* v6, int offset, int n, double* value, double* b
   candidate_poly<double>(v6, offset, n, a);
   *value = poly_at_one<double>(v6[2], a, n);
   *beta = jiang_shu_beta<double>(a, n);
+}
+
+int orc_y_limiter(const orc_params* p, double* Y, const double* Yc) {
+  if (check(p)) return -1;
+  Solver<double> s(*p);
+  return s.y_limiter(Y, Yc) ? 1 : 0;
+}
+
+int orc_face_states(const orc_params* p, const double* U, int d, int i, int j, int k, double* WL,
+                    double* WR, uint32_t* flags) {
+  if (check(p) || d < 0 || d >= p->dim) return ORC_INVALID;
+  Solver<double> s(*p);
+  int ic[3] = {i, j, k};
+  for (int e = 0; e < 3; ++e)
+    if (ic[e] < 0 || ic[e] >= s.G.n[e] + (e == d)) return ORC_INVALID;
+  s.load(U, s.Ukp);
+  s.fill_ghosts(s.Ukp);
+  int st = s.compute_cells(s.Ukp);
+  ic[d] -= 1; /* the cell on the face's low side */
+  const size_t c0 = s.G.pad(ic[0], ic[1], ic[2]);
+  double YL[MAXS], YR[MAXS], uL[3], uR[3], PL, PR, TL, TR;
+  uint32_t fl = s.face_states(d, c0, YL, YR, uL, uR, PL, PR, TL, TR);
+  const int ns = p->ns;
+  for (int q = 0; q < ns; ++q) {
+    WL[q] = YL[q];
+    WR[q] = YR[q];
+  }
+  for (int t = 0; t < 3; ++t) {
+    WL[ns + t] = uL[t];
+    WR[ns + t] = uR[t];
+  }
+  WL[ns + 3] = PL;
+  WR[ns + 3] = PR;
+  WL[ns + 4] = TL;
+  WR[ns + 4] = TR;
+  if (flags) *flags = fl;
+  return st;
 }
 
 int orc_char_matrices(const orc_params* p, int d, const double* Ubar, double* Sinv, double* S, double* scal) {

@@ -119,6 +119,17 @@ double orc_reconstruct(int kind, const double* v6, double eps);
  * i = v6[2]) fitted to the cell averages: its value at the right face of
  * cell i and its Jiang-Shu smoothness indicator on cell i */
 void orc_candidate(const double* v6, int offset, int n, double* value, double* beta);
+/* the mass-fraction limiter of Sec. 3.3.1 on one face side: Y[ns] (in/out)
+ * the reconstructed mass fractions, Yc[ns] the adjacent cell's; returns 1 if
+ * it changed Y, 0 if not, -1 on invalid parameters */
+int orc_y_limiter(const orc_params* p, double* Y, const double* Yc);
+/* face states of the face (i, j, k) of direction d of U (interior cells,
+ * ghosts filled as in orc_stage; the face's low cell is i-1 along d):
+ * W = [Y_0..Y_{ns-1}, u_0, u_1, u_2, P, T] of each side after the
+ * interpolation limiters of Sec. 3.3.1 (before them when pos_limiter = 0);
+ * flags receives their ORC_F_THETA_* / ORC_F_YLIM_* bits */
+int orc_face_states(const orc_params* p, const double* U, int d, int i, int j, int k, double* WL,
+                    double* WR, uint32_t* flags);
 /* characteristic matrices of direction d at the conserved state Ubar:
  * Sinv, S dense nc x nc row-major, nc = ns + dim + 1; scal = [rho, a, alpha, beta, X, rho*a] */
 int orc_char_matrices(const orc_params* p, int d, const double* Ubar, double* Sinv, double* S, double* scal);

@@ -108,6 +108,10 @@ def _declare(L):
     L.orc_candidate.restype = None
     L.orc_weno5z_jvp.argtypes = [_dp, _dp, d, _dp]
     L.orc_weno5z_jvp.restype = d
+    L.orc_y_limiter.argtypes = [P, _dp, _dp]
+    L.orc_y_limiter.restype = ctypes.c_int
+    L.orc_face_states.argtypes = [P, _dp, i, i, i, i, _dp, _dp, _u32p]
+    L.orc_face_states.restype = ctypes.c_int
 
 
 def _ptr(a):
@@ -292,6 +296,31 @@ class Oracle:
         val, beta = ctypes.c_double(), ctypes.c_double()
         self.lib.orc_candidate(_ptr(v), int(offset), int(n), ctypes.byref(val), ctypes.byref(beta))
         return val.value, beta.value
+
+    def y_limiter(self, Y, Yc):
+        """The mass-fraction limiter of Sec. 3.3.1 on one face side: returns
+        (limited Y, whether it changed Y)."""
+        Y = np.array(Y, dtype=np.float64)
+        Yc = np.ascontiguousarray(Yc, dtype=np.float64)
+        assert Y.shape == (self.problem.ns,) and Yc.shape == Y.shape
+        r = self.lib.orc_y_limiter(self.pp, _ptr(Y), _ptr(Yc))
+        assert r in (0, 1)
+        return Y, bool(r)
+
+    def face_states(self, U, d, face):
+        """Face states of the face `face` = (i, j, k) of direction d (its low
+        cell is i - 1 along d) after the interpolation limiters: (WL, WR,
+        flags, status), W = dict(Y, u, P, T)."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        ns = self.problem.ns
+        WL, WR = np.zeros(ns + 5), np.zeros(ns + 5)
+        fl = np.zeros(1, dtype=np.uint32)
+        i, j, k = (list(face) + [0, 0])[:3]
+        st = self.lib.orc_face_states(self.pp, _ptr(U), int(d), int(i), int(j), int(k), _ptr(WL), _ptr(WR),
+                                      _ptr(fl))
+        assert st != 1, "invalid face"
+        split = lambda w: dict(Y=w[:ns].copy(), u=w[ns:ns + 3].copy(), P=float(w[ns + 3]), T=float(w[ns + 4]))
+        return split(WL), split(WR), int(fl[0]), st
 
     def char_matrices(self, d, Ubar):
         nc = self.problem.ns + self.problem.dim + 1
