@@ -1,15 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the MPMC hot path: SSP-RK3 steps (three right-hand-side
-stages with the update fused in) of the 2D shock-bubble workload, 1024 x 512
-cells, 3 species in 2 phases, CDI on, FP64, on one GB300 per rank.
+stages with the update fused in) of the 3D droplet field, 256^3 periodic
+cells, 4 species (two stiffened liquids, air, helium) in 2 phases, CDI and
+non-dilute diffusion on, on one GB300 per rank; the FP64 path and the mixed
+path (FP32 bulk, FP64 EOS inversion / positivity bounds / RK accumulation).
 
-One JSON line on rank 0.  `value` is device-timed cell-updates/s (inputs
-resident in HBM, L2 flushed between steps outside the per-step events);
-`e2e` is the same metric through the host-buffer C-ABI entry, copies
-included; `roofline` is the face-flux kernel (the dominant one) against the
-FP64 ALU peak; `cpu_baseline` is the CPU oracle on the host cores.
-`--impl reference` times the CPU oracle itself (there is no other
-implementation of the paper's method to install).
+One JSON line on rank 0:
+  * `value`: device-timed cell-updates/s of the FP64 path (inputs resident
+    in HBM; the state, 1.07 GB per copy, is larger than L2, so no flush);
+    `mixed`: the same for the mixed path, its speedup and its per-field
+    L1 / Linf error against the FP64 path after a stated number of steps
+    from the initial state.  The timed steps follow those steps, from the
+    developed state;
+  * `e2e`: the same metric through the host-buffer C-ABI entry, copies
+    included;
+  * `roofline`: the FP64 face-flux kernel (the dominant one) against the
+    measured FP64 FMA rate; `rooflines`: every kernel family of both paths
+    against its binding pipe or HBM;
+  * `cpu_baseline`: the CPU oracle on the host cores, on a 16-plane slab of
+    the same field.
+`--impl reference` times the CPU oracle itself on that slab (there is no
+other implementation of the paper's method to install).
 With N ranks (torchrun) every rank runs an independent replica (the path is
 built for one GPU; the whole-job value sums the replicas).
 """
@@ -31,24 +42,34 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s (FP64 vs mixed at stated L1 error); adjoint/forward time ratio"
 UNIT = "cell-updates/s"
-FP64_PEAK_NOMINAL = 1.25e12   # GB300 FP64, nominal (no FP64 figure is measured in MEASURED_PEAKS)
+FP64_PEAK_NOMINAL = 1.25e12   # GB300 FP64, nominal (the recipe's table)
+GRID_N = 256                  # the droplet field's cells per direction
+CPU_SLAB_PLANES = 16          # z-planes of the field in the CPU oracle's sample
 L2_BYTES = 129 * 2 ** 20
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_face launch of this
-# workload from an ncu capture (profiles/k_face_shock_bubble_2d_1024x512_fp64.md),
-# reported while the kernel's sources hash to the captured version
-K_FACE_TRAFFIC_BYTES = 119.78e6
-K_FACE_SOURCES = ("paper_2504_14063_gb300/csrc/mpmc_kernels.cuh", "paper_2504_14063_gb300/csrc/mpmc_device.cuh",
-                  "paper_2504_14063_gb300/csrc/mpmc_kernels_d2.cu")
-K_FACE_SOURCES_SHA256 = "54412546803647e03e3d752381c390cf4f9faf9da355cf77ae95d764d0359eb8"
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of each kernel
+# on this workload, from an ncu capture of the same field at 128^3 scaled by
+# the faces (cells) of a 256^3 launch; reported only while the kernel's
+# sources hash to the captured version (None otherwise)
+TRAFFIC = {}
+TRAFFIC_SOURCES = ("paper_2504_14063_gb300/csrc/mpmc_kernels.cuh", "paper_2504_14063_gb300/csrc/mpmc_device.cuh",
+                   "paper_2504_14063_gb300/csrc/mpmc_kernels_d3.cu", "paper_2504_14063_gb300/csrc/mpmc_mixed.cuh",
+                   "paper_2504_14063_gb300/csrc/mpmc_mixed_d3.cu", "paper_2504_14063_gb300/csrc/mpmc_update.cuh")
+TRAFFIC_SHA256 = None
 
 
-def k_face_traffic():
+def sources_sha256():
     h = hashlib.sha256()
-    for f in K_FACE_SOURCES:
+    for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return K_FACE_TRAFFIC_BYTES if h.hexdigest() == K_FACE_SOURCES_SHA256 else None
+    return h.hexdigest()
+
+
+def traffic_of(kernel):
+    if TRAFFIC_SHA256 is None or kernel not in TRAFFIC:
+        return None
+    return TRAFFIC[kernel] if sources_sha256() == TRAFFIC_SHA256 else None
 
 
 def flops_per_face(ns, D, cdi, diffusion, pos_limiter=True):
@@ -120,27 +141,40 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def workload():
+def workload(n=GRID_N):
     from paper_2504_14063_gb300 import workloads as W
-    return W.shock_bubble_2d(nx=1024, ny=512, seed=0)
+    return W.droplet_field_3d(n=n)
 
 
-def config_of(p, extra=None):
-    c = {"workload": "shock_bubble_2d", "grid": list(p.n[:p.dim]), "cells": p.ncells, "species": p.ns,
-         "phases": 2, "cdi": bool(p.model.cdi), "diffusion": bool(p.model.diffusion),
-         "mach": 1.5, "integrator": "SSP-RK3", "cfl": p.model.cfl,
-         "l2": "flushed between steps (256 MiB write, outside the per-step events)"}
-    if extra:
-        c.update(extra)
-    return c
+def config_of(p):
+    """The workload, identical in both arms."""
+    return {"workload": "droplet_field_3d", "grid": list(p.n[:p.dim]), "cells": p.ncells, "species": p.ns,
+            "phases": 2, "droplets": 32, "cdi": bool(p.model.cdi), "diffusion": bool(p.model.diffusion),
+            "integrator": "SSP-RK3", "cfl": p.model.cfl,
+            "l2": f"inputs larger than L2 (state {p.nvars * p.ncells * 8 / 1e9:.2f} GB per copy), no flush"}
 
 
-def cpu_baseline(p, seconds=12.0):
+def slab_of(p, planes=CPU_SLAB_PLANES):
+    """The CPU oracle's bounded sample of the workload: its first `planes`
+    z-planes, periodic in x and y, zero-gradient in z."""
+    from paper_2504_14063_gb300 import workloads as W
+    prim = np.ascontiguousarray(p.prim[:, :planes])
+    return W.Problem(p.name + "_slab", 3, (p.n[0], p.n[1], planes), p.dx, p.species, p.model, prim,
+                     bc_lo=(p.bc_lo[0], p.bc_lo[1], W.BC_ZEROGRAD), bc_hi=(p.bc_hi[0], p.bc_hi[1], W.BC_ZEROGRAD))
+
+
+def slab_text(q):
+    return (f"SSP-RK3 steps of the oracle on a {q.n[0]}x{q.n[1]}x{q.n[2]} slab of the {q.n[0]}^3 field "
+            f"(its first {q.n[2]} z-planes, zero-gradient in z), {q.ncells} cells per step")
+
+
+def cpu_baseline(p, seconds=12.0, planes=CPU_SLAB_PLANES):
     """The CPU oracle, as it stands, on the host cores: SSP-RK3 steps of the
-    full workload until about `seconds` have passed."""
+    slab sample until about `seconds` have passed."""
     from oracle import Oracle
     cores = os.cpu_count() or 1
-    o = Oracle(p, nthreads=cores)
+    q = slab_of(p, planes)
+    o = Oracle(q, nthreads=cores)
     U = o.init_state()
     t0 = time.perf_counter()
     n = 0
@@ -150,16 +184,8 @@ def cpu_baseline(p, seconds=12.0):
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
-    # one thread: one step of the same workload
-    o1 = Oracle(p, nthreads=1)
-    t1 = time.perf_counter()
-    o1.rk_step(o1.init_state())
-    el1 = time.perf_counter() - t1
-    return {"value": p.ncells * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} SSP-RK3 steps of the full {p.n[0]}x{p.n[1]} workload from its initial state "
-                      f"({el:.1f} s, OpenMP threads = {cores})",
-            "single_thread": {"value": p.ncells / el1, "unit": UNIT, "cores": 1,
-                              "sample": f"1 SSP-RK3 step of the same workload ({el1:.1f} s)"}}
+    return {"value": q.ncells * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} {slab_text(q)} ({el:.1f} s, OpenMP threads = {cores})"}
 
 
 def field_errors(A, B, p):
@@ -292,10 +318,11 @@ def whole_job_value(world, cells, steps, seconds):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    p = workload()
+    p = workload(args.grid)
+    q = slab_of(p, min(CPU_SLAB_PLANES, p.n[2]))
     from oracle import Oracle
     cores = os.cpu_count() or 1
-    o = Oracle(p, nthreads=cores)
+    o = Oracle(q, nthreads=cores)
     U = o.init_state()
     for _ in range(args.warmup):
         U = o.rk_step(U)[0]
@@ -303,14 +330,13 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         U = o.rk_step(U)[0]
     el = time.perf_counter() - t0
-    v = p.ncells * args.steps / el
+    v = q.ncells * args.steps / el
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": config_of(p, {"l2": "n/a (CPU)"}),
+            "impl": "reference", "config": config_of(p),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} timed SSP-RK3 steps of the full workload after "
-                                       f"{args.warmup} warm-up steps"},
+                             "sample": f"{args.steps} timed {slab_text(q)}, after {args.warmup} warm-up steps"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -405,19 +431,127 @@ def adjoint_section(mp, torch, nsteps=200, every=20, n=512):
                     "recorded) + per step the reverse of SSP-RK3"}
 
 
+def timed_steps(torch, ctx, U, steps):
+    """`steps` SSP-RK3 steps of ctx on U, each bracketed by CUDA events on
+    torch's current stream (the context's stream is the legacy default
+    stream, which synchronizes with it); library profiling off.  Returns the
+    per-step times in ms."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        ev[k][0].record()
+        ctx.rk_step(U)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def kernel_pass(torch, ctx, U, steps):
+    """`steps` more steps with the library's per-launch CUDA events on its
+    stream: per kernel family, (ms per launch, launches per step)."""
+    ctx.profile(reset=True)
+    ctx.set_profiling(True)
+    for _ in range(steps):
+        ctx.rk_step(U)
+    torch.cuda.synchronize()
+    ctx.set_profiling(False)
+    prof = ctx.profile(reset=True)
+    return {k: (ms / n if n else 0.0, n / steps) for k, (ms, n) in prof.items()}
+
+
+def fma_peaks(mp, torch, reps=5):
+    """Measured FMA rates of the FP64 and FP32 pipes (mpmc_fma_probe, eight
+    independent chains per thread, 4 blocks of 256 threads per SM): the best
+    of `reps` launches, CUDA events on torch's current stream, with the SM
+    clock sampled over a second of repeated launches."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks = 4 * sms
+    out = {}
+    for label, fp64, iters in (("fp64", True, 4096), ("fp32", False, 131072)):
+        buf = torch.empty(blocks * 256, dtype=torch.float64 if fp64 else torch.float32, device="cuda")
+        mp.fma_probe(fp64, blocks, iters, buf)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            flops = mp.fma_probe(fp64, blocks, iters, buf)
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3
+            best = t if best is None or t < best else best
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 1.0:
+            mp.fma_probe(fp64, blocks, iters, buf)
+            torch.cuda.synchronize()
+        clk = clocks.stop()
+        out[label] = {"tflops": flops / best / 1e12, "launch_ms": best * 1e3, "flops_per_launch": flops,
+                      "blocks": blocks, "threads": 256, "iters": iters, "clocks": clk}
+    return out
+
+
+def update_bytes(p, stage):
+    """Bytes the divergence + RK update kernel moves as designed for one
+    launch: U^n (and U^(k) when distinct, stages 2 and 3), each face flux of
+    every direction once, and U^(k+1)."""
+    nv, D, N = p.nvars, p.dim, p.ncells
+    faces = sum(N // p.n[d] * (p.n[d] + 1) for d in range(D))
+    states = 2 if stage == 1 else 3
+    return 8 * nv * (states * N) + 8 * nv * faces
+
+
+def cache_fields(p):
+    """Fields of the primitive cache a context keeps per cell: T, P, rho, a,
+    Y_k, u_d; with CDI phi_0, psi, (Y^c/Y_p) rho_p, h_p rho_p of both
+    phases; with diffusion X^c/X_p and W^c D^c_p / W_p; with viscous terms
+    mu and lambda (the layout of the library's cache)."""
+    m = p.model
+    return (4 + p.ns + p.dim + (4 + p.ns if m.cdi else 0) + (2 * p.ns if m.diffusion else 0)
+            + (2 if m.viscous else 0))
+
+
+def prim_bytes(p, n_w, wbytes):
+    """Bytes of one primitive-recovery launch: U read, n_w cache fields written."""
+    return p.ncells * (8 * p.nvars + wbytes * n_w)
+
+
+def lockstep_error(mp, torch, p, c64, cmx, A, B, steps, every=25):
+    """FP64 (A) and mixed (B) advanced in lockstep with a common step (the
+    FP64 path's CFL step each step) from the same state; per-field L1/Linf
+    of the difference after `steps` steps and every `every` steps."""
+    hist, t_phys = [], 0.0
+    l1 = li = None
+    for n in range(1, steps + 1):
+        dt = float(c64.dt_gamma(A)[0])
+        c64.rk_step(A, dt)
+        cmx.rk_step(B, dt)
+        t_phys += dt
+        if n % every == 0 or n == steps:
+            l1, li = field_errors(A, B, p)
+            hist.append({"step": n, "l1_max": max(l1.values()), "linf_max": max(li.values())})
+    torch.cuda.synchronize()
+    return {"steps": steps, "t_end": t_phys, "dt": "common: the FP64 path's CFL step each step",
+            "norm": "state-scaled (partial densities by rho, momenta by rho*1000 m/s, energy by E)",
+            "l1": l1, "linf": li, "history": hist}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=GRID_N,
+                    help="cells per direction of the droplet field (256 is the benchmarked configuration)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--compare-steps", type=int, default=100)
+    ap.add_argument("--compare-steps", type=int, default=100,
+                    help="steps of the FP64-vs-mixed lockstep from the initial state, before the timed steps")
+    ap.add_argument("--kernel-steps", type=int, default=3)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-recon", action="store_true")
-    ap.add_argument("--recon-steps", type=int, default=5)
+    ap.add_argument("--recon-steps", type=int, default=3)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--study", choices=sorted(STUDIES), action="append",
                     help="instead of the benchmark line: the mixed-vs-FP64 precision study of a 3D workload "
@@ -456,122 +590,129 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_2504_14063_gb300 import binding as mp
-    p = workload()
+    t0 = time.perf_counter()
+    p = workload(args.grid)
+    t_build = time.perf_counter() - t0
+    prim = torch.from_numpy(p.prim)
     ctx = mp.Context(p)
-    U = ctx.init_state(torch.from_numpy(p.prim))
-    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    ctxm = mp.Context(p, precision=mp.MIXED)
+
+    # ---- mixed vs FP64 from the initial state; the timed steps follow ------
+    U = ctx.init_state(prim)
+    Um = ctxm.init_state(prim)
+    err = lockstep_error(mp, torch, p, ctx, ctxm, U, Um, args.compare_steps)
+
+    # ---- device-timed region: FP64, then mixed ------------------------------
     for _ in range(args.warmup):
         ctx.rk_step(U)
+        ctxm.rk_step(Um)
     torch.cuda.synchronize()
     ctx.stats(reset=True)
-    ctx.profile(reset=True)
-
-    # ---- device-timed region -----------------------------------------------
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    ctx.set_profiling(True)
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        ev[k][0].record()
-        ctx.rk_step(U)
-        ev[k][1].record()
-    torch.cuda.synchronize()
-    ctx.set_profiling(False)
+    step_ms = timed_steps(torch, ctx, U, args.steps)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     status = ctx.status()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    total_s = max_over_ranks(total_s, "cuda")
-    prof = ctx.profile(reset=True)
     stats = ctx.stats(reset=True)
+    total_s = max_over_ranks(sum(step_ms) / 1e3, "cuda")
     value = whole_job_value(world, p.ncells, args.steps, total_s)
 
-    # roofline of the face-flux kernel (dominant): algorithmic FP64 flops
-    face_ms, face_n = prof["face"]
+    clocks_m = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks_m.start()
+    step_ms_m = timed_steps(torch, ctxm, Um, args.steps)
+    if world > 1:
+        dist.barrier()
+    clk_m = clocks_m.stop()
+    tm = max_over_ranks(sum(step_ms_m) / 1e3, "cuda")
+    vm = whole_job_value(world, p.ncells, args.steps, tm)
+    mstat = ctxm.status()
+
+    # ---- per-kernel times: a separate pass with the library's events -------
+    kp = kernel_pass(torch, ctx, U, args.kernel_steps)
+    kpm = kernel_pass(torch, ctxm, Um, args.kernel_steps)
+    launches_per_step = sum(n for _, n in kp.values())
+    peaks = fma_peaks(mp, torch)
+    fp64_peak = peaks["fp64"]["tflops"]
+    fp32_peak = peaks["fp32"]["tflops"]
+    hbm_peak, hbm_src = None, "MEASURED_PEAKS.json hbm_gbs (driver-measured copy)"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak = float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        hbm_peak, hbm_src = 6800.0, "recipe fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
     faces_per_launch = ctx.nfaces_total / p.dim
     fpf = flops_per_face(p.ns, p.dim, p.model.cdi, p.model.diffusion, p.model.pos_limiter)
-    achieved = fpf * faces_per_launch / (face_ms / face_n / 1e3) / 1e12
-    launches = int(sum(n for _, n in prof.values()))
 
-    # ---- mixed precision: same workload, same timing; error vs FP64 --------
-    mixed = None
-    if not args.no_mixed:
-        ctxm = mp.Context(p, precision=mp.MIXED)
-        Um = ctxm.init_state(torch.from_numpy(p.prim))
-        for _ in range(args.warmup):
-            ctxm.rk_step(Um)
-        torch.cuda.synchronize()
-        ctxm.profile(reset=True)
-        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        ctxm.set_profiling(True)
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            evm[k][0].record()
-            ctxm.rk_step(Um)
-            evm[k][1].record()
-        torch.cuda.synchronize()
-        ctxm.set_profiling(False)
-        mstat = ctxm.status()
-        mprof = ctxm.profile(reset=True)
-        tm = max_over_ranks(sum(a.elapsed_time(b) for a, b in evm) / 1e3, "cuda")
-        # accuracy: 100 steps from the initial state, FP64 path vs mixed path
-        A = ctx.init_state(torch.from_numpy(p.prim))
-        B = ctxm.init_state(torch.from_numpy(p.prim))
-        ctx.step_n(A, args.compare_steps)
-        ctxm.step_n(B, args.compare_steps)
-        l1, li = field_errors(A, B, p)
-        vm = whole_job_value(world, p.ncells, args.steps, tm)
-        mixed = {"value": vm, "unit": UNIT, "ms_per_step": 1e3 * tm / args.steps,
-                 "speedup_vs_fp64": vm / value,
-                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in mprof.items()},
-                 "error_vs_fp64": {"steps": args.compare_steps,
-                                   "norm": "state-scaled (partial densities by rho, momenta by rho*1000 m/s, "
-                                           "energy by E)", "l1": l1, "linf": li},
-                 "status": mstat}
-        del ctxm, Um, A, B
+    def alu(kernel, ms, peak, pipe):
+        ach = fpf * faces_per_launch / (ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": traffic_of(kernel), "kernel": kernel, "pipe": pipe, "flops_per_face": fpf,
+                "faces_per_launch": faces_per_launch, "avg_launch_ms": ms}
 
-    # ---- Sec. 4.1's other ENO-type interpolations: the same FP64 step ------
+    def hbm(kernel, ms, nbytes, note):
+        ach = nbytes / (ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "traffic": traffic_of(kernel), "kernel": kernel, "bytes_per_launch": nbytes,
+                "avg_launch_ms": ms, "note": note}
+
+    n_w64 = cache_fields(p)
+    upd_b = (update_bytes(p, 1) + 2 * update_bytes(p, 2)) / 3.0
+    peak_note = (f"measured: mpmc_fma_probe, FP64 FMA chains, {peaks['fp64']['blocks']} blocks x 256 threads, "
+                 f"best of 5 (SM clock {peaks['fp64']['clocks'].get('sm_mhz')} MHz)")
+    roofline = alu("k_face", kp["face"][0], fp64_peak, "FP64")
+    roofline["peak_source"] = peak_note
+    rooflines = {
+        "k_face": roofline,
+        "mx::k_face": dict(alu("mx::k_face", kpm["face"][0], fp32_peak, "FP32"),
+                           peak_source="measured: mpmc_fma_probe, FP32 FMA chains (the same algorithmic "
+                                       "operation count, executed in FP32 but for the FP64 limiter re-checks)"),
+        "k_update": hbm("k_update", kp["update"][0], upd_b,
+                        "FP64 flux differences and RK combination; bytes averaged over the three stages"),
+        "mx::k_update": hbm("mx::k_update", kpm["update"][0], upd_b, "the same body on the FP64 fluxes"),
+    }
+    rooflines["k_prim"] = hbm("k_prim", kp["prim"][0], prim_bytes(p, n_w64, 8), "FP64 p-T inversion")
+    rooflines["mx::k_prim"] = hbm("mx::k_prim", kpm["prim"][0], prim_bytes(p, n_w64, 4),
+                                  "FP64 p-T inversion, FP32 cache")
+    mixed = {"value": vm, "unit": UNIT, "ms_per_step": 1e3 * tm / args.steps, "speedup_vs_fp64": vm / value,
+             "clocks": clk_m, "kernel_ms_per_step": {k: v[0] * v[1] for k, v in kpm.items()},
+             "error_vs_fp64": err, "status": mstat}
+    del ctxm, Um
+    torch.cuda.empty_cache()
+
+    # ---- Sec. 4.1's other ENO-type interpolations and the viscous terms ----
     recon = None
     if not args.no_recon:
-        recon = {"note": "the FP64 SSP-RK3 step of the same workload with each other interpolation "
-                         "(WENO5-JS, TENO5, TENO6) and with viscous stress and heat conduction on, "
-                         "same timing (CUDA events per step, L2 flushed between steps)"}
+        import dataclasses
         from paper_2504_14063_gb300 import workloads as W
+        recon = {"note": "the FP64 SSP-RK3 step of the same workload from the same developed state with each "
+                         "other interpolation (WENO5-JS, TENO5, TENO6) and with viscous stress and heat "
+                         "conduction on, CUDA events per step after one warm-up step"}
         variants = (("WENO5JS", dict(recon=W.RECON_WENO5JS)), ("TENO5", dict(recon=W.RECON_TENO5)),
                     ("TENO6", dict(recon=W.RECON_TENO6)), ("viscous", dict(viscous=1)))
         for rname, fields in variants:
-            pr_ = workload()
-            for f_, v_ in fields.items():
-                setattr(pr_.model, f_, v_)
+            pr_ = dataclasses.replace(p, model=dataclasses.replace(p.model, **fields))
             ctxr = mp.Context(pr_)
-            Ur = ctxr.init_state(torch.from_numpy(pr_.prim))
-            for _ in range(args.warmup):
-                ctxr.rk_step(Ur)
+            Ur = U.clone()
+            ctxr.rk_step(Ur)
             torch.cuda.synchronize()
-            evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                   for _ in range(args.recon_steps)]
-            ctxr.set_profiling(True)
-            for k in range(args.recon_steps):
-                flush.fill_(k & 0xFF)
-                evr[k][0].record()
-                ctxr.rk_step(Ur)
-                evr[k][1].record()
-            torch.cuda.synchronize()
-            ctxr.set_profiling(False)
-            rprof = ctxr.profile(reset=True)
-            tr = max_over_ranks(sum(a.elapsed_time(b) for a, b in evr) / 1e3, "cuda")
+            ms_r = timed_steps(torch, ctxr, Ur, args.recon_steps)
+            kr = kernel_pass(torch, ctxr, Ur, 1)
+            tr = max_over_ranks(sum(ms_r) / 1e3, "cuda")
             vr = whole_job_value(world, pr_.ncells, args.recon_steps, tr)
             recon[rname] = {"value": vr, "unit": UNIT, "ms_per_step": 1e3 * tr / args.recon_steps,
                             "vs_base_step": vr / value, "steps": args.recon_steps,
-                            "face_ms_per_step": rprof["face"][0] / args.recon_steps, "status": ctxr.status()}
+                            "face_ms_per_step": kr["face"][0] * kr["face"][1], "status": ctxr.status()}
             del ctxr, Ur
+            torch.cuda.empty_cache()
 
     adjoint = None
     if not args.no_adjoint and rank == 0:
@@ -593,31 +734,33 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(p, {"parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"}),
+            "config": config_of(p),
+            "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU",
+            "timed_window": f"steps {args.compare_steps + args.warmup + 1}-"
+                            f"{args.compare_steps + args.warmup + args.steps} of the field (after the "
+                            f"{args.compare_steps}-step FP64-vs-mixed comparison and {args.warmup} warm-up steps)",
             "clocks": clk,
             "e2e": {"value": whole_job_value(world, p.ncells, args.steps, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "rhs_cell_evaluations_per_s": 3 * value,
-            "gpu_launches": launches,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL / 1e12,
-                         "unit": "TFLOP/s", "frac": achieved * 1e12 / FP64_PEAK_NOMINAL, "traffic": k_face_traffic(),
-                         "traffic_unit": "bytes per launch (ncu dram read + write)",
-                         "kernel": "k_face (FP64 face flux)", "flops_per_face": fpf,
-                         "faces_per_launch": faces_per_launch, "avg_launch_ms": face_ms / face_n,
-                         "peak_source": "nominal GB300 FP64 rate (recipe table); FP64 pipe, not HBM, binds"},
-            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "roofline": roofline,
+            "rooflines": rooflines,
+            "peaks": {"fp64_fma": peaks["fp64"], "fp32_fma": peaks["fp32"], "hbm_gbs": hbm_peak,
+                      "hbm_source": hbm_src, "fp64_nominal_tflops": FP64_PEAK_NOMINAL / 1e12},
+            "kernel_ms_per_step": {k: v[0] * v[1] for k, v in kp.items()},
             "limiter_activity": {k: stats[k] / max(stats["faces"], 1) for k in
                                  ("hllc_fallback", "cdi_dropped", "theta_p", "theta_t", "ylim", "diff_dropped")},
+            "mixed": mixed,
             "status": status,
+            "workload_build_s": t_build,
         }
-        if mixed is not None:
-            line["mixed"] = mixed
         if recon is not None:
             line["variants"] = recon
         if adjoint is not None:
             line["adjoint"] = adjoint
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+            line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds, min(CPU_SLAB_PLANES, p.n[2]))
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

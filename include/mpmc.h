@@ -279,7 +279,13 @@ int mpmc_get_profile(mpmc_ctx* ctx, double* ms, uint64_t* launches, int reset);
  *     MPMC_INVALID_ARG before any GPU work; *scratch_bytes (nullable) receives
  *     the bytes the grid needs.
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress) and keeps it for the process; make that first
+ *     call before any stream capture.  A device reset (cudaDeviceReset)
+ *     invalidates the kept address: do not call this entry on a device
+ *     after resetting it in the same process.
+ *   - If an error from earlier work is pending on the calling thread
+ *     (cudaPeekAtLastError), the call returns MPMC_CUDA_ERROR before any
+ *     work and leaves that error in place for its owner.
  *   - Every call uses the same array and leaves its contents behind; calls
  *     whose work overlaps on the GPU (different streams without ordering)
  *     race.  Serialize them on one stream.
@@ -289,6 +295,17 @@ int mpmc_get_profile(mpmc_ctx* ctx, double* ms, uint64_t* launches, int reset);
 #define MPMC_NOALLOC_SCRATCH_BYTES (32u << 20)
 int mpmc_rhs_noalloc(const mpmc_grid* grid, const mpmc_eos* eos, const mpmc_model* model, void* stream,
                      const double* U, double* dUdt, const mpmc_stage* stage, size_t* scratch_bytes);
+
+/* Arithmetic-rate probe (a measurement utility; the paper has no counterpart):
+ * one launch of `blocks` x 256 threads, each running eight independent
+ * fused-multiply-add chains for `iters` rounds in FP64 (fp64 != 0) or FP32,
+ * i.e. 16 x iters x blocks x 256 floating-point operations, on `stream`
+ * (cudaStream_t or NULL).  Timed by the caller, it gives the measured peak
+ * of the pipe that bounds the face-flux kernels.  out: device array of at
+ * least blocks x 256 elements of that precision (each thread writes the sum
+ * of its chains); MPMC_INVALID_ARG if it is smaller or an argument is not
+ * positive. */
+int mpmc_fma_probe(int fp64, int blocks, int iters, void* out, size_t out_elems, void* stream);
 
 /* Text of the last error on this context (static storage of the context). */
 const char* mpmc_last_error(const mpmc_ctx* ctx);

@@ -87,6 +87,7 @@ def _load():
         "mpmc_last_error": (ctypes.c_char_p, [vp]),
         "mpmc_set_profiling": (i, [vp, i]),
         "mpmc_get_profile": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64), i]),
+        "mpmc_fma_probe": (i, [i, i, i, vp, ctypes.c_size_t, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -110,6 +111,18 @@ def _ptr(t):
 def _dev(t):
     assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
     return t.data_ptr()
+
+
+def fma_probe(fp64, blocks, iters, out, stream=None):
+    """One launch of mpmc_fma_probe on `stream` (torch's current stream if
+    None); out: CUDA tensor of >= blocks x 256 elements of that precision.
+    Returns the launch's floating-point operation count."""
+    assert out.is_cuda and out.is_contiguous() and out.dtype == (torch.float64 if fp64 else torch.float32)
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    rc = lib.mpmc_fma_probe(1 if fp64 else 0, int(blocks), int(iters), out.data_ptr(), out.numel(), s)
+    if rc != OK:
+        raise MpmcError(rc, "fma_probe")
+    return 16 * int(iters) * int(blocks) * 256
 
 
 def structs_from_problem(problem, precision=FP64):

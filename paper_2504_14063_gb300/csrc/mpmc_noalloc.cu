@@ -33,7 +33,8 @@ constexpr int kMaxDevices = 64;
 std::mutex g_lock;
 void* g_addr[kMaxDevices] = {nullptr};
 
-// device address of g_scratch on the current device (looked up once per device)
+// device address of g_scratch on the current device, looked up once per
+// device and cached: it is not valid after cudaDeviceReset of that device
 int scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MPMC_CUDA_ERROR;
@@ -90,6 +91,9 @@ extern "C" int mpmc_rhs_noalloc(const mpmc_grid* grid, const mpmc_eos* eos, cons
   if (scratch_bytes) *scratch_bytes = need;
   if (need > kScratchBytes) return MPMC_INVALID_ARG;
   if (!U || !dUdt) return MPMC_INVALID_ARG;
+  // an error left pending by earlier work of the caller is reported as it
+  // is and not cleared: the final check below then only sees this call's
+  if (cudaPeekAtLastError() != cudaSuccess) return MPMC_CUDA_ERROR;
   const Ops ops = P.dim == 1 ? ops_fp64_d1(P.ns) : (P.dim == 2 ? ops_fp64_d2(P.ns) : ops_fp64_d3(P.ns));
   if (!ops.face) return MPMC_INVALID_ARG;
   void* base = nullptr;
@@ -108,7 +112,10 @@ extern "C" int mpmc_rhs_noalloc(const mpmc_grid* grid, const mpmc_eos* eos, cons
 
   cudaStream_t s = (cudaStream_t)stream;
   // the array keeps the previous call's contents: clear what starts at zero
-  cudaMemsetAsync(b, 0, kHeader, s);
+  if (cudaMemsetAsync(b, 0, kHeader, s) != cudaSuccess) {
+    cudaGetLastError();
+    return MPMC_CUDA_ERROR;
+  }
   if (P.has_inflow) {
     Inflow in;
     memset(&in, 0, sizeof(in));

@@ -53,3 +53,26 @@ def test_flops_per_face_of_the_benchmark_workload():
     extra_test = 2 * (3 * nv) + 2 * (4 * 3 + 2 * 2 + 6)
     assert bench.flops_per_face(3, 2, 1, 1) == 1592 + extra_flux + extra_test
     assert bench.flops_per_face(3, 2, 1, 1, pos_limiter=False) < bench.flops_per_face(3, 2, 1, 1)
+
+
+def test_update_and_cache_bytes_of_the_droplet_field():
+    """The byte counts behind the HBM rooflines: the 256^3 droplet field keeps
+    27 FP64 cache fields per cell (T, P, rho, a, 4 Y, 3 u; CDI 2 + 4 + 2;
+    diffusion 8); the update moves U^n (+ U^(k) after the first stage),
+    every face flux once and U^(k+1)."""
+    p = W.droplet_field_3d(n=16)
+    assert bench.cache_fields(p) == 27
+    N, nv = 16 ** 3, 8
+    faces = 3 * 17 * 16 * 16
+    assert bench.update_bytes(p, 1) == 8 * nv * (2 * N + faces)
+    assert bench.update_bytes(p, 2) == 8 * nv * (3 * N + faces)
+    assert bench.prim_bytes(p, 27, 4) == N * (8 * nv + 4 * 27)
+
+
+def test_slab_sample_keeps_the_field_and_zero_gradient_z():
+    p = W.droplet_field_3d(n=16)
+    q = bench.slab_of(p, 4)
+    assert q.n == (16, 16, 4) and q.dx == p.dx and q.ns == p.ns
+    assert q.bc_lo[2] == W.BC_ZEROGRAD and q.bc_hi[2] == W.BC_ZEROGRAD
+    assert q.bc_lo[:2] == p.bc_lo[:2]
+    assert (q.prim == p.prim[:, :4]).all()

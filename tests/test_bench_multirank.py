@@ -93,7 +93,7 @@ def test_reference_arm_rank0_line_at_two_ranks():
     """Rank 0 of a two-rank reference run prints the one JSON line with the
     world size in n_gpus and the reference's own e2e block."""
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--gpus", str(WORLD), "--steps", "1", "--warmup", "3"],
+                        "--gpus", str(WORLD), "--steps", "1", "--warmup", "3", "--grid", "32"],
                        env=_bench_env(0), capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
@@ -104,3 +104,6 @@ def test_reference_arm_rank0_line_at_two_ranks():
                            "d2h_bytes_per_step": 0}
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["higher_is_better"] is True and line["scaling"] == "weak"
+    # the same workload description as the GPU arm's line, key for key
+    assert line["config"] == bench.config_of(bench.workload(32))
+    assert "slab" in line["cpu_baseline"]["sample"]

@@ -8,16 +8,21 @@ on sub-boxes cut out of it: the right-hand side at a cell depends only on
 cells within four along each axis (three for the WENO5-Z stencils, one more
 for the tangential psi neighbours of the interface normal), so the oracle on
 a box with a four-cell rim reproduces the box's interior whatever boundary
-it uses.  Bound per field as in test_gpu_parity: 1e-12 of the oracle's L1 +
-1e-15 of the gross flux + 10 x the oracle's own one-ulp conditioning; cells
-next to a face whose discrete decision differs (a tie) are left out.  The
-mixed path's step is compared with the FP64 step over the whole domain."""
+it uses.  Bound element by element as in test_gpu_parity: per cell and
+field, 1e-12 of |L_oracle| + 1e-15 of the cell's gross flux and of the
+rounding scale of its face fluxes at the signal speed, with the per-field
+L1 form (1e-12 of the oracle's L1 + 1e-15 of the gross flux + 10 x the
+oracle's own one-ulp conditioning) beside it; cells next to a face whose discrete decision differs (a tie) are
+left out.  The mixed path's step is compared with the FP64 step over the
+whole domain."""
 import numpy as np
 import pytest
 import torch
 
 from oracle import Oracle
 from paper_2504_14063_gb300 import workloads as W
+from tests.test_gpu_parity import (DECISIVE, YLIM, _gross_cells, cellwise_parity, flux_scale_cells,
+                                   jitter_sensitivity)
 
 pytestmark = pytest.mark.gpu
 RIM, HALF = 4, 8                     # 16^3 interior, 24^3 box
@@ -46,18 +51,6 @@ def _sub(T, zi, yi, xi):
     return a.cpu().numpy()
 
 
-def _gross_cells(problem, F):
-    """per field and cell: sum_d (|F_low| + |F_high|) / dx"""
-    out = 0.0
-    for d, Fd in enumerate(F):
-        ax = 3 - d
-        a = np.abs(Fd)
-        lo = np.take(a, range(0, a.shape[ax] - 1), axis=ax)
-        hi = np.take(a, range(1, a.shape[ax]), axis=ax)
-        out = out + (lo + hi) / problem.dx
-    return out
-
-
 def _box_parity(mp, p, ctx, U, L, flags, centers, dt, G):
     periodic = [p.bc_lo[d] == W.BC_PERIODIC for d in range(3)]
     sub = W.Problem("box", 3, (2 * (HALF + RIM),) * 3, p.dx, p.species, p.model,
@@ -72,12 +65,12 @@ def _box_parity(mp, p, ctx, U, L, flags, centers, dt, G):
         zi = _box_index(c[2], p.n[2], periodic[2])
         Ub = _sub(U, zi, yi, xi)
         Lg = _sub(L, zi, yi, xi)[inner]
-        _, Lo, flo, st = o.stage(Ub, Ub, (1.0, 0.0, 1.0), dt, G, flags=True)
+        _, Lfull, flo, st = o.stage(Ub, Ub, (1.0, 0.0, 1.0), dt, G, flags=True)
         assert st == 0
-        Lo = Lo[inner]
+        Lo = Lfull[inner]
         # decisions on the faces of the interior cells, GPU vs oracle
         bad = np.zeros(Lo.shape[1:], dtype=bool)
-        off, nties = 0, 0
+        off, nties, nylim = 0, 0, 0
         for d in range(3):
             nb = [2 * (HALF + RIM)] * 3
             nb[d] += 1
@@ -92,27 +85,34 @@ def _box_parity(mp, p, ctx, U, L, flags, centers, dt, G):
             fidx[d] = np.arange(st_d, st_d + nb[d])
             fidx[d] = fidx[d] % p.n[d] if periodic[d] else fidx[d]
             fg = flags[d][np.ix_(fidx[2], fidx[1], fidx[0])]
-            diff = ((fg ^ fo) & 0x13F) != 0
+            diff = ((fg ^ fo) & DECISIVE) != 0
+            ydiff = ((fg ^ fo) & YLIM) != 0
             # faces touching interior cells: box faces RIM .. RIM + 2 HALF along d
             sl = [slice(RIM, RIM + 2 * HALF)] * 3
             for s in (0, 1):
                 sl_d = list(sl)
                 sl_d[2 - d] = slice(RIM + s, RIM + s + 2 * HALF)
                 bad |= diff[tuple(sl_d)]
-            nties += int(diff.sum())
+            sl_f = list(sl)
+            sl_f[2 - d] = slice(RIM, RIM + 2 * HALF + 1)
+            nties += int(diff[tuple(sl_f)].sum())
+            nylim += int(ydiff[tuple(sl_f)].sum())
         keep = ~bad
         F, _ = o.face_fluxes(Ub, Ub, (1.0, 0.0, 1.0), dt, G)
         Gv = np.array([g[tuple(s for s in inner[1:])][keep].sum() for g in _gross_cells(sub, F)])
-        rng = np.random.default_rng(1)
-        Uj = Ub * (1.0 + 2e-16 * rng.standard_normal(Ub.shape))
-        Lt = o.stage(Uj, Uj, (1.0, 0.0, 1.0), dt, G)[1][inner]
-        Tv = np.array([np.abs(Lt[v] - Lo[v])[keep].sum() for v in range(p.nvars)])
+        Tc = jitter_sensitivity(o, (Ub, Ub, (1.0, 0.0, 1.0), dt, G), Lfull)[inner]
+        Tv = np.array([Tc[v][keep].sum() for v in range(p.nvars)])
         num = np.array([np.abs(Lg[v] - Lo[v])[keep].sum() for v in range(p.nvars)])
         ref = np.array([np.abs(Lo[v])[keep].sum() for v in range(p.nvars)])
         bound = 1e-12 * ref + 1e-15 * Gv + 10.0 * Tv
         print(f"{p.name} {p.n} box at {tuple(c)}: rel err {np.array2string(num / ref, precision=2)}, "
-              f"err/bound {np.array2string(num / bound, precision=2)}, ties {nties}")
+              f"err/bound {np.array2string(num / bound, precision=2)}, ties {nties}, "
+              f"Y-limiter bits differing {nylim}")
+        gc = _gross_cells(sub, F)[inner]
+        sc = flux_scale_cells(o, sub, Ub)[inner]
+        cellwise_parity(Lg, Lo, gc, sc, keep, f"{p.name} {p.n} box at {tuple(c)} element-wise")
         assert nties <= 8
+        assert nylim <= 0.01 * 3 * Lo[0].size
         assert np.all(num <= bound), (num, bound)
         worst = np.maximum(worst, num / ref)
     return worst

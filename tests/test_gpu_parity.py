@@ -1,16 +1,25 @@
 """GPU FP64 path against the CPU oracle, through the C ABI.
 
 Tolerances (the targets of this build):
-  * per right-hand-side evaluation, for every conserved field v,
+  * per right-hand-side evaluation, element by element: for every conserved
+    field v and cell c
+        |L_gpu - L_oracle| <= 1e-12 |L_oracle| + 1e-15 (g_c + s_c),
+    g_c = sum over directions of (|F_low| + |F_high|)/dx at that cell and
+    field, the gross flux whose difference makes up L there, and s_c =
+    (2 D / dx) S_v the rounding scale of a face flux of that cell at its
+    signal speed |u| + a: S = rho (|u| + a) for every partial density (the
+    face mass fractions are normalized to sum to one, so each carries an
+    absolute rounding error of the mixture's size: a trace species inside
+    a liquid is exact only to the liquid's mass flux), rho (|u| + a)^2 + P
+    for the momenta, (E + P)(|u| + a) for the energy (a pressure difference
+    of one rounding moves the contact speed and with it every flux; a field
+    whose fluxes are exactly zero in a quiescent region, such as the energy
+    before a shock arrives, is exact only to that scale).  1e-15 is 4.5
+    units of rounding.  The worst cell is printed with the number of cells
+    that need the s term.  The per-field L1 form is checked beside it:
         ||L_gpu - L_oracle||_1 <= 1e-12 ||L_oracle||_1 + 1e-15 G_v + 10 T_v,
-    G_v = sum over cells and directions of (|F_i+1/2| + |F_i-1/2|)/dx, the
-    gross flux whose differences make up L: 1e-15 G_v is the round-off
-    floor of a difference of fluxes (a field whose net rate is itself
-    round-off, e.g. rho v before any transverse motion, has no meaningful
-    relative error); T_v = ||L(U (1 + 2e-16 xi)) - L(U)||_1 is the oracle's
-    own change under a one-ulp perturbation of its input (xi standard
-    normal): the conditioning of the evaluation, which is large only where
-    the regularization's far-field phi_min balance nearly cancels;
+    G_v the sum of g_c over the cells, T_v the oracle's own L1 change under
+    a jitter of its input by one ulp (U (1 + 2e-16 xi), xi standard normal);
   * after 100 SSP-RK3 steps, in the state-scaled L1 norm (partial
     densities scaled by ||rho||_1, momenta by ||rho||_1 * 1000 m/s, energy
     by ||E||_1), <= 1e-10, on configurations whose 100-step map is
@@ -20,8 +29,12 @@ Tolerances (the targets of this build):
     far field at the phi_min floor), the GPU must stay within ten times the
     oracle's own divergence from its perturbed twin.
 Faces where a discrete limiter decision differs between the two (a tie at
-the admissibility boundary) are counted, logged, and the cells next to them
-are left out of the norm.
+the admissibility boundary: theta_T, theta_P, first-order fallback, dropped
+regularization or diffusive flux) are counted, logged, and the cells next to
+them are left out.  The mass-fraction limiter's bits are compared too; its
+correction is continuous, so a face where the two sides disagree on whether
+it acted (the sum of Y within rounding of one) stays in the element-wise
+check.
 """
 import os
 
@@ -99,6 +112,71 @@ def _gross(problem, F):
     return out
 
 
+def _gross_cells(problem, F):
+    """per field and cell: sum_d (|F_low| + |F_high|) / dx"""
+    out = 0.0
+    for d, Fd in enumerate(F):
+        ax = 3 - d
+        a = np.abs(Fd)
+        lo = np.take(a, range(0, a.shape[ax] - 1), axis=ax)
+        hi = np.take(a, range(1, a.shape[ax]), axis=ax)
+        out = out + (lo + hi) / problem.dx
+    return out
+
+
+DECISIVE = np.uint32(0x13F)   # theta_T, theta_P, fallback, CDI drop, diffusive drop
+YLIM = np.uint32(0xC0)        # mass-fraction limiter (continuous correction)
+
+
+def jitter_sensitivity(o, stage_args, Lo, n=3):
+    """T_c: the largest |L(U (1 + 2e-16 xi)) - L(U)| per cell and field over
+    n jitters; stage_args = (U_n, U_k, rk, dt, Gamma) of the oracle stage"""
+    Un, Uk, rk, dt, G = stage_args
+    T = np.zeros_like(Lo)
+    for s in range(n):
+        rng = np.random.default_rng(1 + s)
+        jit = lambda A: A * (1.0 + 2e-16 * rng.standard_normal(A.shape))
+        Lt = o.stage(jit(Un), jit(Uk), rk, dt, G)[1]
+        T = np.maximum(T, np.abs(Lt - Lo))
+    return T
+
+
+def flux_scale_cells(o, problem, U):
+    """s_c of the module docstring, per field and cell, from the oracle's
+    primitives of U"""
+    ns, D = problem.ns, problem.dim
+    pr = o.primitives(U)
+    rho, a, P = pr["rho"], pr["a"], pr["P"]
+    umag = np.sqrt(sum((U[ns + d] / rho) ** 2 for d in range(D)))
+    lam = umag + a
+    out = np.empty_like(U)
+    out[:ns] = rho * lam
+    out[ns:ns + D] = rho * lam * lam + np.abs(P)
+    out[ns + D] = (np.abs(U[ns + D]) + np.abs(P)) * lam
+    return out * (2.0 * D / problem.dx)
+
+
+def cellwise_parity(Lg, Lo, gcell, scell, keep, label, tol=None):
+    """Element-wise bound of the module docstring; keep: cells to check
+    ([nz, ny, nx] bool).  Prints the worst cell and how many cells need the
+    flux-scale term; returns (worst ratio to the bound, worst ratio to the
+    bound without the flux-scale term)."""
+    tol = RHS_TOL if tol is None else tol
+    err = np.abs(Lg - Lo)
+    strict = tol * np.abs(Lo) + 1e-15 * gcell
+    bound = strict + 1e-15 * scell
+    k = np.broadcast_to(keep, Lo.shape)
+    ratio = np.where(k, err / np.maximum(bound, 1e-300), 0.0)
+    sratio = np.where(k, err / np.maximum(strict, 1e-300), 0.0)
+    w = np.unravel_index(int(np.argmax(ratio)), ratio.shape)
+    need = int(((err > strict) & k).sum())
+    print(f"{label}: worst cell (field, z, y, x) {tuple(int(i) for i in w)}: |dL| {err[w]:.2e}, "
+          f"|L| {abs(Lo[w]):.2e}, g {gcell[w]:.2e}, s {scell[w]:.2e}, err/bound {ratio[w]:.2e}; "
+          f"cells that need the flux-scale term {need} of {int(k.sum())}")
+    assert ratio.max() <= 1.0, (label, w, err[w], bound[w])
+    return float(ratio.max()), float(sratio.max())
+
+
 def scaled_l1(a, b, ns, D):
     """state-scaled L1 error of a against b (see module docstring)"""
     rho = np.abs(b[:ns].sum(0)).sum()
@@ -132,20 +210,17 @@ def rhs_parity(mp, problem, pre_steps=2, rk=(0.75, 0.25, 0.25), report=None, dt_
     assert dtg[0] == pytest.approx(dt_cfl, rel=1e-13)
     assert dtg[1] == pytest.approx(G, rel=1e-13, abs=1e-300)
     flg = flg.cpu().numpy().view(np.uint32)
-    # the mass-fraction limiter bits are informational (its correction is
-    # continuous); ties are counted on the discrete decisions only
-    decisive = np.uint32(0x13F)
-    diff = _split_flags(problem, (flg & decisive) != (flo & decisive))
+    diff = _split_flags(problem, (flg & DECISIVE) != (flo & DECISIVE))
     nties = int(sum(d.sum() for d in diff))
+    ylim_diff = int(((flg & YLIM) != (flo & YLIM)).sum())
     mask = _face_mask_to_cells(problem, diff) if nties else None
     Lgh = Lg.cpu().numpy()
     F, _ = o.face_fluxes(Un, Uk, rk, dt, G)
     G_v = _gross(problem, F)
-    rng = np.random.default_rng(1)
-    jit = lambda A: A * (1.0 + 2e-16 * rng.standard_normal(A.shape))
-    _, Lt, _, _ = o.stage(jit(Un), jit(Uk), rk, dt, G)
+    gcell = _gross_cells(problem, F)
+    Tcell = jitter_sensitivity(o, (Un, Uk, rk, dt, G), Lo)
     keep = ~mask if mask is not None else np.ones(Lo.shape[1:], dtype=bool)
-    T_v = np.array([np.abs(Lt[v] - Lo[v])[keep].sum() for v in range(Lo.shape[0])])
+    T_v = np.array([Tcell[v][keep].sum() for v in range(Lo.shape[0])])
     num = np.array([np.abs(Lgh[v] - Lo[v])[keep].sum() for v in range(Lo.shape[0])])
     ref = np.array([np.abs(Lo[v])[keep].sum() for v in range(Lo.shape[0])])
     bound = RHS_TOL * ref + 1e-15 * G_v + 10.0 * T_v
@@ -156,8 +231,11 @@ def rhs_parity(mp, problem, pre_steps=2, rk=(0.75, 0.25, 0.25), report=None, dt_
                       diff_dropped_gpu=int(((flg & 256) != 0).sum()))
     print(f"{problem.name} {problem.n}: rhs rel err {np.array2string(err, precision=2)}, err/bound "
           f"{np.array2string(num / bound, precision=2)}, limiter-active faces {int((flo != 0).sum())}, "
-          f"flag ties {nties}")
+          f"flag ties {nties}, Y-limiter bits differing on {ylim_diff} faces")
+    cellwise_parity(Lgh, Lo, gcell, flux_scale_cells(o, problem, Uk), keep,
+                    f"{problem.name} {problem.n} element-wise")
     assert nties <= max(2, 1e-3 * flo.size)
+    assert ylim_diff <= max(2, 1e-2 * flo.size)
     assert np.all(num <= bound), (num, bound)
     return err
 
@@ -216,6 +294,8 @@ def test_rhs_forward_euler_default_stage(mp):
     Lg = ctx.rhs(_cuda(U)).cpu().numpy()
     num = np.abs(Lg - Lo).sum(axis=(1, 2, 3))
     assert np.all(num <= RHS_TOL * np.abs(Lo).sum(axis=(1, 2, 3)) + 1e-15 * _gross(p, F))
+    cellwise_parity(Lg, Lo, _gross_cells(p, F), flux_scale_cells(o, p, U), np.ones(Lo.shape[1:], dtype=bool),
+                    "forward-Euler default stage element-wise")
 
 
 def _twin(o, U0, n):
