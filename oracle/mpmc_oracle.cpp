@@ -868,6 +868,52 @@ struct Solver {
             Up[(size_t)v * G.npad + G.pad(i, j, k)] = U[(size_t)v * G.ncell + G.cell(i, j, k)];
   }
 
+  /* ghost state of a characteristic boundary (Sec. 3.5: the non-reflecting
+   * inflow / outflow conditions of Thompson and of Poinsot & Lele).  The paper
+   * gives no formulation; reading: their locally one-dimensional inviscid
+   * form, realized through the ghost state with the characteristic
+   * decomposition of Appendix A at the boundary cell: the acoustic
+   * invariants P +- rho a u_n (speeds u_n +- a) and, with speed u_n, the
+   * entropy variable T - X P, the mass fractions and the tangential
+   * velocity.  A field that leaves the domain (its speed along the outward
+   * normal > 0; >= 0 for speed u_n) keeps the boundary cell's value, one
+   * that enters takes the far-field state's (the inflow state), so that no
+   * wave is reflected by the boundary in the linear limit and the incoming
+   * waves carry the far field in.  A ghost that is not admissible (T <= 0,
+   * or P + Pinf_k <= 0 for a species present) is replaced by the boundary
+   * cell.  side 0: low boundary of direction d, 1: high. */
+  void char_ghost(int d, int side, const R* Ub, R* Ug) const {
+    Cell<R> cb, ct;
+    cell_from_conserved(p, D, Ub, cb);
+    cell_from_conserved(p, D, Uin, ct);
+    R rho, a, al, be, X, c;
+    char_scalars(p, D, Ub, rho, a, al, be, X, c);
+    const double out = side == 0 ? -1.0 : 1.0;
+    const R un = cb.u[d];
+    const bool out_p = val(out * (un + a)) > 0.0;
+    const bool out_m = val(out * (un - a)) > 0.0;
+    const bool out_0 = val(out * un) >= 0.0;
+    const R wp = out_p ? cb.P + c * un : ct.P + c * ct.u[d];
+    const R wm = out_m ? cb.P - c * un : ct.P - c * ct.u[d];
+    const R Pg = 0.5 * (wp + wm);
+    const R w1 = out_0 ? cb.T - X * cb.P : ct.T - X * ct.P;
+    const R Tg = w1 + X * Pg;
+    R Yg[MAXS], ug[3];
+    for (int k = 0; k < ns; ++k) Yg[k] = out_0 ? cb.Y[k] : ct.Y[k];
+    for (int t = 0; t < 3; ++t) ug[t] = out_0 ? cb.u[t] : ct.u[t];
+    ug[d] = (wp - wm) / (2.0 * c);
+    bool ok = val(Tg) > 0.0;
+    for (int k = 0; k < ns; ++k)
+      if (val(Yg[k]) > 0.0 && !(val(Pg + p.pinf[k]) > 0.0)) ok = false;
+    if (!ok) {
+      for (int v = 0; v < nv; ++v) Ug[v] = Ub[v];
+      return;
+    }
+    State<R> s;
+    state_from_primitive(p, D, Yg, ug, Pg, Tg, s);
+    conserved_of(ns, D, s, Ug);
+  }
+
   /* ghost layers, one direction after the other (x, y, z) over the full
    * padded extent of the other directions */
   void fill_ghosts(vector<R>& Up) const {
@@ -900,6 +946,15 @@ struct Solver {
                 size_t dst = G.pad(ig[0], ig[1], ig[2]);
                 if (bc == ORC_BC_INFLOW) {
                   for (int v = 0; v < nv; ++v) Up[(size_t)v * G.npad + dst] = Uin[v];
+                } else if (bc == ORC_BC_CHAR) {
+                  /* every ghost layer takes the ghost state of the boundary
+                   * cell of its row (rows outside the other directions'
+                   * ranges are overwritten when those directions are filled) */
+                  is[d] = side == 0 ? 0 : n - 1;
+                  R Ub[MAXV], Ug[MAXV];
+                  cell_U(Up, G.pad(is[0], is[1], is[2]), Ub);
+                  char_ghost(d, side, Ub, Ug);
+                  for (int v = 0; v < nv; ++v) Up[(size_t)v * G.npad + dst] = Ug[v];
                 } else {
                   size_t s = G.pad(is[0], is[1], is[2]);
                   for (int v = 0; v < nv; ++v) Up[(size_t)v * G.npad + dst] = Up[(size_t)v * G.npad + s];
@@ -1441,8 +1496,12 @@ using namespace orc;
 
 static int check(const orc_params* p) {
   if (!p || p->dim < 1 || p->dim > 3 || p->ns < 1 || p->ns > ORC_MAXS || !(p->dx > 0)) return ORC_INVALID;
-  for (int d = 0; d < p->dim; ++d)
+  for (int d = 0; d < p->dim; ++d) {
     if (p->n[d] < 1) return ORC_INVALID;
+    /* characteristic boundaries along x only (their ghost rows are then
+     * never corners of two such boundaries) */
+    if (d > 0 && (p->bc_lo[d] == ORC_BC_CHAR || p->bc_hi[d] == ORC_BC_CHAR)) return ORC_INVALID;
+  }
 #ifdef _OPENMP
   if (p->nthreads > 0) omp_set_num_threads(p->nthreads);
 #endif

@@ -31,6 +31,8 @@ extern "C" {
 #define ORC_BC_WALL 1      /* reflecting slip wall: mirror, normal velocity negated */
 #define ORC_BC_ZEROGRAD 2  /* copy of the boundary cell */
 #define ORC_BC_INFLOW 3    /* Dirichlet: fixed primitive state `inflow` */
+#define ORC_BC_CHAR 4      /* characteristic non-reflecting inflow/outflow towards the far-field
+                              state `inflow` (Sec. 3.5); direction 0 only */
 
 /* per-face flag bits written by orc_stage (same meaning as the GPU tape bits,
  * defined independently there) */

@@ -1,9 +1,12 @@
 """ctypes front end of the CPU oracle (test infrastructure only).
 
 `build()` compiles mpmc_oracle.cpp with the host C++ compiler (plain FP64,
-no FMA contraction so that x86 and Arm hosts agree bit for bit).  `Oracle`
-wraps one problem (grid, species, model) and exposes init_state, stage,
-rk_step, run and the point functions used by the pins.
+no FMA contraction so that x86 and Arm hosts agree bit for bit), and a
+rounding twin of the same source with fused multiply-add contraction whose
+results differ from the plain build's only by rounding: the parity tests
+read their differences as the method's own rounding noise.  `Oracle` wraps
+one problem (grid, species, model) and exposes init_state, stage, rk_step,
+run and the point functions used by the pins.
 """
 from __future__ import annotations
 
@@ -22,34 +25,57 @@ MAXS = 8
 
 _lock = threading.Lock()
 _lib = None
+_lib_fma = None
 
 
-def lib_path():
-    return os.path.join(HERE, "liboracle.so")
+def lib_path(fma=False):
+    return os.path.join(HERE, "liboracle_fma.so" if fma else "liboracle.so")
+
+
+def _fma_flags():
+    # fused multiply-adds wherever the compiler contracts (x86-64 needs the
+    # FMA instructions named; AArch64 has them in its base set)
+    import platform
+    return ["-ffp-contract=fast"] + (["-mfma"] if platform.machine() in ("x86_64", "AMD64") else [])
 
 
 def build(force=False, verbose=False):
-    """Compile the oracle shared library if it is missing or stale."""
-    out = lib_path()
+    """Compile the oracle shared library if it is missing or stale, and its
+    rounding twin: the same source with fused multiply-add contraction
+    (liboracle_fma.so), whose differences from the plain build measure the
+    method's own rounding noise in the parity tests."""
     newest = max(os.path.getmtime(f) for f in SRC + HDR)
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
-        return out
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-           "-o", out + ".tmp"] + SRC
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
-    os.replace(out + ".tmp", out)
-    return out
+    jobs = []
+    for fma in (False, True):
+        out = lib_path(fma)
+        if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
+            jobs.append((out, fma))
+    procs = []
+    for out, fma in jobs:
+        flags = _fma_flags() if fma else ["-ffp-contract=off"]
+        cmd = ["g++", "-O2", "-std=c++17"] + flags + ["-fopenmp", "-fPIC", "-shared", "-o", out + ".tmp"] + SRC
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append((out, subprocess.Popen(cmd)))
+    for out, p in procs:
+        if p.wait() != 0:
+            raise RuntimeError("oracle build failed: " + out)
+        os.replace(out + ".tmp", out)
+    return lib_path(False)
 
 
-def _load():
-    global _lib
+def _load(fma=False):
+    global _lib, _lib_fma
     with _lock:
-        if _lib is None:
-            _lib = ctypes.CDLL(build())
-            _declare(_lib)
-    return _lib
+        if (_lib_fma if fma else _lib) is None:
+            build()
+            L = ctypes.CDLL(lib_path(fma))
+            _declare(L)
+            if fma:
+                _lib_fma = L
+            else:
+                _lib = L
+    return _lib_fma if fma else _lib
 
 
 class OrcParams(ctypes.Structure):
@@ -128,8 +154,10 @@ class Oracle:
     """One problem on the CPU oracle.  Arrays are numpy float64 SoA
     [var, nz, ny, nx] of interior cells."""
 
-    def __init__(self, problem, nthreads=0, recon_basis=0, eos_iterative=0, **model_overrides):
-        self.lib = _load()
+    def __init__(self, problem, nthreads=0, recon_basis=0, eos_iterative=0, fma=False, **model_overrides):
+        """fma: the rounding twin (same source, fused multiply-adds), for
+        estimating rounding noise only"""
+        self.lib = _load(fma)
         self.problem = problem
         p = OrcParams()
         pr = problem

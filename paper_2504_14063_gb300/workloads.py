@@ -28,7 +28,7 @@ import numpy as np
 
 R_UNIVERSAL = 8.314462618
 
-BC_PERIODIC, BC_WALL, BC_ZEROGRAD, BC_INFLOW = 0, 1, 2, 3
+BC_PERIODIC, BC_WALL, BC_ZEROGRAD, BC_INFLOW, BC_CHAR = 0, 1, 2, 3, 4
 LIQUID, GAS = 0, 1
 
 
@@ -458,6 +458,56 @@ def shock_droplet_3d(n=512, seed=4, mach=2.0, nsteps=200, cdi=1, diffusion=1, ph
                    Model(cdi=cdi, diffusion=diffusion), pr,
                    bc_lo=(BC_INFLOW, BC_PERIODIC, BC_PERIODIC), bc_hi=(BC_ZEROGRAD, BC_PERIODIC, BC_PERIODIC),
                    inflow=inflow, nsteps=nsteps)
+
+
+def acoustic_tube(n=200, amplitude=1e-3, u0=0.0, direction=1, bc_lo=BC_CHAR, bc_hi=BC_CHAR, ny=1,
+                  x0=0.5, width=0.05, he=0.0, he_far=None, P0=1e5, T0=300.0):
+    """Air (optionally with a helium mass fraction `he`) in the tube [0, 1],
+    at P0, T0 and mean velocity u0, with a Gaussian acoustic pulse of
+    relative amplitude `amplitude` centred at x0 running in `direction`
+    (+1 / -1): the textbook linear simple wave of an ideal gas, dP =
+    amplitude P0 exp(-((x - x0)/width)^2), du = direction dP/(rho0 a0),
+    isentropic dT = T0 (gamma - 1)/gamma dP/P0, with the mixture's gamma and
+    gas constant.  dim 1, or 2 with `ny` rows periodic in y.  The inflow
+    (far-field) state is the undisturbed one, with helium fraction `he_far`
+    (default `he`)."""
+    he_far = he if he_far is None else he_far
+    dx = 1.0 / n
+    x = (np.arange(n) + 0.5) * dx
+    sp = [AIR, HELIUM]
+    def mix(y_he):
+        Y = np.array([1.0 - y_he, y_he])
+        R = sum(Y[k] * (s.gamma - 1.0) * s.cv for k, s in enumerate(sp))
+        cv = sum(Y[k] * s.cv for k, s in enumerate(sp))
+        return Y, R, (R + cv) / cv
+    Y, R, g = mix(he)
+    rho0 = P0 / (R * T0)
+    a0 = math.sqrt(g * P0 / rho0)
+    dP = amplitude * P0 * np.exp(-((x - x0) / width) ** 2)
+    P = P0 + dP
+    u = u0 + direction * dP / (rho0 * a0)
+    T = T0 * (1.0 + (g - 1.0) / g * dP / P0)
+    dim = 1 if ny == 1 else 2
+    shape = (1, ny, n)
+    pr = _prim(2, dim, shape)
+    # volume fractions of an ideal-gas mixture at common P, T: the mole
+    # fractions, Y_k / W_k normalized
+    mol = np.array([Y[k] / s.W for k, s in enumerate(sp)])
+    vol = mol / mol.sum()
+    pr[0], pr[1] = vol[0], vol[1]
+    pr[2] = u[None, None, :]
+    if dim == 2:
+        pr[3] = 0.0
+    pr[2 + dim] = P[None, None, :]
+    pr[3 + dim] = T[None, None, :]
+    Yf, _, _ = mix(he_far)
+    molf = np.array([Yf[k] / s.W for k, s in enumerate(sp)])
+    volf = molf / molf.sum()
+    inflow = np.array([volf[0], volf[1], u0] + ([0.0] if dim == 2 else []) + [P0, T0])
+    p = Problem("acoustic_tube", dim, (n, ny, 1), dx, sp, Model(), pr,
+                bc_lo=(bc_lo, BC_PERIODIC, BC_PERIODIC), bc_hi=(bc_hi, BC_PERIODIC, BC_PERIODIC), inflow=inflow)
+    p.a0, p.rho0 = a0, rho0
+    return p
 
 
 def random_smooth_2d(nx=40, ny=32, seed=0, cdi=1, diffusion=1, bc=BC_PERIODIC, u0=30.0):
