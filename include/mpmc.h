@@ -60,6 +60,13 @@ extern "C" {
 #define MPMC_BC_WALL 1     /* reflecting slip wall: mirror image, normal velocity negated */
 #define MPMC_BC_ZEROGRAD 2 /* copy of the boundary cell */
 #define MPMC_BC_INFLOW 3   /* Dirichlet: the fixed primitive state mpmc_grid.inflow */
+#define MPMC_BC_CHAR 4     /* characteristic non-reflecting inflow / outflow (Sec. 3.5, the conditions
+                              of Thompson and of Poinsot & Lele in their locally one-dimensional
+                              inviscid form): per boundary cell, the characteristic fields of
+                              Appendix A that leave the domain keep the cell's values and those that
+                              enter take the far-field state mpmc_grid.inflow.  x boundaries only
+                              (MPMC_INVALID_ARG on y or z); forward paths only: the adjoint entries
+                              and mpmc_rhs_noalloc refuse it (MPMC_INVALID_ARG) */
 
 /* ENO-type interpolation of the face states (Sec. 3.1.3; Sec. 4.1 runs all
  * four).  WENO5-Z (Borges et al. 2008) is the method's; the others follow
@@ -95,7 +102,8 @@ typedef struct {
   int n[3];
   double dx;
   int bc_lo[3], bc_hi[3];
-  double inflow[MPMC_MAXS + 5]; /* primitive inflow state [alpha(ns), u(dim), P, T] */
+  double inflow[MPMC_MAXS + 5]; /* primitive inflow state [alpha(ns), u(dim), P, T]; also the
+                                   far-field state of MPMC_BC_CHAR boundaries */
 } mpmc_grid;
 
 /* Species table (Eq. NASG_EOS per species; Table NASGMaterialParamters).

@@ -134,7 +134,7 @@ struct FaceAvg {
 
 template <int NS, int D>
 __device__ __forceinline__ void face_avg_fwd(const KParams& P, const double* Uk, const double* Uin, CRef ri, CRef rj,
-                                             FaceAvg<NS, D>& f) {
+                                             FaceAvg<NS, D>& f, double p_guess) {
   constexpr int NV = NS + D + 1;
   double Ui[NV], Uj[NV];
   load_U<NS, D>(P, Uk, Uin, ri, Ui);
@@ -142,7 +142,7 @@ __device__ __forceinline__ void face_avg_fwd(const KParams& P, const double* Uk,
 #pragma unroll
   for (int v = 0; v < NV; ++v) f.Ub[v] = 0.5 * (Ui[v] + Uj[v]);
   decode<NS, D, false>(f.Ub, f.rb, f.Yb, f.ub, f.eb, f.vb);
-  pt_equilibrium<NS, false>(P, f.Yb, f.eb, f.vb, f.pb, f.Tb, f.rb);
+  pt_equilibrium<NS, false>(P, f.Yb, f.eb, f.vb, f.pb, f.Tb, f.rb, p_guess);
 #pragma unroll
   for (int k = 0; k < NS; ++k) f.tb.Y[k] = f.Yb[k];
   f.tb.p = f.pb;
@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(VJP_THREADS)
 
   // ================= forward recomputation (values only) =================
   FaceAvg<NS, D> fa;
-  face_avg_fwd<NS, D>(P, Uk, Uin, ri, rj, fa);
+  // the forward face kernel's start for the averaged state's pressure
+  face_avg_fwd<NS, D>(P, Uk, Uin, ri, rj, fa, 0.5 * (wget(P, Wc, P.wP, ri) + wget(P, Wc, P.wP, rj)));
   const double X = fa.X, c = fa.c, ic = 1.0 / c;
   // reconstruction values with their gradients w.r.t. the stencil values
   double TL, TR, PL, PR, uL[3] = {0.0, 0.0, 0.0}, uR[3] = {0.0, 0.0, 0.0};

@@ -32,7 +32,11 @@ struct mpmc_ctx {
   double* U1 = nullptr;
   double* U2 = nullptr;
   double* Ud = nullptr;   // device state of the host-buffer entry
+  // ghost buffers [nv][gstride]: column 0 the inflow (far-field) state,
+  // then the characteristic ghosts; Uin for U^n (KParams.gn), Gk for the
+  // stage states (Gk == Uin without characteristic boundaries)
   double* Uin = nullptr;
+  double* Gk = nullptr;
   double* scal = nullptr; // [dt, Gamma]
   unsigned long long* red = nullptr;
   int* status = nullptr;
@@ -143,7 +147,7 @@ static void free_all(mpmc_ctx* c) {
   // g_U and g_hist are caller-owned and never freed here
   void* ptrs[] = {c->Wc,   c->F[0],  c->F[1],    c->F[2],   c->U1,   c->U2,   c->Ud,   c->Uin,
                   c->scal, c->red,   c->status,  c->stats,  c->counter, c->gW, c->lamA, c->lamB,
-                  c->tape_int, c->Cslots, c->gU, c->unf};
+                  c->tape_int, c->Cslots, c->gU, c->unf, c->Gk != c->Uin ? c->Gk : nullptr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -225,7 +229,11 @@ extern "C" int mpmc_create(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_m
   }
   rc = rc ? rc : alloc(c, (void**)&c->U1, st_bytes);
   rc = rc ? rc : alloc(c, (void**)&c->U2, st_bytes);
-  rc = rc ? rc : alloc(c, (void**)&c->Uin, 32 * sizeof(double));
+  const size_t gbytes = (size_t)P.nv * P.gstride * sizeof(double);
+  rc = rc ? rc : alloc(c, (void**)&c->Uin, gbytes < 32 * sizeof(double) ? 32 * sizeof(double) : gbytes);
+  if (!rc && P.nslots) rc = alloc(c, (void**)&c->Gk, gbytes);
+  if (!rc && !P.nslots) c->Gk = c->Uin;
+  P.gn = c->Uin;
   rc = rc ? rc : alloc(c, (void**)&c->scal, 8 * sizeof(double));
   rc = rc ? rc : alloc(c, (void**)&c->red, 4 * sizeof(unsigned long long));
   rc = rc ? rc : alloc(c, (void**)&c->status, 4 * sizeof(int));
@@ -242,16 +250,25 @@ extern "C" int mpmc_create(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_m
   cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->stream);
   cudaMemsetAsync(c->stats, 0, 8 * sizeof(unsigned long long), c->stream);
   cudaMemsetAsync(c->scal, 0, 8 * sizeof(double), c->stream);
-  cudaMemsetAsync(c->Uin, 0, 32 * sizeof(double), c->stream);
+  cudaMemsetAsync(c->Uin, 0, gbytes < 32 * sizeof(double) ? 32 * sizeof(double) : gbytes, c->stream);
+  if (c->Gk != c->Uin) cudaMemsetAsync(c->Gk, 0, gbytes, c->stream);
   if (P.has_inflow) {
-    // inflow state: primitive -> conserved on the device (1 cell)
+    // inflow state: primitive -> conserved on the device (1 cell), then into
+    // column 0 of each ghost buffer
     double* tmp = nullptr;
-    rc = alloc(c, (void**)&tmp, 32 * sizeof(double));
+    rc = alloc(c, (void**)&tmp, 64 * sizeof(double));
     if (!rc) {
       double w[32] = {0};
       for (int v = 0; v < ns + D + 2; ++v) w[v] = g->inflow[v];
       cudaMemcpy(tmp, w, sizeof(w), cudaMemcpyHostToDevice);
-      c->ops.init(P, c->stream, tmp, c->Uin, 1);
+      c->ops.init(P, c->stream, tmp, tmp + 32, 1);
+      for (int v = 0; v < P.nv; ++v) {
+        cudaMemcpyAsync(c->Uin + (size_t)v * P.gstride, tmp + 32 + v, sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->stream);
+        if (c->Gk != c->Uin)
+          cudaMemcpyAsync(c->Gk + (size_t)v * P.gstride, tmp + 32 + v, sizeof(double), cudaMemcpyDeviceToDevice,
+                          c->stream);
+      }
       cudaStreamSynchronize(c->stream);
       cudaFree(tmp);
     }
@@ -297,9 +314,10 @@ static void stage(mpmc_ctx* c, cudaStream_t s, const double* Un, const double* U
                   double* Uout, double* dUdt, uint32_t* flags) {
   const KParams& P = c->P;
   long long off = 0;
+  const double* Gk = Uk == Un ? c->Uin : c->Gk;   // the ghost buffer of U^(k)
   for (int d = 0; d < P.dim; ++d) {
     ProfScope ps(c, FAM_FACE, s);
-    c->ops.face(P, s, d, c->Wc, Un, Uk, c->Uin, c->scal, rk0, rk1, rk2, c->F[d], flags ? flags + off : nullptr,
+    c->ops.face(P, s, d, c->Wc, Un, Uk, Gk, c->scal, rk0, rk1, rk2, c->F[d], flags ? flags + off : nullptr,
                 c->stats);
     off += c->nface[d];
   }
@@ -307,9 +325,14 @@ static void stage(mpmc_ctx* c, cudaStream_t s, const double* Un, const double* U
   c->ops.update(P, s, Un, Uk, c->F, c->scal, rk0, rk1, rk2, Uout, dUdt, c->status);
 }
 
+// primitive cache of U; the pass that computes dt and Gamma (red != null)
+// is the one of U^n, every other one of a stage state: each first fills its
+// ghost buffer's characteristic ghosts
 static void prim(mpmc_ctx* c, cudaStream_t s, const double* U, unsigned long long* red) {
   ProfScope ps(c, FAM_PRIM, s);
-  c->ops.prim(c->P, s, U, c->Uin, c->Wc, red, c->status);
+  double* G = red ? c->Uin : c->Gk;
+  if (c->P.nslots) c->ops.ghost(c->P, s, U, G);
+  c->ops.prim(c->P, s, U, G, c->Wc, red, c->status);
 }
 
 // dt and Gamma from U (prim pass with the block maxima), then k_dt
@@ -431,6 +454,7 @@ extern "C" int mpmc_dt_gamma(mpmc_ctx* c, const double* U, double* out_dev) {
 // discrete adjoint (FP64 contexts)
 static int ensure_adjoint(mpmc_ctx* c) {
   if (c->precision != MPMC_FP64) return fail(c, MPMC_INVALID_ARG, "adjoint: needs an FP64 context");
+  if (c->P.nslots) return fail(c, MPMC_INVALID_ARG, "adjoint: characteristic boundaries are not differentiated");
   const KParams& P = c->P;
   int rc = MPMC_OK;
   const size_t st_bytes = (size_t)P.nv * P.ncell * sizeof(double);
@@ -449,9 +473,10 @@ static int ensure_adjoint(mpmc_ctx* c) {
 static void faces_only(mpmc_ctx* c, cudaStream_t s, const double* Un, const double* Uk, double rk0, double rk1,
                        double rk2, uint32_t* flags) {
   long long off = 0;
+  const double* Gk = Uk == Un ? c->Uin : c->Gk;
   for (int d = 0; d < c->P.dim; ++d) {
     ProfScope ps(c, FAM_FACE, s);
-    c->ops.face(c->P, s, d, c->Wc, Un, Uk, c->Uin, c->scal, rk0, rk1, rk2, c->F[d], flags + off, nullptr);
+    c->ops.face(c->P, s, d, c->Wc, Un, Uk, Gk, c->scal, rk0, rk1, rk2, c->F[d], flags + off, nullptr);
     off += c->nface[d];
   }
 }

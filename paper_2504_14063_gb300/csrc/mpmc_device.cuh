@@ -18,7 +18,7 @@ constexpr double GTOL = 1e-8;
 // per species: |sum Y - 1| up to which the Y limiter does not renormalize
 constexpr double YSUM_TOL = 1e-15;
 
-enum { BC_PERIODIC = 0, BC_WALL = 1, BC_ZEROGRAD = 2, BC_INFLOW = 3 };
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_ZEROGRAD = 2, BC_INFLOW = 3, BC_CHAR = 4 };
 enum { ST_OK = 0, ST_INADMISSIBLE = 3, ST_EOS_NO_CONVERGE = 4 };
 enum : uint32_t {
   F_THETA_T_L = 1u << 0, F_THETA_T_R = 1u << 1, F_THETA_P_L = 1u << 2, F_THETA_P_R = 1u << 3,
@@ -45,9 +45,18 @@ struct KParams {
   int has_b, has_q;  // some species has a nonzero NASG covolume b / reference energy q
   double cdi_eps, cdi_gamma, phi_min, psi_delta, cfl, mu_liquid, sharp0;
   // primitive cache: field f of cell c at Wc[f * wstride + c]; slot ncell
-  // holds the inflow state
+  // holds the inflow state, slots ncell + 1 .. ncell + nslots the ghost
+  // states of the characteristic boundaries (one per boundary cell: the low
+  // x side first, then the high one, each ordered like the cells of an
+  // x-plane)
   int wT, wP, wRho, wA, wY, wU, wPhi0, wPsi, wYrho, wHrho, wXr, wB, wMu, wLam, nW;
   long long wstride;
+  // conserved states of those slots: ghost buffers [nv][gstride], column 0
+  // the inflow (far-field) state, column 1 + s slot s.  Kernels get the
+  // buffer of U^(k) as an argument; gn is the one of U^n.
+  int nslots, char_lo, char_hi;  // char_*: the x side is characteristic
+  long long gstride, nextra;     // nextra: cache slots beyond ncell (0, or 1 + nslots)
+  const double* gn;
   // mixed precision only: FP32 copy of U^n ([nv][wstride]) written by the
   // primitive pass that computes the step's dt and Gamma; FP32 copies of
   // U^(k) live in the FP32 cache at fields nW .. nW + nv - 1
@@ -111,6 +120,7 @@ __device__ __forceinline__ CRef map_cell(const KParams& P, int i, int j, int k) 
   int c[3] = {i, j, k};
   unsigned flip = 0u;
   bool inflow = false;
+  int chr = -1;  // a characteristic x boundary: 0 low side, 1 high side
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (d < P.dim) {
@@ -126,6 +136,12 @@ __device__ __forceinline__ CRef map_cell(const KParams& P, int i, int j, int k) 
           flip ^= 1u << d;
         } else if (bc == BC_ZEROGRAD) {
           c[d] = lo ? 0 : n - 1;
+        } else if (bc == BC_CHAR) {
+          // the ghost slot of the boundary cell of this row (x only): the
+          // other directions still map the row's coordinates (and walls
+          // mirror the ghost's velocity)
+          chr = lo ? 0 : 1;
+          c[d] = lo ? 0 : n - 1;
         } else {
           inflow = true;
           flip = 0u;
@@ -135,21 +151,29 @@ __device__ __forceinline__ CRef map_cell(const KParams& P, int i, int j, int k) 
   }
   CRef r;
   r.flip = flip;
-  r.idx = inflow ? P.ncell : ((long long)c[2] * P.n[1] + c[1]) * P.n[0] + c[0];
+  if (inflow) {
+    r.idx = P.ncell;
+  } else if (chr >= 0) {
+    const long long row = (long long)c[2] * P.n[1] + c[1];
+    r.idx = P.ncell + 1 + (chr == 1 && P.char_lo ? (long long)P.n[1] * P.n[2] : 0) + row;
+  } else {
+    r.idx = ((long long)c[2] * P.n[1] + c[1]) * P.n[0] + c[0];
+  }
   return r;
 }
 
 __device__ __forceinline__ double sgn_flip(unsigned flip, int d) { return (flip >> d) & 1u ? -1.0 : 1.0; }
 
 // conserved vector of a mapped cell (U has ncell entries per component; the
-// inflow state comes from Uin)
+// inflow state and the characteristic ghosts come from U's ghost buffer G)
 template <int NS, int D>
 __device__ __forceinline__ void load_U(const KParams& P, const double* __restrict__ U,
-                                       const double* __restrict__ Uin, CRef r, double* out) {
+                                       const double* __restrict__ G, CRef r, double* out) {
   constexpr int NV = NS + D + 1;
-  if (r.idx == P.ncell) {
+  if (r.idx >= P.ncell) {
+    const long long col = r.idx - P.ncell;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) out[v] = Uin[v];
+    for (int v = 0; v < NV; ++v) out[v] = G[(long long)v * P.gstride + col];
   } else {
 #pragma unroll
     for (int v = 0; v < NV; ++v) out[v] = U[(long long)v * P.ncell + r.idx];
@@ -174,22 +198,38 @@ __device__ __forceinline__ double h_k(const KParams& P, int k, double p, double 
   return P.cp[k] * T + P.b[k] * p + P.q[k];
 }
 
-// common-pressure residual of NASG_T1 = NASG_T2 and its derivative
-// (mag: the sum of the magnitudes of its terms, the scale of its rounding)
+// common-pressure residual of NASG_T1 = NASG_T2 and its first two
+// derivatives, f(x) = sum_k w_k / (x + Pinf_k) - Cv with w_k = Y_k R_k
+// (E' - Pinf_k) precomputed for the species present (mag: the sum of the
+// magnitudes of its terms, the scale of its rounding).  The ideal-gas
+// species share one reciprocal 1/x.
 template <int NS>
-__device__ __forceinline__ void pt_residual(const KParams& P, const double* Y, double Ep, double Cv, double x,
-                                            double& f, double& df, double& mag) {
+__device__ __forceinline__ void pt_residual(const KParams& P, const double* Y, const double* w, double Cv, double x,
+                                            double& f, double& df, double& d2f, double& mag) {
   f = -Cv;
   df = 0.0;
+  d2f = 0.0;
   mag = Cv;
+  double rg = 0.0;
+  bool have_rg = false;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     if (Y[k] != 0.0) {
-      const double w = Y[k] * P.Rk[k] * (Ep - P.pinf[k]);
-      const double r = 1.0 / (x + P.pinf[k]);
-      f += w * r;
-      df -= w * r * r;
-      mag += fabs(w * r);
+      double r;
+      if (P.pinf[k] == 0.0) {
+        if (!have_rg) {
+          rg = 1.0 / x;
+          have_rg = true;
+        }
+        r = rg;
+      } else {
+        r = 1.0 / (x + P.pinf[k]);
+      }
+      const double t = w[k] * r;
+      f += t;
+      df -= t * r;
+      d2f += 2.0 * t * r * r;
+      mag += fabs(t);
     }
   }
 }
@@ -253,7 +293,7 @@ __device__ __forceinline__ void decode(const double* U, double& rho, double* Y, 
 // Y-weighted Pinf, at most 100 iterations.
 template <int NS, bool EX = true>
 __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, double v, double& p, double& T,
-                              double rho = 0.0) {
+                              double rho = 0.0, double guess = -1e300) {
   double Cv = 0.0, q = 0.0, b = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
@@ -297,42 +337,50 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
       p = a2 >= 0.0 ? add_<EX>(a2, sq) / mul_<EX>(2.0, a1) : mul_<EX>(2.0, a3) / sub_<EX>(sq, a2);
     }
   } else {
+    // Halley steps on the residual from the caller's guess (a nearby
+    // pressure) or the quadratic with the liquids merged into one, kept
+    // inside the bracket (a, bb) of the root on (lo, inf); the upper end is
+    // found only if a step leaves the bracket while it is still open
     const double lo = -pmin;
-    double hi = fmax(fabs(Ep), 1.0) + fabs(lo);
-    double f, df, mag;
-    int it = 0;
-    pt_residual<NS>(P, Y, Ep, Cv, hi, f, df, mag);
-    while (f >= 0.0 && it < 200) {
-      hi *= 2.0;
-      pt_residual<NS>(P, Y, Ep, Cv, hi, f, df, mag);
-      ++it;
+    double w[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) w[k] = Y[k] != 0.0 ? Y[k] * P.Rk[k] * (Ep - P.pinf[k]) : 0.0;
+    double a = lo, bb = INFINITY;
+    double x;
+    if (guess > lo && guess < 1e300) {
+      x = guess;
+    } else {
+      const double pe = wpl / Rl;
+      const double a2 = Ep * (Rg + Rl) - pe * Cv - pe * Rl, a3 = Ep * pe * Rg;
+      x = gas ? (a2 >= 0.0 ? (a2 + sqrt(a2 * a2 + 4.0 * Cv * a3)) / (2.0 * Cv)
+                           : 2.0 * a3 / (sqrt(a2 * a2 + 4.0 * Cv * a3) - a2))
+              : (Ep * Rl - pe * Cv - pe * Rl) / Cv;
+      if (!(x > a)) x = lo + fmax(fabs(lo), 1.0);
     }
-    double a = lo, bb = hi;
-    // initial guess: the quadratic with the liquids merged into one
-    const double pe = wpl / Rl;
-    const double a2 = Ep * (Rg + Rl) - pe * Cv - pe * Rl, a3 = Ep * pe * Rg;
-    double x = gas ? (a2 >= 0.0 ? (a2 + sqrt(a2 * a2 + 4.0 * Cv * a3)) / (2.0 * Cv)
-                                : 2.0 * a3 / (sqrt(a2 * a2 + 4.0 * Cv * a3) - a2))
-                   : (Ep * Rl - pe * Cv - pe * Rl) / Cv;
-    if (!(x > a && x < bb)) x = 0.5 * (a + bb);
+    double f, df, d2f, mag;
     bool conv = false;
-    for (it = 0; it < 100; ++it) {
-      pt_residual<NS>(P, Y, Ep, Cv, x, f, df, mag);
+    for (int it = 0; it < 100; ++it) {
+      pt_residual<NS>(P, Y, w, Cv, x, f, df, d2f, mag);
       if (f > 0.0) a = x;
       else bb = x;
       // the residual is a difference of terms of size mag: once it is at its
       // own rounding level, x is the root as far as the data determine it
-      // (a stiff liquid with trace gas: Newton would wander in that band)
+      // (a stiff liquid with trace gas: the iterate would wander in that band)
       if (fabs(f) <= 16.0 * 2.220446049250313e-16 * mag) { conv = true; break; }
-      double xn = x - f / df;
+      const double hd = 2.0 * df * df - f * d2f;
+      double xn = hd > 0.0 ? x - 2.0 * f * df / hd : x - f / df;
       if (!(xn > a && xn < bb)) {
-        const double da = a - lo, db = bb - lo;
-        xn = (da > 0.0 && db > 16.0 * da) ? lo + sqrt(da * db) : 0.5 * (a + bb);
+        if (bb == INFINITY) {
+          xn = x + fmax(x - lo, 1.0);       // root above every point tried so far
+        } else {
+          const double da = a - lo, db = bb - lo;
+          xn = (da > 0.0 && db > 16.0 * da) ? lo + sqrt(da * db) : 0.5 * (a + bb);
+        }
       }
       const double dxn = fabs(xn - x);
       x = xn;
       if (dxn <= 4.5e-16 * fabs(x) || !(bb > a)) {
-        pt_residual<NS>(P, Y, Ep, Cv, x, f, df, mag);
+        pt_residual<NS>(P, Y, w, Cv, x, f, df, d2f, mag);
         x = x - f / df;   // one more Newton step at full accuracy
         conv = true;
         break;

@@ -48,6 +48,76 @@ __global__ void __launch_bounds__(CELL_THREADS) k_init(const KParams P, const do
 }
 
 // ---------------------------------------------------------------------------
+// ghost states of the characteristic x boundaries (the non-reflecting inflow
+// / outflow conditions Sec. 3.5 cites, in their locally one-dimensional
+// inviscid form): at each boundary cell, the characteristic decomposition of
+// Appendix A at that cell's state -- the acoustic invariants P +- rho a u_x
+// (speeds u_x +- a) and, with speed u_x, T - X P, the mass fractions and the
+// tangential velocity.  A field leaving the domain (speed along the outward
+// normal > 0, >= 0 for u_x) keeps the cell's value, an entering one takes
+// the far-field state's (G column 0, the inflow state).  A ghost that is not
+// admissible (T <= 0, or P + Pinf_k <= 0 for a species present) is the
+// boundary cell itself.  G: U's ghost buffer; slot s is written to column 1 + s.
+template <int NS, int D>
+__global__ void __launch_bounds__(CELL_THREADS)
+    k_char_ghost(const KParams P, const double* __restrict__ U, double* __restrict__ G) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= P.nslots) return;
+  constexpr int NV = NS + D + 1;
+  const long long plane = (long long)P.n[1] * P.n[2];
+  const int side = (P.char_lo && s < plane) ? 0 : 1;
+  const long long row = s - (side == 1 && P.char_lo ? plane : 0);
+  const long long cb = row * P.n[0] + (side == 0 ? 0 : P.n[0] - 1);
+  double Ub[NV], Ut[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    Ub[v] = U[(long long)v * P.ncell + cb];
+    Ut[v] = G[(long long)v * P.gstride];
+  }
+  double rho, Y[NS], u[3], e, vol, p, T;
+  decode<NS, D>(Ub, rho, Y, u, e, vol);
+  pt_equilibrium<NS>(P, Y, e, vol, p, T);
+  double r2, e2, a, al, be;
+  eos_forward<NS>(P, Y, p, T, r2, e2, a, al, be);
+  const double X = (rho * a * a * be - 1.0) / (al * a * a * rho), c = a * rho;
+  double rt, Yt[NS], ut[3], et, vt, pt, Tt;
+  decode<NS, D>(Ut, rt, Yt, ut, et, vt);
+  pt_equilibrium<NS>(P, Yt, et, vt, pt, Tt);
+  const double out = side == 0 ? -1.0 : 1.0;
+  const double un = u[0];
+  const bool out_p = out * (un + a) > 0.0, out_m = out * (un - a) > 0.0, out_0 = out * un >= 0.0;
+  const double wp = out_p ? p + c * un : pt + c * ut[0];
+  const double wm = out_m ? p - c * un : pt - c * ut[0];
+  const double Pg = 0.5 * (wp + wm);
+  const double Tg = (out_0 ? T - X * p : Tt - X * pt) + X * Pg;
+  double Yg[NS], ug[3];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) Yg[k] = out_0 ? Y[k] : Yt[k];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) ug[t] = out_0 ? u[t] : ut[t];
+  ug[0] = (wp - wm) / (2.0 * c);
+  bool ok = Tg > 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+    if (Yg[k] > 0.0 && !(Pg + P.pinf[k] > 0.0)) ok = false;
+  double Ug[NV];
+  if (ok) {
+    State<NS> st;
+    state_from_primitive<NS>(P, Yg, ug, Pg, Tg, st);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) Ug[k] = st.rhoY[k];
+#pragma unroll
+    for (int d = 0; d < D; ++d) Ug[NS + d] = st.m[d];
+    Ug[NS + D] = st.E;
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Ug[v] = Ub[v];
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) G[(long long)v * P.gstride + 1 + s] = Ug[v];
+}
+
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -85,12 +155,13 @@ __global__ void __launch_bounds__(CELL_THREADS)
            unsigned long long* __restrict__ red, int* __restrict__ status) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double smax = 0.0, gmax = 0.0;
-  if (c < P.ncell + P.has_inflow) {
+  if (c < P.ncell + P.nextra) {
     constexpr int NV = NS + D + 1;
     double Uc[NV];
-    if (c == P.ncell) {
+    if (c >= P.ncell) {
+      // the inflow state or a characteristic ghost, from U's ghost buffer
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Uc[v] = Uin[v];
+      for (int v = 0; v < NV; ++v) Uc[v] = Uin[(long long)v * P.gstride + (c - P.ncell)];
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) Uc[v] = U[(long long)v * P.ncell + c];
@@ -267,7 +338,10 @@ __global__ void __launch_bounds__(FACE_THREADS)
     double rho, Y[NS], uu[3], e, vol;
     decode<NS, D, false>(Ui, rho, Y, uu, e, vol);
     double p, T, a, al, be;
-    pt_equilibrium<NS, false>(P, Y, e, vol, p, T, rho);
+    // the Newton start of several stiffened liquids: the mean of the two
+    // cells' pressures, close to the averaged state's
+    pt_equilibrium<NS, false>(P, Y, e, vol, p, T, rho,
+                              0.5 * (wget(P, Wc, P.wP, ri) + wget(P, Wc, P.wP, rj)));
     eos_char<NS>(P, Y, p, T, rho, a, al, be);
     X = (rho * a * a * be - 1.0) / (al * a * a * rho);
     c = a * rho;
@@ -359,8 +433,8 @@ __global__ void __launch_bounds__(FACE_THREADS)
   double Uni[NV], Unj[NV], Uki[NV], Ukj[NV];
   const double lam = 2.0 * D * rk2 * dt * P.inv_dx;
   if (P.pos_limiter || P.cdi) {
-    load_U<NS, D>(P, Un, Uin, ri, Uni);
-    load_U<NS, D>(P, Un, Uin, rj, Unj);
+    load_U<NS, D>(P, Un, P.gn, ri, Uni);
+    load_U<NS, D>(P, Un, P.gn, rj, Unj);
     load_U<NS, D>(P, Uk, Uin, ri, Uki);
     load_U<NS, D>(P, Uk, Uin, rj, Ukj);
   }
@@ -661,7 +735,7 @@ struct Impl {
   }
   static void prim(const KParams& P, cudaStream_t s, const double* U, const double* Uin, double* Wc,
                    unsigned long long* red, int* status) {
-    k_prim<NS, D><<<nblocks(P.ncell + P.has_inflow, CELL_THREADS), CELL_THREADS, 0, s>>>(P, U, Uin, Wc, red,
+    k_prim<NS, D><<<nblocks(P.ncell + P.nextra, CELL_THREADS), CELL_THREADS, 0, s>>>(P, U, Uin, Wc, red,
                                                                                             status);
   }
   static void face(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* Un, const double* Uk,
@@ -675,12 +749,16 @@ struct Impl {
     k_update<NS, D><<<nblocks(P.ncell, CELL_THREADS), CELL_THREADS, 0, s>>>(
         P, Un, Uk, F[0], D > 1 ? F[1] : F[0], D > 2 ? F[2] : F[0], scal, rk0, rk1, rk2, Uout, dUdt, status);
   }
+  static void ghost(const KParams& P, cudaStream_t s, const double* U, double* G) {
+    if (P.nslots > 0) k_char_ghost<NS, D><<<nblocks(P.nslots, CELL_THREADS), CELL_THREADS, 0, s>>>(P, U, G);
+  }
   static Ops ops() {
     Ops o;
     o.init = &init;
     o.prim = &prim;
     o.face = &face;
     o.update = &update;
+    o.ghost = &ghost;
     return o;
   }
 };

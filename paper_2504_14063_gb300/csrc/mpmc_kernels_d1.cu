@@ -9,7 +9,7 @@ Ops ops_fp64_d1(int ns) {
     case 2: return Impl<2, 1>::ops();
     case 3: return Impl<3, 1>::ops();
     case 4: return Impl<4, 1>::ops();
-    default: return Ops{nullptr, nullptr, nullptr, nullptr};
+    default: return Ops{};
   }
 }
 

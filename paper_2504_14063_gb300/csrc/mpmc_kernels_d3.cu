@@ -9,7 +9,7 @@ Ops ops_fp64_d3(int ns) {
     case 2: return Impl<2, 3>::ops();
     case 3: return Impl<3, 3>::ops();
     case 4: return Impl<4, 3>::ops();
-    default: return Ops{nullptr, nullptr, nullptr, nullptr};
+    default: return Ops{};
   }
 }
 

@@ -371,12 +371,13 @@ __global__ void __launch_bounds__(CELL_THREADS)
            unsigned long long* __restrict__ red, int* __restrict__ status) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   float smax = 0.f, gmax = 0.f;
-  if (c < P.ncell + P.has_inflow) {
+  if (c < P.ncell + P.nextra) {
     constexpr int NV = NS + D + 1;
     double Uc[NV];
-    if (c == P.ncell) {
+    if (c >= P.ncell) {
+      // the inflow state or a characteristic ghost, from U's ghost buffer
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Uc[v] = Uin[v];
+      for (int v = 0; v < NV; ++v) Uc[v] = Uin[(long long)v * P.gstride + (c - P.ncell)];
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) Uc[v] = U[(long long)v * P.ncell + c];
@@ -581,12 +582,13 @@ __device__ __forceinline__ bool admissible_stream(const KParams& P, const double
                                                   const double* __restrict__ Uk, const double* __restrict__ Uin,
                                                   const CRef r, const float* Ft, const double rk0, const double rk1,
                                                   const double s) {
-  const bool inflow = r.idx == P.ncell;
+  const bool ghost = r.idx >= P.ncell;
+  const long long col = r.idx - P.ncell;
   // (a wall's mirror image negates the cell's momentum component d, as
   // load_U does, before the flux term is added)
   auto T = [&](int v) {
-    double un = inflow ? Uin[v] : Un[(long long)v * P.ncell + r.idx];
-    double uk = inflow ? Uin[v] : Uk[(long long)v * P.ncell + r.idx];
+    double un = ghost ? P.gn[(long long)v * P.gstride + col] : Un[(long long)v * P.ncell + r.idx];
+    double uk = ghost ? Uin[(long long)v * P.gstride + col] : Uk[(long long)v * P.ncell + r.idx];
     if (v >= NS && v < NS + D) {
       un *= sgn_flip(r.flip, v - NS);
       uk *= sgn_flip(r.flip, v - NS);
@@ -1076,7 +1078,7 @@ template <int NS, int D>
 struct Impl {
   static void prim(const KParams& P, cudaStream_t s, const double* U, const double* Uin, double* Wc,
                    unsigned long long* red, int* status) {
-    k_prim<NS, D><<<nblocks(P.ncell + P.has_inflow, CELL_THREADS), CELL_THREADS, 0, s>>>(
+    k_prim<NS, D><<<nblocks(P.ncell + P.nextra, CELL_THREADS), CELL_THREADS, 0, s>>>(
         P, U, Uin, reinterpret_cast<float*>(Wc), red, status);
   }
   static void face(const KParams& P, cudaStream_t s, int d, const double* Wc, const double* Un, const double* Uk,

@@ -18,7 +18,7 @@ Ops ops_mixed_d2(int ns) {
     case 2: return mixed_ops<2>();
     case 3: return mixed_ops<3>();
     case 4: return mixed_ops<4>();
-    default: return Ops{nullptr, nullptr, nullptr, nullptr};
+    default: return Ops{};
   }
 }
 

@@ -65,7 +65,9 @@ size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Kernel parameters as mpmc_create sets them up (FP64, WENO5-Z only)
 int params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_model* m, KParams& P) {
   if (m && (m->precision != MPMC_FP64 || m->recon != MPMC_RECON_WENO5Z)) return MPMC_INVALID_ARG;
-  return build_params(g, eos, m, P);
+  const int rc = build_params(g, eos, m, P);
+  // no characteristic boundaries: their ghost buffers are not laid out here
+  return rc ? rc : (P.nslots ? MPMC_INVALID_ARG : MPMC_OK);
 }
 
 }  // namespace
@@ -105,6 +107,7 @@ extern "C" int mpmc_rhs_noalloc(const mpmc_grid* grid, const mpmc_eos* eos, cons
   int* status = reinterpret_cast<int*>(b + 512);
   int* counter = reinterpret_cast<int*>(b + 768);
   double* Uin = reinterpret_cast<double*>(b + 1024);                  // 32 doubles
+  P.gn = Uin;   // the inflow state serves U^n and the stage state alike
   double* prim_in = reinterpret_cast<double*>(b + 2048);              // 32 doubles
   double* Wc = reinterpret_cast<double*>(b + kHeader);
   double* F[3] = {nullptr, nullptr, nullptr};

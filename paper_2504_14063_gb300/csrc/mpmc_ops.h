@@ -17,6 +17,9 @@ struct Ops {
                uint32_t* flags, unsigned long long* stats);
   void (*update)(const KParams&, cudaStream_t, const double* Un, const double* Uk, double* const* F,
                  const double* scal, double rk0, double rk1, double rk2, double* Uout, double* dUdt, int* status);
+  // ghost states of the characteristic boundaries of U into its ghost buffer
+  // G (FP64 on both paths; nothing to do without such boundaries)
+  void (*ghost)(const KParams&, cudaStream_t, const double* U, double* G);
 };
 
 // discrete adjoint (FP64): per-face contributions of one direction into a

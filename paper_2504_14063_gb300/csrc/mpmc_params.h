@@ -24,15 +24,18 @@ inline int build_params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_mode
   for (int d = 0; d < 3; ++d) {
     if (d < g->dim && g->n[d] < 3) return MPMC_INVALID_ARG;
     if (d >= g->dim && g->n[d] != 1) return MPMC_INVALID_ARG;
-    if (d < g->dim && (g->bc_lo[d] < 0 || g->bc_lo[d] > 3 || g->bc_hi[d] < 0 || g->bc_hi[d] > 3))
+    if (d < g->dim && (g->bc_lo[d] < 0 || g->bc_lo[d] > 4 || g->bc_hi[d] < 0 || g->bc_hi[d] > 4))
+      return MPMC_INVALID_ARG;
+    // characteristic boundaries along x only
+    if (d > 0 && d < g->dim && (g->bc_lo[d] == MPMC_BC_CHAR || g->bc_hi[d] == MPMC_BC_CHAR))
       return MPMC_INVALID_ARG;
     if (d < g->dim && ((g->bc_lo[d] == MPMC_BC_PERIODIC) != (g->bc_hi[d] == MPMC_BC_PERIODIC)))
       return MPMC_INVALID_ARG;
   }
-  // cells (plus the inflow slot) and the faces of each direction are
-  // indexed in 32 bits on the device
+  // cells (plus the inflow slot and the characteristic ghost slots) and the
+  // faces of each direction are indexed in 32 bits on the device
   {
-    long long lim = (long long)g->n[0] * g->n[1] * g->n[2] + 1;
+    long long lim = (long long)g->n[0] * g->n[1] * g->n[2] + 1 + 2LL * g->n[1] * g->n[2];
     for (int d = 0; d < g->dim; ++d) {
       long long nf = 1;
       for (int e = 0; e < 3; ++e) nf *= (long long)g->n[e] + (e == d);
@@ -51,6 +54,12 @@ inline int build_params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_mode
     P.bc_hi[d] = d < D ? g->bc_hi[d] : 0;
     if (d < D && (P.bc_lo[d] == MPMC_BC_INFLOW || P.bc_hi[d] == MPMC_BC_INFLOW)) P.has_inflow = 1;
   }
+  // characteristic x boundaries: one ghost slot per boundary cell; their far
+  // field is the inflow state
+  P.char_lo = g->bc_lo[0] == MPMC_BC_CHAR ? 1 : 0;
+  P.char_hi = g->bc_hi[0] == MPMC_BC_CHAR ? 1 : 0;
+  P.nslots = (P.char_lo + P.char_hi) * g->n[1] * g->n[2];
+  if (P.nslots) P.has_inflow = 1;
   P.ncell = (long long)g->n[0] * g->n[1] * g->n[2];
   P.dx = g->dx;
   P.inv_dx = 1.0 / g->dx;
@@ -124,7 +133,9 @@ inline int build_params(const mpmc_grid* g, const mpmc_eos* eos, const mpmc_mode
     P.wLam = f++;
   }
   P.nW = f;
-  P.wstride = P.ncell + 1;
+  P.wstride = P.ncell + 1 + P.nslots;
+  P.gstride = 1 + P.nslots;
+  P.nextra = P.has_inflow ? 1 + P.nslots : 0;
   round_consts32(P);
   return MPMC_OK;
 }

@@ -105,3 +105,27 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     m.recon, m.viscous, m.precision, m.prandtl = 0, 1, b.FP64, 0.0
     assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
     assert h.value is None
+
+
+def test_characteristic_boundaries_are_validated_without_a_gpu(lib):
+    """MPMC_BC_CHAR (the header's value) is accepted along x only; the
+    allocation-free entry refuses it before any CUDA call."""
+    from paper_2504_14063_gb300 import binding as b
+    from paper_2504_14063_gb300 import workloads as W
+    txt = open(HDR).read()
+    assert re.search(r"#define\s+MPMC_BC_CHAR\s+4\b", txt) and W.BC_CHAR == 4
+    p = W.acoustic_tube(n=16, ny=4)
+    g, e, m = b.structs_from_problem(p)
+    h = ctypes.c_void_p()
+    g.bc_lo[1] = g.bc_hi[1] = W.BC_CHAR
+    assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
+    assert h.value is None
+    g.bc_lo[1] = g.bc_hi[1] = W.BC_PERIODIC
+    g.bc_hi[0] = 5
+    assert b.lib.mpmc_create(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, ctypes.byref(h)) == b.INVALID_ARG
+    g.bc_hi[0] = W.BC_CHAR
+    f = b.lib.mpmc_rhs_noalloc
+    f.restype = ctypes.c_int
+    need = ctypes.c_size_t(0)
+    assert f(ctypes.byref(g), ctypes.byref(e), ctypes.byref(m), None, None, None, None, ctypes.byref(need)) == \
+        b.INVALID_ARG

@@ -170,49 +170,6 @@ def _J_fixed_dt(mp, ag, ctx, p, amps, nsteps, probe, dt):
     return float(J)
 
 
-def test_full_size_gradient_vs_central_differences(mp, ag):
-    """The sensitivity workload at its full size: 512 x 512, 200 SSP-RK3
-    steps of fixed length (the CFL step of the initial state), checkpoint
-    every 20 steps, gradient of the time-integrated pressure probe on the
-    column x = 140 with respect to the 16 interface amplitudes, against
-    central differences of the GPU forward with h = 1e-6 cells (Gamma
-    frozen).  The differences' own error (truncation O(h^2) plus rounding
-    ~ eps J / h) and any limiter decision that switches between the +h and
-    -h runs bound the agreement; the bound is 1e-3 of the largest
-    component."""
-    n, nsteps, G = 512, 200, 400.0
-    p = _amplitude_problem(n, G)
-    ctx = mp.Context(p)
-    probe = _probe(p, 140)
-    amps0 = W.seeded_fourier_amplitudes(3, 8, 1.0)
-    dt = float(ctx.dt_gamma(ctx.init_state(torch.from_numpy(p.prim)))[0])
-    amps = torch.from_numpy(amps0).cuda().requires_grad_(True)
-    phi_l = torch.from_numpy(p.prim[2, 0]).cuda()
-    a0, a1 = W.interface_fractions(n, amps, phi_l, xp=torch)
-    prim = torch.cat([a0[None, None], a1[None, None], torch.from_numpy(p.prim[2:]).cuda()], 0)
-    _, J, _ = ag.rollout(ctx, ag.init_state(ctx, prim), nsteps, every=20, probe=probe, dt=dt)
-    grad, = torch.autograd.grad(J, amps)
-    grad = grad.cpu().numpy()
-    J0 = _J_fixed_dt(mp, ag, ctx, p, torch.from_numpy(amps0).cuda(), nsteps, probe, dt)
-    assert J0 == pytest.approx(float(J.detach()), rel=1e-13)
-    h = 1e-6
-    fd = np.zeros_like(amps0)
-    for m in range(8):
-        for c in range(2):
-            e = np.zeros_like(amps0)
-            e[m, c] = h
-            Jp = _J_fixed_dt(mp, ag, ctx, p, torch.from_numpy(amps0 + e).cuda(), nsteps, probe, dt)
-            Jm = _J_fixed_dt(mp, ag, ctx, p, torch.from_numpy(amps0 - e).cuda(), nsteps, probe, dt)
-            fd[m, c] = (Jp - Jm) / (2 * h)
-    err = np.abs(grad - fd).max() / np.abs(fd).max()
-    print(f"512^2, {nsteps} steps: max |adjoint - central difference| / max |gradient| = {err:.2e}")
-    print("adjoint", np.array2string(grad.ravel(), precision=5))
-    print("fd     ", np.array2string(fd.ravel(), precision=5))
-    assert ctx.status() == 0
-    assert np.abs(fd).max() > 0
-    assert err < 1e-3
-
-
 def test_gradient_vs_oracle_tangent_128(mp, ag):
     """The sensitivity workload reduced to 128 x 128 and 50 steps: <grad J,
     da> from the GPU adjoint against dJ along da from the oracle's
