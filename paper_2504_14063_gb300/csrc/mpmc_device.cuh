@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mpmc_narrow.h"
+
 namespace mpmc {
 
 constexpr int MAXS = 4;
@@ -116,14 +118,18 @@ struct CRef {
   unsigned flip;   // bit d: negate u_d / m_d
 };
 
-__device__ __forceinline__ CRef map_cell(const KParams& P, int i, int j, int k) {
+// MASK bit d: coordinate d may lie outside the grid (the others are known to
+// be inside, so their tests and the slot arithmetic they would need are
+// compiled out at the call sites that know it)
+template <unsigned MASK>
+__device__ __forceinline__ CRef map_cell_m(const KParams& P, int i, int j, int k) {
   int c[3] = {i, j, k};
   unsigned flip = 0u;
   bool inflow = false;
-  int chr = -1;  // a characteristic x boundary: 0 low side, 1 high side
+  int chr = 0;  // a characteristic x boundary: 1 low side, 2 high side
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    if (d < P.dim) {
+    if (((MASK >> d) & 1u) && d < P.dim) {
       const int n = P.n[d];
       if (c[d] < 0 || c[d] >= n) {
         const bool lo = c[d] < 0;
@@ -136,12 +142,12 @@ __device__ __forceinline__ CRef map_cell(const KParams& P, int i, int j, int k) 
           flip ^= 1u << d;
         } else if (bc == BC_ZEROGRAD) {
           c[d] = lo ? 0 : n - 1;
-        } else if (bc == BC_CHAR) {
+        } else if (d == 0 && bc == BC_CHAR) {
           // the ghost slot of the boundary cell of this row (x only): the
           // other directions still map the row's coordinates (and walls
           // mirror the ghost's velocity)
-          chr = lo ? 0 : 1;
-          c[d] = lo ? 0 : n - 1;
+          chr = lo ? 1 : 2;
+          c[d] = 0;
         } else {
           inflow = true;
           flip = 0u;
@@ -151,15 +157,24 @@ __device__ __forceinline__ CRef map_cell(const KParams& P, int i, int j, int k) 
   }
   CRef r;
   r.flip = flip;
-  if (inflow) {
-    r.idx = P.ncell;
-  } else if (chr >= 0) {
-    const long long row = (long long)c[2] * P.n[1] + c[1];
-    r.idx = P.ncell + 1 + (chr == 1 && P.char_lo ? (long long)P.n[1] * P.n[2] : 0) + row;
-  } else {
-    r.idx = ((long long)c[2] * P.n[1] + c[1]) * P.n[0] + c[0];
-  }
+  // a row's cells, or its characteristic slot after the inflow slot
+  const long long row = (long long)c[2] * P.n[1] + c[1];
+  const long long slot = P.ncell + 1 + (chr == 2 && P.char_lo ? (long long)P.n[1] * P.n[2] : 0) + row;
+  r.idx = inflow ? P.ncell : (((MASK & 1u) && chr) ? slot : row * P.n[0] + c[0]);
   return r;
+}
+
+__device__ __forceinline__ CRef map_cell(const KParams& P, int i, int j, int k) {
+  return map_cell_m<7u>(P, i, j, k);
+}
+
+// a neighbour whose coordinates DIR and t (a tangential direction) may lie
+// outside the grid
+template <int DIR>
+__device__ __forceinline__ CRef map_cell_dt(const KParams& P, int t, int i, int j, int k) {
+  if (t == 0) return map_cell_m<(1u << DIR) | 1u>(P, i, j, k);
+  if (t == 1) return map_cell_m<(1u << DIR) | 2u>(P, i, j, k);
+  return map_cell_m<(1u << DIR) | 4u>(P, i, j, k);
 }
 
 __device__ __forceinline__ double sgn_flip(unsigned flip, int d) { return (flip >> d) & 1u ? -1.0 : 1.0; }
@@ -234,12 +249,6 @@ __device__ __forceinline__ void pt_residual(const KParams& P, const double* Y, c
   }
 }
 
-// p-T equilibrium from mass fractions, specific internal energy and volume
-// (Eqs. NASG_T1, NASG_T2, NASG_P).  One stiffened component (or several
-// sharing Pinf): the quadratic of NASG_P, larger root in cancellation-free
-// form, linear root without gas.  Several distinct Pinf: safeguarded Newton
-// on the common-pressure residual, started from the quadratic with a
-// Y-weighted Pinf, at most 100 iterations.
 // Non-contracting arithmetic for the inversion U -> (P, T).  The pressure of
 // a stiff liquid (P << Pinf) is the small difference of terms ~ gamma Pinf,
 // so it inherits the rounding of every operation before it; evaluating in
@@ -285,12 +294,63 @@ __device__ __forceinline__ void decode(const double* U, double& rho, double* Y, 
   }
 }
 
+// the same residual solved in FP32 (its coefficients rounded once, on the
+// integer pipes, the constants from KParams.f32) by safeguarded Halley steps
+// from x0: a start for the FP64 iteration that costs little on the FP32 pipe.
+// Its root is within FP32 rounding of the residual's terms (for a stiff
+// liquid, P to ~eps32 Pinf), from which one or two FP64 steps reach the
+// FP64 root.
+template <int NS>
+__device__ __forceinline__ double pt_start_f32(const KParams& P, const double* Y, const double* w, double Cv,
+                                               double lo, double x0) {
+  float wf[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) wf[k] = Y[k] != 0.0 ? narrow(w[k]) : 0.f;
+  const float cvf = narrow(Cv), lof = narrow(lo);
+  float x = narrow(x0), a = lof, b = INFINITY;
+  for (int it = 0; it < 40; ++it) {
+    float f = -cvf, df = 0.f, d2f = 0.f, mag = cvf, rg = 0.f;
+    bool have_rg = false;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      if (Y[k] != 0.0) {
+        float r;
+        if (P.f32.pinf[k] == 0.f) {
+          if (!have_rg) {
+            rg = __frcp_rn(x);
+            have_rg = true;
+          }
+          r = rg;
+        } else {
+          r = __frcp_rn(x + P.f32.pinf[k]);
+        }
+        const float t = wf[k] * r;
+        f += t;
+        df -= t * r;
+        d2f += 2.f * t * r * r;
+        mag += fabsf(t);
+      }
+    }
+    if (f > 0.f) a = x;
+    else b = x;
+    if (fabsf(f) <= 16.f * 1.1920929e-7f * mag) break;
+    const float hd = 2.f * df * df - f * d2f;
+    float xn = hd > 0.f ? x - 2.f * f * df / hd : x - f / df;
+    if (!(xn > a && xn < b)) xn = b == INFINITY ? x + fmaxf(x - lof, 1.f) : 0.5f * (a + b);
+    const bool done = fabsf(xn - x) <= 2.4e-7f * fabsf(xn);
+    x = xn;
+    if (done || !(b > a)) break;
+  }
+  return (double)x;
+}
+
 // p-T equilibrium from mass fractions, specific internal energy and volume
 // (Eqs. NASG_T1, NASG_T2, NASG_P).  One stiffened component (or several
 // sharing Pinf): the quadratic of NASG_P, larger root in cancellation-free
-// form, linear root without gas.  Several distinct Pinf: safeguarded Newton
-// on the common-pressure residual, started from the quadratic with a
-// Y-weighted Pinf, at most 100 iterations.
+// form, linear root without gas.  Several distinct Pinf: safeguarded Halley
+// steps on the common-pressure residual from the caller's guess or, without
+// one, from an FP32 solve started at the quadratic with a Y-weighted Pinf,
+// at most 100 iterations.
 template <int NS, bool EX = true>
 __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, double v, double& p, double& T,
                               double rho = 0.0, double guess = -1e300) {
@@ -356,6 +416,8 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
                            : 2.0 * a3 / (sqrt(a2 * a2 + 4.0 * Cv * a3) - a2))
               : (Ep * Rl - pe * Cv - pe * Rl) / Cv;
       if (!(x > a)) x = lo + fmax(fabs(lo), 1.0);
+      const double xs = pt_start_f32<NS>(P, Y, w, Cv, lo, x);
+      if (xs > a && xs < 1e300) x = xs;
     }
     double f, df, d2f, mag;
     bool conv = false;

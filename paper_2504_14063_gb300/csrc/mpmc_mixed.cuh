@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
   for (int j = 0; j < 6; ++j) {
     int cc[3] = {ci[0], ci[1], ci[2]};
     cc[d] += j - 2;
-    cr[j] = map_cell(P, cc[0], cc[1], cc[2]);
+    cr[j] = map_cell_m<1u << d>(P, cc[0], cc[1], cc[2]);
   }
   const CRef ri = cr[2], rj = cr[3];
   uint32_t fl = 0u;
@@ -862,10 +862,10 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
         int b0[3] = {a0[0], a0[1], a0[2]}, b1[3] = {a1[0], a1[1], a1[2]};
         b0[d] += 1;
         b1[d] += 1;
-        const float pip = wgetf(P, Wc, P.wPsi, map_cell(P, a0[0], a0[1], a0[2]));
-        const float pim = wgetf(P, Wc, P.wPsi, map_cell(P, a1[0], a1[1], a1[2]));
-        const float pjp = wgetf(P, Wc, P.wPsi, map_cell(P, b0[0], b0[1], b0[2]));
-        const float pjm = wgetf(P, Wc, P.wPsi, map_cell(P, b1[0], b1[1], b1[2]));
+        const float pip = wgetf(P, Wc, P.wPsi, map_cell_dt<d>(P, t, a0[0], a0[1], a0[2]));
+        const float pim = wgetf(P, Wc, P.wPsi, map_cell_dt<d>(P, t, a1[0], a1[1], a1[2]));
+        const float pjp = wgetf(P, Wc, P.wPsi, map_cell_dt<d>(P, t, b0[0], b0[1], b0[2]));
+        const float pjm = wgetf(P, Wc, P.wPsi, map_cell_dt<d>(P, t, b1[0], b1[1], b1[2]));
         g[t] = 0.25f * idx * ((pip - pim) + (pjp - pjm));
       }
       const float gn = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
@@ -969,8 +969,8 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
       int b0[3] = {a0[0], a0[1], a0[2]}, b1[3] = {a1[0], a1[1], a1[2]};
       b0[d] += 1;
       b1[d] += 1;
-      const CRef ip = map_cell(P, a0[0], a0[1], a0[2]), im = map_cell(P, a1[0], a1[1], a1[2]);
-      const CRef jp = map_cell(P, b0[0], b0[1], b0[2]), jm = map_cell(P, b1[0], b1[1], b1[2]);
+      const CRef ip = map_cell_dt<d>(P, t, a0[0], a0[1], a0[2]), im = map_cell_dt<d>(P, t, a1[0], a1[1], a1[2]);
+      const CRef jp = map_cell_dt<d>(P, t, b0[0], b0[1], b0[2]), jm = map_cell_dt<d>(P, t, b1[0], b1[1], b1[2]);
 #pragma unroll
       for (int i = 0; i < D; ++i) {
         const float dip = wgetf(P, Wc, P.wU + i, ip) * sgnf(ip.flip, i) - wgetf(P, Wc, P.wU + i, im) * sgnf(im.flip, i);
