@@ -47,15 +47,21 @@ GRID_N = 256                  # the droplet field's cells per direction
 CPU_SLAB_PLANES = 16          # z-planes of the field in the CPU oracle's sample
 L2_BYTES = 129 * 2 ** 20
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of each kernel
-# on this workload, from an ncu capture of the same field at 128^3 scaled by
-# the faces (cells) of a 256^3 launch; reported only while the kernel's
-# sources hash to the captured version (None otherwise)
-TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel on
+# the 256^3 droplet field, in bytes: an ncu capture of the same field at
+# 128^3 (every launch of one SSP-RK3 step of each path: nine face launches,
+# three of each other kernel, averaged) scaled by the faces (cells) of a
+# 256^3 launch, 7.969 (8); the counters take more than one ncu pass, which
+# the full-size workload is not captured with.  Reported only on that grid
+# and while the kernels' sources hash to the captured version (None
+# otherwise).
+TRAFFIC_GRID = 256
+TRAFFIC = {"k_face": 6.281e9, "mx::k_face": 3.765e9, "k_prim": 4.206e9, "mx::k_prim": 3.107e9,
+           "k_update": 5.961e9, "mx::k_update": 5.958e9}
 TRAFFIC_SOURCES = ("paper_2504_14063_gb300/csrc/mpmc_kernels.cuh", "paper_2504_14063_gb300/csrc/mpmc_device.cuh",
                    "paper_2504_14063_gb300/csrc/mpmc_kernels_d3.cu", "paper_2504_14063_gb300/csrc/mpmc_mixed.cuh",
                    "paper_2504_14063_gb300/csrc/mpmc_mixed_d3.cu", "paper_2504_14063_gb300/csrc/mpmc_update.cuh")
-TRAFFIC_SHA256 = None
+TRAFFIC_SHA256 = "1562b02de83041437917033f0e03b960c9d0cca1f5d5dee2c677b7c7d3a42d7d"
 
 
 def sources_sha256():
@@ -66,8 +72,8 @@ def sources_sha256():
     return h.hexdigest()
 
 
-def traffic_of(kernel):
-    if TRAFFIC_SHA256 is None or kernel not in TRAFFIC:
+def traffic_of(kernel, grid):
+    if TRAFFIC_SHA256 is None or kernel not in TRAFFIC or grid != TRAFFIC_GRID:
         return None
     return TRAFFIC[kernel] if sources_sha256() == TRAFFIC_SHA256 else None
 
@@ -207,10 +213,25 @@ def field_errors(A, B, p):
 
 
 STUDIES = {
-    # name: (workload, the configuration's step count)
+    # name: (workload, the configuration's step count; None: one period of
+    # the workload's end time at its initial CFL step)
+    "interface_advection_1d": (lambda W: W.interface_advection_1d(n=400), None),
+    "shock_bubble_2d": (lambda W: W.shock_bubble_2d(nx=1024, ny=512), 2000),
     "droplet_field_3d": (lambda W: W.droplet_field_3d(n=256), 500),
     "shock_droplet_3d": (lambda W: W.shock_droplet_3d(n=512), 200),
 }
+# the uniform (P, T, u) of the interface-equilibrium workload, whose
+# deviation after the run each path reports
+IEC_STATE = {"interface_advection_1d": (1e5, 300.0, 100.0)}
+
+
+def iec_errors(ctx, U, p, ref):
+    """max |P/P0 - 1|, |T/T0 - 1|, |u/u0 - 1| over the cells (Appendix C's
+    interface-equilibrium invariant)."""
+    W = ctx.primitives(U)
+    P0, T0, u0 = ref
+    return {"P": float((W[1] / P0 - 1).abs().max()), "T": float((W[0] / T0 - 1).abs().max()),
+            "u": float((W[4 + p.ns] / u0 - 1).abs().max())}
 
 
 def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=None, twin=False):
@@ -227,6 +248,7 @@ def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=
     problem's own response to rounding at FP32 level, the scale against
     which the mixed path's error is read."""
     steps = max(int(steps), 1)
+    every = max(every, steps // 10)
     prim = torch.from_numpy(p.prim)
     out = {"study": name, "metric": "mixed vs FP64: per-field L1/Linf of the state difference; cell-updates/s",
            "unit": UNIT, "grid": list(p.n[:p.dim]), "cells": p.ncells, "species": p.ns,
@@ -290,6 +312,10 @@ def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=
                             "norm": "state-scaled (partial densities by rho, momenta by rho*1000 m/s, energy by E)",
                             "l1": l1, "linf": li, "history": hist}
     out["status"] = {"fp64": c64.status(), "mixed": cmx.status()}
+    if name in IEC_STATE:
+        out["iec"] = {"fp64": iec_errors(c64, A, p, IEC_STATE[name]),
+                      "mixed": iec_errors(cmx, B, p, IEC_STATE[name]),
+                      "note": "max relative deviation of P, T, u from the uniform initial values"}
     if twin:
         out["error_vs_fp64"]["twin"] = {"perturbation": "U0 (1 + 2^-24 xi), xi standard normal, seed 7",
                                         "l1": t1, "linf": ti}
@@ -501,6 +527,23 @@ def update_bytes(p, stage):
     return 8 * nv * (states * N) + 8 * nv * faces
 
 
+def update_flops(p, stage):
+    """FP64 arithmetic of the divergence + RK update per cell as the method
+    states it (comparisons not counted): per variable the D flux
+    differences summed (2D - 1), the scaling by rk2 dt / dx (1) and the RK
+    combination (one FMA in stage 1, two in stages 2 and 3, 2 flops each);
+    the admissibility test of Eqs. PositivityReqs1/2: the density sum
+    (NS - 1), the covolume and reference-energy sums (2 NS each when
+    present), -YTOL rho (1), |m|^2 (2D - 1) and rho E - |m|^2/2 (2), minus
+    rho sum rhoY_k q_k (2 when present)."""
+    nv, D, ns = p.nvars, p.dim, p.ns
+    has_b = any(getattr(sp, "b", 0.0) != 0.0 for sp in p.species)
+    has_q = any(getattr(sp, "q", 0.0) != 0.0 for sp in p.species)
+    per_var = (2 * D - 1) + 1 + 2 * (1 if stage == 1 else 2)
+    adm = (ns - 1) + 2 * ns * has_b + 2 * ns * has_q + 1 + (2 * D - 1) + 2 + 2 * has_q
+    return nv * per_var + adm
+
+
 def cache_fields(p):
     """Fields of the primitive cache a context keeps per cell: T, P, rho, a,
     Y_k, u_d; with CDI phi_0, psi, (Y^c/Y_p) rho_p, h_p rho_p of both
@@ -581,6 +624,11 @@ def main():
             t0 = time.perf_counter()
             p = make(W)
             t_build = time.perf_counter() - t0
+            if nsteps is None:
+                c = mp.Context(p)
+                dt0 = float(c.dt_gamma(c.init_state(torch.from_numpy(p.prim)))[0])
+                nsteps = int(np.ceil(p.t_end / dt0))
+                del c
             line = precision_study(mp, torch, name, p, args.study_steps or nsteps, t_build=t_build,
                                    twin=args.twin)
             print(json.dumps(line), flush=True)
@@ -655,17 +703,32 @@ def main():
     def alu(kernel, ms, peak, pipe):
         ach = fpf * faces_per_launch / (ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": traffic_of(kernel), "kernel": kernel, "pipe": pipe, "flops_per_face": fpf,
+                "traffic": traffic_of(kernel, p.n[0]), "kernel": kernel, "pipe": pipe, "flops_per_face": fpf,
                 "faces_per_launch": faces_per_launch, "avg_launch_ms": ms}
 
     def hbm(kernel, ms, nbytes, note):
         ach = nbytes / (ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                "traffic": traffic_of(kernel), "kernel": kernel, "bytes_per_launch": nbytes,
+                "traffic": traffic_of(kernel, p.n[0]), "kernel": kernel, "bytes_per_launch": nbytes,
                 "avg_launch_ms": ms, "note": note}
 
     n_w64 = cache_fields(p)
     upd_b = (update_bytes(p, 1) + 2 * update_bytes(p, 2)) / 3.0
+    upd_f = p.ncells * (update_flops(p, 1) + 2 * update_flops(p, 2)) / 3.0
+
+    def update_roof(kernel, ms, note):
+        """The update against both roofs; `bound` names the one whose time
+        at its peak is the longer (the FP64 pipe on GB300)."""
+        mem = hbm(kernel, ms, upd_b, note)
+        ach = upd_f / (ms / 1e3) / 1e12
+        fp64 = {"achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                "flops_per_launch": upd_f, "pipe": "FP64"}
+        if upd_f / (fp64_peak * 1e12) > upd_b / (hbm_peak * 1e9):
+            out = dict(mem, bound="alu", achieved=ach, peak=fp64_peak, unit="TFLOP/s", frac=ach / fp64_peak,
+                       flops_per_launch=upd_f, pipe="FP64")
+            out["hbm"] = {k: mem[k] for k in ("achieved", "peak", "unit", "frac", "bytes_per_launch")}
+            return out
+        return dict(mem, fp64=fp64)
     peak_note = (f"measured: mpmc_fma_probe, FP64 FMA chains, {peaks['fp64']['blocks']} blocks x 256 threads, "
                  f"best of 5 (SM clock {peaks['fp64']['clocks'].get('sm_mhz')} MHz)")
     roofline = alu("k_face", kp["face"][0], fp64_peak, "FP64")
@@ -675,13 +738,17 @@ def main():
         "mx::k_face": dict(alu("mx::k_face", kpm["face"][0], fp32_peak, "FP32"),
                            peak_source="measured: mpmc_fma_probe, FP32 FMA chains (the same algorithmic "
                                        "operation count, executed in FP32 but for the FP64 limiter re-checks)"),
-        "k_update": hbm("k_update", kp["update"][0], upd_b,
-                        "FP64 flux differences and RK combination; bytes averaged over the three stages"),
-        "mx::k_update": hbm("mx::k_update", kpm["update"][0], upd_b, "the same body on the FP64 fluxes"),
+        "k_update": update_roof("k_update", kp["update"][0],
+                                "FP64 flux differences and RK combination; bytes and flops averaged over "
+                                "the three stages"),
+        "mx::k_update": update_roof("mx::k_update", kpm["update"][0], "the same body on the FP64 fluxes"),
     }
-    rooflines["k_prim"] = hbm("k_prim", kp["prim"][0], prim_bytes(p, n_w64, 8), "FP64 p-T inversion")
+    prim_note = ("bound by the FP64 pipe, not HBM: an ncu capture of the 128^3 case shows the FP64 pipe "
+                 "82-88 % active and DRAM at 2-4 % of peak; the iterative p-T solve has no fixed flop "
+                 "count, so the HBM fraction of the bytes it moves is what is reported")
+    rooflines["k_prim"] = hbm("k_prim", kp["prim"][0], prim_bytes(p, n_w64, 8), "FP64 p-T inversion; " + prim_note)
     rooflines["mx::k_prim"] = hbm("mx::k_prim", kpm["prim"][0], prim_bytes(p, n_w64, 4),
-                                  "FP64 p-T inversion, FP32 cache")
+                                  "FP64 p-T inversion, FP32 cache; " + prim_note)
     mixed = {"value": vm, "unit": UNIT, "ms_per_step": 1e3 * tm / args.steps, "speedup_vs_fp64": vm / value,
              "clocks": clk_m, "kernel_ms_per_step": {k: v[0] * v[1] for k, v in kpm.items()},
              "error_vs_fp64": err, "status": mstat}

@@ -351,7 +351,13 @@ __device__ __forceinline__ double pt_start_f32(const KParams& P, const double* Y
 // steps on the common-pressure residual from the caller's guess or, without
 // one, from an FP32 solve started at the quadratic with a Y-weighted Pinf,
 // at most 100 iterations.
-template <int NS, bool EX = true>
+// F32OUT: the caller keeps P and T only in FP32 (the mixed path's cache).
+// The FP64 iteration then stops after a Halley step smaller than 1e-6 of the
+// distance to the nearest pole of the residual (x - lo): the terms are
+// analytic within that distance, so the step leaves an error of order
+// 1e-18 (x - lo), far below FP32 rounding of P.  T follows in FP32 (its
+// ratios (P + gamma Pinf) / (P + Pinf) are well conditioned).
+template <int NS, bool EX = true, bool F32OUT = false>
 __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, double v, double& p, double& T,
                               double rho = 0.0, double guess = -1e300) {
   double Cv = 0.0, q = 0.0, b = 0.0;
@@ -441,6 +447,7 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
       }
       const double dxn = fabs(xn - x);
       x = xn;
+      if (F32OUT && dxn <= 1e-6 * (x - lo)) { conv = true; break; }
       if (dxn <= 4.5e-16 * fabs(x) || !(bb > a)) {
         pt_residual<NS>(P, Y, w, Cv, x, f, df, d2f, mag);
         x = x - f / df;   // one more Newton step at full accuracy
@@ -450,6 +457,20 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
     }
     if (!conv && st == ST_OK) st = ST_EOS_NO_CONVERGE;
     p = x;
+    if (F32OUT) {
+      const float pf = narrow(p);
+      float den = 0.f;
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+        if (Y[k] != 0.0) {
+          const float r = P.f32.pinf[k] == 0.f
+                              ? 1.f
+                              : __fdividef(pf + P.f32.gam[k] * P.f32.pinf[k], pf + P.f32.pinf[k]);
+          den += narrow(Y[k]) * P.f32.cv[k] * r;
+        }
+      T = (double)__fdividef(narrow(em), den);
+      return st;
+    }
   }
   if (!EX && !multi && pl > 0.0) {
     // every stiffened species present shares P + pl: T = em (P + pl) /
@@ -553,11 +574,17 @@ __device__ __forceinline__ void eos_char(const KParams& P, const double* Y, doub
 }
 
 // ---------------------------------------------------------------------------
-// WENO5-Z (Borges et al. 2008), exponent 1: value at the right face of v2
+// WENO5-Z (Borges et al. 2008), exponent 1: value at the right face of v2.
+// Same weights, fewer FP64 instructions: the candidates are carried as
+// 6 q_0, 36 q_1, 18 q_2 (the 1/6 of the stencils and the ideal weights
+// d = (1, 6, 3)/10 folded into their coefficients), and alpha_k = d_k (1 +
+// tau/(b_k+eps)) over the common denominator prod_j (b_j+eps) reads
+// (c_k + tau) prod_{j!=k} c_j; the quotient is scaled back by the 6 in the
+// denominator.
 __device__ __forceinline__ double weno5z(double v0, double v1, double v2, double v3, double v4, double eps) {
-  const double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
-  const double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) * (1.0 / 6.0);
-  const double q2 = (2.0 * v2 + 5.0 * v3 - v4) * (1.0 / 6.0);
+  const double q0 = 2.0 * v0 - 7.0 * v1 + 11.0 * v2;
+  const double q1 = -6.0 * v1 + 30.0 * v2 + 12.0 * v3;
+  const double q2 = 6.0 * v2 + 15.0 * v3 - 3.0 * v4;
   double t = v0 - 2.0 * v1 + v2, s = v0 - 4.0 * v1 + 3.0 * v2;
   const double b0 = (13.0 / 12.0) * t * t + 0.25 * s * s;
   t = v1 - 2.0 * v2 + v3;
@@ -567,12 +594,11 @@ __device__ __forceinline__ double weno5z(double v0, double v1, double v2, double
   s = 3.0 * v2 - 4.0 * v3 + v4;
   const double b2 = (13.0 / 12.0) * t * t + 0.25 * s * s;
   const double tau = fabs(b0 - b2);
-  // alpha_k = d_k (1 + tau/(b_k+eps)) brought to one common denominator
   const double c0 = b0 + eps, c1 = b1 + eps, c2 = b2 + eps;
-  const double a0 = 0.1 * (c0 + tau) * c1 * c2;
-  const double a1 = 0.6 * (c1 + tau) * c0 * c2;
-  const double a2 = 0.3 * (c2 + tau) * c0 * c1;
-  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+  const double a0 = (c0 + tau) * (c1 * c2);
+  const double a1 = (c1 + tau) * (c0 * c2);
+  const double a2 = (c2 + tau) * (c0 * c1);
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (6.0 * a0 + 36.0 * a1 + 18.0 * a2);
 }
 
 // ---------------------------------------------------------------------------

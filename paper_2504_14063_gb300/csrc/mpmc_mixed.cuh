@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
     for (int k = 0; k < NS; ++k)
       if (Uc[k] < -YTOL * rho) st = ST_INADMISSIBLE;
     double pd, Td;
-    const int st2 = pt_equilibrium<NS, false>(P, Y, e, vol, pd, Td, rho);
+    const int st2 = pt_equilibrium<NS, false, true>(P, Y, e, vol, pd, Td, rho);
     if (st == ST_OK) st = st2;
     SpeciesF sp[NS];
     load_species<NS>(P, sp);

@@ -38,9 +38,45 @@ def test_field_errors_scaling():
         assert l1[k] == 0.0 and li[k] == 0.0
 
 
-def test_studies_are_the_3d_configurations():
+def test_studies_are_the_configurations():
+    """The 1D interface advection runs one period (its step count follows
+    from the initial CFL step), the 2D shock-bubble 2000 steps, the 3D
+    fields 500 and 200; the 1D one reports the interface-equilibrium
+    deviation of its uniform (P, T, u)."""
+    assert bench.STUDIES["interface_advection_1d"][1] is None
+    assert bench.STUDIES["shock_bubble_2d"][1] == 2000
     assert bench.STUDIES["droplet_field_3d"][1] == 500
     assert bench.STUDIES["shock_droplet_3d"][1] == 200
+    p = bench.STUDIES["interface_advection_1d"][0](W)
+    assert p.n[0] == 400 and p.t_end == pytest.approx(1.0 / 100.0)
+    assert bench.IEC_STATE["interface_advection_1d"] == (1e5, 300.0, 100.0)
+    q = bench.STUDIES["shock_bubble_2d"][0](W)
+    assert tuple(q.n[:2]) == (1024, 512) and q.ns == 3
+
+
+def test_update_flops_of_the_droplet_field():
+    """The FP64 operation count behind the update's roofline: per variable
+    2D - 1 for the flux differences, 1 for the scaling and 2 per RK FMA (one
+    in stage 1, two after), plus the admissibility test (covolumes and
+    reference energies of the NASG liquids present)."""
+    p = W.droplet_field_3d(n=16)
+    nv, D, ns = 8, 3, 4
+    has_b = any(sp.b != 0.0 for sp in p.species)
+    has_q = any(sp.q != 0.0 for sp in p.species)
+    adm = (ns - 1) + 2 * ns * has_b + 2 * ns * has_q + 1 + (2 * D - 1) + 2 + 2 * has_q
+    assert bench.update_flops(p, 1) == nv * (2 * D - 1 + 1 + 2) + adm
+    assert bench.update_flops(p, 2) == nv * (2 * D - 1 + 1 + 4) + adm
+
+
+def test_traffic_is_reported_only_for_the_captured_grid_and_sources():
+    """The DRAM bytes of the ncu capture belong to the 256^3 launches of the
+    kernels as captured: another grid, or changed sources, report None."""
+    assert bench.traffic_of("k_face", 128) is None
+    assert bench.traffic_of("no_such_kernel", bench.TRAFFIC_GRID) is None
+    if bench.TRAFFIC_SHA256 is not None and bench.sources_sha256() == bench.TRAFFIC_SHA256:
+        assert bench.traffic_of("k_face", bench.TRAFFIC_GRID) == bench.TRAFFIC["k_face"]
+    else:
+        assert bench.traffic_of("k_face", bench.TRAFFIC_GRID) is None
 
 
 def test_flops_per_face_of_the_benchmark_workload():
