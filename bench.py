@@ -56,12 +56,12 @@ L2_BYTES = 129 * 2 ** 20
 # and while the kernels' sources hash to the captured version (None
 # otherwise).
 TRAFFIC_GRID = 256
-TRAFFIC = {"k_face": 6.281e9, "mx::k_face": 3.765e9, "k_prim": 4.206e9, "mx::k_prim": 3.107e9,
+TRAFFIC = {"k_face": 6.282e9, "mx::k_face": 3.764e9, "k_prim": 4.206e9, "mx::k_prim": 3.109e9,
            "k_update": 5.961e9, "mx::k_update": 5.958e9}
 TRAFFIC_SOURCES = ("paper_2504_14063_gb300/csrc/mpmc_kernels.cuh", "paper_2504_14063_gb300/csrc/mpmc_device.cuh",
                    "paper_2504_14063_gb300/csrc/mpmc_kernels_d3.cu", "paper_2504_14063_gb300/csrc/mpmc_mixed.cuh",
                    "paper_2504_14063_gb300/csrc/mpmc_mixed_d3.cu", "paper_2504_14063_gb300/csrc/mpmc_update.cuh")
-TRAFFIC_SHA256 = "1562b02de83041437917033f0e03b960c9d0cca1f5d5dee2c677b7c7d3a42d7d"
+TRAFFIC_SHA256 = "d6d4ba50a99450c275fa7fa362febd4e1afef7816102db13a16801fed0402ea0"
 
 
 def sources_sha256():
@@ -234,13 +234,14 @@ def iec_errors(ctx, U, p, ref):
             "u": float((W[4 + p.ns] / u0 - 1).abs().max())}
 
 
-def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=None, twin=False):
+def precision_study(mp, torch, name, p, steps, n_timed=5, every=50, t_build=None, twin=False):
     """The mixed path against the FP64 path on a 3D workload at full size:
     both advanced in lockstep from the same initial state with a common
     step size (the FP64 path's CFL step, so that both reach the same
     physical times), per-field L1/Linf of the difference every `every`
     steps; throughput of each path timed separately with CUDA events over
-    `timed_steps` steps (CFL step on the device, after 3 warm-up steps).
+    `n_timed` steps (CFL step on the device, after 3 warm-up steps;
+    library profiling off), per-kernel times from as many further steps.
     The states exceed L2 many times over, so no flush is needed.
     twin: a third context, FP64, started from the initial state with a
     relative perturbation 2^-24 xi (xi standard normal, seed 7) and
@@ -261,23 +262,14 @@ def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=
         for _ in range(3):
             ctx.rk_step(U)
         torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(timed_steps)]
         clocks = ClockSampler(torch.cuda.current_device())
         clocks.start()
-        ctx.set_profiling(True)
-        for k in range(timed_steps):
-            ev[k][0].record()
-            ctx.rk_step(U)
-            ev[k][1].record()
-        torch.cuda.synchronize()
-        ctx.set_profiling(False)
+        ts = sum(timed_steps(torch, ctx, U, n_timed)) / 1e3
         clk = clocks.stop()
-        ts = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-        prof = ctx.profile(reset=True)
-        perf[label] = {"value": p.ncells * timed_steps / ts, "ms_per_step": 1e3 * ts / timed_steps,
-                       "kernel_ms_per_step": {k: v[0] / timed_steps for k, v in prof.items()},
-                       "timed_steps": timed_steps, "clocks": clk, "status": ctx.status()}
+        kp = kernel_pass(torch, ctx, U, n_timed)
+        perf[label] = {"value": p.ncells * n_timed / ts, "ms_per_step": 1e3 * ts / n_timed,
+                       "kernel_ms_per_step": {k: v[0] * v[1] for k, v in kp.items()},
+                       "timed_steps": n_timed, "clocks": clk, "status": ctx.status()}
         del ctx, U
         torch.cuda.empty_cache()
     perf["mixed"]["speedup_vs_fp64"] = perf["mixed"]["value"] / perf["fp64"]["value"]
@@ -313,8 +305,9 @@ def precision_study(mp, torch, name, p, steps, timed_steps=5, every=50, t_build=
                             "l1": l1, "linf": li, "history": hist}
     out["status"] = {"fp64": c64.status(), "mixed": cmx.status()}
     if name in IEC_STATE:
+        # (both states are FP64 vectors; the FP64 context decodes either)
         out["iec"] = {"fp64": iec_errors(c64, A, p, IEC_STATE[name]),
-                      "mixed": iec_errors(cmx, B, p, IEC_STATE[name]),
+                      "mixed": iec_errors(c64, B, p, IEC_STATE[name]),
                       "note": "max relative deviation of P, T, u from the uniform initial values"}
     if twin:
         out["error_vs_fp64"]["twin"] = {"perturbation": "U0 (1 + 2^-24 xi), xi standard normal, seed 7",

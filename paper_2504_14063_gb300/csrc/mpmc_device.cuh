@@ -356,7 +356,8 @@ __device__ __forceinline__ double pt_start_f32(const KParams& P, const double* Y
 // distance to the nearest pole of the residual (x - lo): the terms are
 // analytic within that distance, so the step leaves an error of order
 // 1e-18 (x - lo), far below FP32 rounding of P.  T follows in FP32 (its
-// ratios (P + gamma Pinf) / (P + Pinf) are well conditioned).
+// ratios (P + gamma Pinf) / (P + Pinf) are well conditioned).  The
+// contracted FP64 solve (EX = false) stops the same way at 1e-7.
 template <int NS, bool EX = true, bool F32OUT = false>
 __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, double v, double& p, double& T,
                               double rho = 0.0, double guess = -1e300) {
@@ -447,7 +448,11 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
       }
       const double dxn = fabs(xn - x);
       x = xn;
-      if (F32OUT && dxn <= 1e-6 * (x - lo)) { conv = true; break; }
+      // the contracted solve (face averages, the mixed cell inversion) takes
+      // a Halley step below 1e-7 (FP32 output: 1e-6) of the distance to the
+      // nearest pole as final: the error it leaves is of order dxn^3 /
+      // (x - lo)^2, 1e-21 (FP32 output: 1e-18) of x - lo
+      if (!EX && dxn <= (F32OUT ? 1e-6 : 1e-7) * (x - lo)) { conv = true; break; }
       if (dxn <= 4.5e-16 * fabs(x) || !(bb > a)) {
         pt_residual<NS>(P, Y, w, Cv, x, f, df, d2f, mag);
         x = x - f / df;   // one more Newton step at full accuracy
@@ -581,7 +586,8 @@ __device__ __forceinline__ void eos_char(const KParams& P, const double* Y, doub
 // tau/(b_k+eps)) over the common denominator prod_j (b_j+eps) reads
 // (c_k + tau) prod_{j!=k} c_j; the quotient is scaled back by the 6 in the
 // denominator.
-__device__ __forceinline__ double weno5z(double v0, double v1, double v2, double v3, double v4, double eps) {
+__device__ __forceinline__ void weno5z_nd(double v0, double v1, double v2, double v3, double v4, double eps,
+                                          double& num, double& den) {
   const double q0 = 2.0 * v0 - 7.0 * v1 + 11.0 * v2;
   const double q1 = -6.0 * v1 + 30.0 * v2 + 12.0 * v3;
   const double q2 = 6.0 * v2 + 15.0 * v3 - 3.0 * v4;
@@ -598,7 +604,14 @@ __device__ __forceinline__ double weno5z(double v0, double v1, double v2, double
   const double a0 = (c0 + tau) * (c1 * c2);
   const double a1 = (c1 + tau) * (c0 * c2);
   const double a2 = (c2 + tau) * (c0 * c1);
-  return (a0 * q0 + a1 * q1 + a2 * q2) / (6.0 * a0 + 36.0 * a1 + 18.0 * a2);
+  num = a0 * q0 + a1 * q1 + a2 * q2;
+  den = 6.0 * a0 + 36.0 * a1 + 18.0 * a2;
+}
+
+__device__ __forceinline__ double weno5z(double v0, double v1, double v2, double v3, double v4, double eps) {
+  double num, den;
+  weno5z_nd(v0, v1, v2, v3, v4, eps, num, den);
+  return num / den;
 }
 
 // ---------------------------------------------------------------------------
@@ -747,6 +760,34 @@ __device__ __forceinline__ double recon(double v0, double v1, double v2, double 
   else if constexpr (RC == RC_TENO5) return teno5(v0, v1, v2, v3, v4);
   else if constexpr (RC == RC_TENO6) return teno6(v0, v1, v2, v3, v4, v5);
   else return weno5z(v0, v1, v2, v3, v4, eps);
+}
+
+// both face values of one field from the cells y[0..5] = i-2..i+3 around
+// the face i+1/2: L from the left (recon of y[0..5]), R from the right (of
+// y[5..0]).  WENO5-Z forms the two quotients with one reciprocal,
+// num_L d_R / (d_L d_R) and num_R d_L / (d_L d_R), while d_L d_R is a
+// normal number whose reciprocal is normal too (exponent field 2..2044,
+// tested on the integer pipe), else with two divisions.
+template <int RC>
+__device__ __forceinline__ void recon_lr(const double* y, double eps, double& L, double& R) {
+  if constexpr (RC == RC_WENO5Z) {
+    double nL, dL, nR, dR;
+    weno5z_nd(y[0], y[1], y[2], y[3], y[4], eps, nL, dL);
+    weno5z_nd(y[5], y[4], y[3], y[2], y[1], eps, nR, dR);
+    const double dd = dL * dR;
+    const unsigned ex = ((unsigned)__double2hiint(dd) >> 20) & 0x7ffu;
+    if (ex - 2u <= 2042u) {
+      const double r = 1.0 / dd;
+      L = nL * (dR * r);
+      R = nR * (dL * r);
+    } else {
+      L = nL / dL;
+      R = nR / dR;
+    }
+  } else {
+    L = recon<RC>(y[0], y[1], y[2], y[3], y[4], y[5], eps);
+    R = recon<RC>(y[5], y[4], y[3], y[2], y[1], y[0], eps);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -363,12 +363,10 @@ __global__ void __launch_bounds__(FACE_THREADS)
       w5[j] = (0.5 * c) * un + 0.5 * p;
       w6[j] = (-0.5 * c) * un + 0.5 * p;
     }
-    const double w1L = recon<RC>(w1[0], w1[1], w1[2], w1[3], w1[4], w1[5], eps);
-    const double w1R = recon<RC>(w1[5], w1[4], w1[3], w1[2], w1[1], w1[0], eps);
-    const double w5L = recon<RC>(w5[0], w5[1], w5[2], w5[3], w5[4], w5[5], eps);
-    const double w5R = recon<RC>(w5[5], w5[4], w5[3], w5[2], w5[1], w5[0], eps);
-    const double w6L = recon<RC>(w6[0], w6[1], w6[2], w6[3], w6[4], w6[5], eps);
-    const double w6R = recon<RC>(w6[5], w6[4], w6[3], w6[2], w6[1], w6[0], eps);
+    double w1L, w1R, w5L, w5R, w6L, w6R;
+    recon_lr<RC>(w1, eps, w1L, w1R);
+    recon_lr<RC>(w5, eps, w5L, w5R);
+    recon_lr<RC>(w6, eps, w6L, w6R);
     TL = w1L + X * w5L + X * w6L;
     TR = w1R + X * w5R + X * w6R;
     uL[d] = ic * w5L + (-ic) * w6L;
@@ -381,8 +379,7 @@ __global__ void __launch_bounds__(FACE_THREADS)
     double y[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) y[j] = wget(P, Wc, P.wY + k, cr[j]);
-    YL[k] = recon<RC>(y[0], y[1], y[2], y[3], y[4], y[5], eps);
-    YR[k] = recon<RC>(y[5], y[4], y[3], y[2], y[1], y[0], eps);
+    recon_lr<RC>(y, eps, YL[k], YR[k]);
   }
 #pragma unroll
   for (int t = 0; t < D; ++t) {
@@ -390,8 +387,7 @@ __global__ void __launch_bounds__(FACE_THREADS)
     double y[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) y[j] = wget(P, Wc, P.wU + t, cr[j]) * sgn_flip(cr[j].flip, t);
-    uL[t] = recon<RC>(y[0], y[1], y[2], y[3], y[4], y[5], eps);
-    uR[t] = recon<RC>(y[5], y[4], y[3], y[2], y[1], y[0], eps);
+    recon_lr<RC>(y, eps, uL[t], uR[t]);
   }
 
   // cell values of the two face neighbours
@@ -430,22 +426,27 @@ __global__ void __launch_bounds__(FACE_THREADS)
   }
 
   // flux limiter (Sec. 3.3.2): pseudo-updates of both cells
-  double Uni[NV], Unj[NV], Uki[NV], Ukj[NV];
+  // Bi, Bj: the RK combination rk0 U^n + rk1 U^(k) of both cells, formed
+  // once for the (up to three) pseudo-update tests of this face
+  double Bi[NV], Bj[NV], Uki[NV], Ukj[NV];
   const double lam = 2.0 * D * rk2 * dt * P.inv_dx;
   if (P.pos_limiter || P.cdi) {
-    load_U<NS, D>(P, Un, P.gn, ri, Uni);
-    load_U<NS, D>(P, Un, P.gn, rj, Unj);
     load_U<NS, D>(P, Uk, Uin, ri, Uki);
     load_U<NS, D>(P, Uk, Uin, rj, Ukj);
+    load_U<NS, D>(P, Un, P.gn, ri, Bi);
+    load_U<NS, D>(P, Un, P.gn, rj, Bj);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Bi[v] = rk0 * Bi[v] + rk1 * Uki[v];
+      Bj[v] = rk0 * Bj[v] + rk1 * Ukj[v];
+    }
   }
   auto passes = [&](const double* Ft) {
     double Ti_[NV], Tj_[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double base_i = rk0 * Uni[v] + rk1 * Uki[v];
-      const double base_j = rk0 * Unj[v] + rk1 * Ukj[v];
-      Ti_[v] = base_i - lam * Ft[v];
-      Tj_[v] = base_j + lam * Ft[v];
+      Ti_[v] = Bi[v] - lam * Ft[v];
+      Tj_[v] = Bj[v] + lam * Ft[v];
     }
     return admissible<NS, D>(P, Ti_) && admissible<NS, D>(P, Tj_);
   };

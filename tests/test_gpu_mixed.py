@@ -153,7 +153,7 @@ def test_precision_study_small_3d(mp):
     of the same norm, and the n-step mixed-precision bound above."""
     import bench
     p = W.droplet_field_3d(n=24, ndrops=4, seed=2, rmin=3.0, rmax=5.0)
-    out = bench.precision_study(mp, torch, "droplet_field_3d_24", p, 6, timed_steps=2, every=3, twin=True)
+    out = bench.precision_study(mp, torch, "droplet_field_3d_24", p, 6, n_timed=2, every=3, twin=True)
     assert out["status"] == {"fp64": 0, "mixed": 0, "fp64_twin": 0}
     tw = out["error_vs_fp64"]["twin"]
     assert 0.0 < max(tw["l1"].values()) < 1e-5
