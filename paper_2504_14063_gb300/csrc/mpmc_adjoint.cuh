@@ -18,13 +18,14 @@ namespace adj {
 // candidate to rounding, and the weights' own derivative grows like 1/eps)
 constexpr double WENO_FLAT = 1e-10;
 
-// WENO5-Z (the kernel's form with one common denominator): its value and
-// gradient g[j] = d(out)/d(v_j) in one pass
+// WENO5-Z (the forward kernel's form: candidates carried as 6 q_0, 36 q_1,
+// 18 q_2, weights over one common denominator): its value and gradient
+// g[j] = d(out)/d(v_j) in one pass
 __device__ __forceinline__ double weno_val_grad(double v0, double v1, double v2, double v3, double v4, double eps,
                                                 double* g) {
-  const double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
-  const double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) * (1.0 / 6.0);
-  const double q2 = (2.0 * v2 + 5.0 * v3 - v4) * (1.0 / 6.0);
+  const double Q0 = 2.0 * v0 - 7.0 * v1 + 11.0 * v2;
+  const double Q1 = -6.0 * v1 + 30.0 * v2 + 12.0 * v3;
+  const double Q2 = 6.0 * v2 + 15.0 * v3 - 3.0 * v4;
   const double t0 = v0 - 2.0 * v1 + v2, s0 = v0 - 4.0 * v1 + 3.0 * v2;
   const double t1 = v1 - 2.0 * v2 + v3, s1 = v1 - v3;
   const double t2 = v2 - 2.0 * v3 + v4, s2 = 3.0 * v2 - 4.0 * v3 + v4;
@@ -33,11 +34,12 @@ __device__ __forceinline__ double weno_val_grad(double v0, double v1, double v2,
   const double b2 = (13.0 / 12.0) * t2 * t2 + 0.25 * s2 * s2;
   const double tau = fabs(b0 - b2);
   const double c0 = b0 + eps, c1 = b1 + eps, c2 = b2 + eps;
-  const double A0 = 0.1 * (c0 + tau) * c1 * c2;
-  const double A1 = 0.6 * (c1 + tau) * c0 * c2;
-  const double A2 = 0.3 * (c2 + tau) * c0 * c1;
-  const double iS = 1.0 / (A0 + A1 + A2);
-  const double out = (A0 * q0 + A1 * q1 + A2 * q2) * iS;
+  const double p12 = c1 * c2, p02 = c0 * c2, p01 = c0 * c1;
+  const double A0 = (c0 + tau) * p12, A1 = (c1 + tau) * p02, A2 = (c2 + tau) * p01;
+  // out = sum_k A_k Q_k / S, S = 6 A0 + 36 A1 + 18 A2 (the ideal weights
+  // 1/10, 6/10, 3/10 and the candidates' 1/6 folded in)
+  const double iS = 1.0 / (6.0 * A0 + 36.0 * A1 + 18.0 * A2);
+  const double out = (A0 * Q0 + A1 * Q1 + A2 * Q2) * iS;
   double M = fmax(fmax(fabs(v0), fabs(v1)), fmax(fmax(fabs(v2), fabs(v3)), fabs(v4)));
   const double tol = (WENO_FLAT * M) * (WENO_FLAT * M);
   if (b0 <= tol && b1 <= tol && b2 <= tol) {
@@ -49,26 +51,24 @@ __device__ __forceinline__ double weno_val_grad(double v0, double v1, double v2,
     g[4] = -1.0 / 20.0;
     return out;
   }
-  // out = sum A_k q_k / S: dA_k -> (q_k - out)/S, dq_k -> A_k/S
-  const double lA0 = (q0 - out) * iS, lA1 = (q1 - out) * iS, lA2 = (q2 - out) * iS;
-  const double lq0 = A0 * iS, lq1 = A1 * iS, lq2 = A2 * iS;
-  double lc0 = 0.0, lc1 = 0.0, lc2 = 0.0, ltau = 0.0;
-  double a = lA0 * 0.1;
-  lc0 += a * c1 * c2; ltau += a * c1 * c2; lc1 += a * (c0 + tau) * c2; lc2 += a * (c0 + tau) * c1;
-  a = lA1 * 0.6;
-  lc1 += a * c0 * c2; ltau += a * c0 * c2; lc0 += a * (c1 + tau) * c2; lc2 += a * (c1 + tau) * c0;
-  a = lA2 * 0.3;
-  lc2 += a * c0 * c1; ltau += a * c0 * c1; lc0 += a * (c2 + tau) * c1; lc1 += a * (c2 + tau) * c0;
+  // dA_k -> (Q_k - w_k out)/S with w = (6, 36, 18); dQ_k -> A_k/S
+  const double lA0 = (Q0 - 6.0 * out) * iS, lA1 = (Q1 - 36.0 * out) * iS, lA2 = (Q2 - 18.0 * out) * iS;
+  const double lQ0 = A0 * iS, lQ1 = A1 * iS, lQ2 = A2 * iS;
+  // A0 = (c0 + tau) c1 c2 and cyclically
+  const double lc0 = lA0 * p12 + lA1 * (c1 + tau) * c2 + lA2 * (c2 + tau) * c1;
+  const double lc1 = lA1 * p02 + lA0 * (c0 + tau) * c2 + lA2 * (c2 + tau) * c0;
+  const double lc2 = lA2 * p01 + lA0 * (c0 + tau) * c1 + lA1 * (c1 + tau) * c0;
+  const double ltau = lA0 * p12 + lA1 * p02 + lA2 * p01;
   const double sg = (b0 - b2) >= 0.0 ? 1.0 : -1.0;
   const double lb0 = lc0 + sg * ltau, lb1 = lc1, lb2 = lc2 - sg * ltau;
   const double lt0 = lb0 * (13.0 / 6.0) * t0, ls0 = lb0 * 0.5 * s0;
   const double lt1 = lb1 * (13.0 / 6.0) * t1, ls1 = lb1 * 0.5 * s1;
   const double lt2 = lb2 * (13.0 / 6.0) * t2, ls2 = lb2 * 0.5 * s2;
-  g[0] = lt0 + ls0 + lq0 * (2.0 / 6.0);
-  g[1] = -2.0 * lt0 - 4.0 * ls0 + lt1 + ls1 - lq0 * (7.0 / 6.0) - lq1 * (1.0 / 6.0);
-  g[2] = lt0 + 3.0 * ls0 - 2.0 * lt1 + lt2 + 3.0 * ls2 + lq0 * (11.0 / 6.0) + lq1 * (5.0 / 6.0) + lq2 * (2.0 / 6.0);
-  g[3] = lt1 - ls1 - 2.0 * lt2 - 4.0 * ls2 + lq1 * (2.0 / 6.0) + lq2 * (5.0 / 6.0);
-  g[4] = lt2 + ls2 - lq2 * (1.0 / 6.0);
+  g[0] = lt0 + ls0 + 2.0 * lQ0;
+  g[1] = -2.0 * lt0 - 4.0 * ls0 + lt1 + ls1 - 7.0 * lQ0 - 6.0 * lQ1;
+  g[2] = lt0 + 3.0 * ls0 - 2.0 * lt1 + lt2 + 3.0 * ls2 + 11.0 * lQ0 + 30.0 * lQ1 + 6.0 * lQ2;
+  g[3] = lt1 - ls1 - 2.0 * lt2 - 4.0 * ls2 + 12.0 * lQ1 + 15.0 * lQ2;
+  g[4] = lt2 + ls2 - 3.0 * lQ2;
   return out;
 }
 

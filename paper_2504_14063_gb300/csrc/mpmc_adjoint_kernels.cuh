@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(VJP_THREADS)
   for (int j = 0; j < 6; ++j) {
     int cc[3] = {ci[0], ci[1], ci[2]};
     cc[d] += j - 2;
-    cr[j] = map_cell(P, cc[0], cc[1], cc[2]);
+    cr[j] = map_cell_m<1u << d, false>(P, cc[0], cc[1], cc[2]);
   }
   const CRef ri = cr[2], rj = cr[3];
   // adjoint of this face's flux: F enters L_i with -1/dx and L_{i+1} with +1/dx
@@ -430,10 +430,10 @@ __global__ void __launch_bounds__(VJP_THREADS)
         int b0[3] = {a0[0], a0[1], a0[2]}, b1[3] = {a1[0], a1[1], a1[2]};
         b0[d] += 1;
         b1[d] += 1;
-        g[t] = 0.5 * ((wget(P, Wc, P.wPsi, map_cell(P, a0[0], a0[1], a0[2])) -
-                       wget(P, Wc, P.wPsi, map_cell(P, a1[0], a1[1], a1[2]))) * (0.5 * P.inv_dx) +
-                      (wget(P, Wc, P.wPsi, map_cell(P, b0[0], b0[1], b0[2])) -
-                       wget(P, Wc, P.wPsi, map_cell(P, b1[0], b1[1], b1[2]))) * (0.5 * P.inv_dx));
+        g[t] = 0.5 * ((wget(P, Wc, P.wPsi, map_cell_dt<d, false>(P, t, a0[0], a0[1], a0[2])) -
+                       wget(P, Wc, P.wPsi, map_cell_dt<d, false>(P, t, a1[0], a1[1], a1[2]))) * (0.5 * P.inv_dx) +
+                      (wget(P, Wc, P.wPsi, map_cell_dt<d, false>(P, t, b0[0], b0[1], b0[2])) -
+                       wget(P, Wc, P.wPsi, map_cell_dt<d, false>(P, t, b1[0], b1[1], b1[2]))) * (0.5 * P.inv_dx));
       }
       const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
       const bool nact = gn >= GTOL;
@@ -799,10 +799,10 @@ __global__ void __launch_bounds__(VJP_THREADS)
   unflatten(fid, f0, f1, fc);
   int ci[3] = {fc[0], fc[1], fc[2]};
   ci[d] -= 1;
-  const CRef ri = map_cell(P, ci[0], ci[1], ci[2]);
+  const CRef ri = map_cell_m<1u << d, false>(P, ci[0], ci[1], ci[2]);
   int cj3[3] = {ci[0], ci[1], ci[2]};
   cj3[d] += 1;
-  const CRef rj = map_cell(P, cj3[0], cj3[1], cj3[2]);
+  const CRef rj = map_cell_m<1u << d, false>(P, cj3[0], cj3[1], cj3[2]);
   const double sc = (mul_dt ? coef * scal[0] : coef) * P.inv_dx;
   const bool real_i = ci[d] >= 0, real_j = ci[d] + 1 <= P.n[d] - 1;
   double nu[NV];
@@ -846,10 +846,10 @@ __global__ void __launch_bounds__(VJP_THREADS)
     int b0[3] = {a0[0], a0[1], a0[2]}, b1[3] = {a1[0], a1[1], a1[2]};
     b0[d] += 1;
     b1[d] += 1;
-    tn[t][0] = map_cell(P, a0[0], a0[1], a0[2]);
-    tn[t][1] = map_cell(P, a1[0], a1[1], a1[2]);
-    tn[t][2] = map_cell(P, b0[0], b0[1], b0[2]);
-    tn[t][3] = map_cell(P, b1[0], b1[1], b1[2]);
+    tn[t][0] = map_cell_dt<d, false>(P, t, a0[0], a0[1], a0[2]);
+    tn[t][1] = map_cell_dt<d, false>(P, t, a1[0], a1[1], a1[2]);
+    tn[t][2] = map_cell_dt<d, false>(P, t, b0[0], b0[1], b0[2]);
+    tn[t][3] = map_cell_dt<d, false>(P, t, b1[0], b1[1], b1[2]);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       const double dip = wget(P, Wc, P.wU + i, tn[t][0]) * sgn_flip(tn[t][0].flip, i) -

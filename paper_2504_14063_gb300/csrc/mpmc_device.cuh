@@ -114,14 +114,17 @@ __device__ __forceinline__ void unflatten(long long l, int n0, int n1, int* x) {
 // negates that velocity component, an inflow face replaces the cell by the
 // inflow state (later walls still mirror it).
 struct CRef {
-  long long idx;   // cell index, or ncell for the inflow state
+  int idx;         // cell index, or ncell for the inflow state (the host keeps
+                   // every cell, slot and face index below 2^31 - 1)
   unsigned flip;   // bit d: negate u_d / m_d
 };
 
 // MASK bit d: coordinate d may lie outside the grid (the others are known to
 // be inside, so their tests and the slot arithmetic they would need are
 // compiled out at the call sites that know it)
-template <unsigned MASK>
+// CHR = false: the caller's context has no characteristic boundary (the
+// adjoint refuses them), so their slot arithmetic is compiled out as well
+template <unsigned MASK, bool CHR = true>
 __device__ __forceinline__ CRef map_cell_m(const KParams& P, int i, int j, int k) {
   int c[3] = {i, j, k};
   unsigned flip = 0u;
@@ -142,7 +145,7 @@ __device__ __forceinline__ CRef map_cell_m(const KParams& P, int i, int j, int k
           flip ^= 1u << d;
         } else if (bc == BC_ZEROGRAD) {
           c[d] = lo ? 0 : n - 1;
-        } else if (d == 0 && bc == BC_CHAR) {
+        } else if (CHR && d == 0 && bc == BC_CHAR) {
           // the ghost slot of the boundary cell of this row (x only): the
           // other directions still map the row's coordinates (and walls
           // mirror the ghost's velocity)
@@ -158,9 +161,10 @@ __device__ __forceinline__ CRef map_cell_m(const KParams& P, int i, int j, int k
   CRef r;
   r.flip = flip;
   // a row's cells, or its characteristic slot after the inflow slot
-  const long long row = (long long)c[2] * P.n[1] + c[1];
-  const long long slot = P.ncell + 1 + (chr == 2 && P.char_lo ? (long long)P.n[1] * P.n[2] : 0) + row;
-  r.idx = inflow ? P.ncell : (((MASK & 1u) && chr) ? slot : row * P.n[0] + c[0]);
+  const int nc = (int)P.ncell;
+  const int row = c[2] * P.n[1] + c[1];
+  const int slot = nc + 1 + (chr == 2 && P.char_lo ? P.n[1] * P.n[2] : 0) + row;
+  r.idx = inflow ? nc : ((CHR && (MASK & 1u) && chr) ? slot : row * P.n[0] + c[0]);
   return r;
 }
 
@@ -170,11 +174,11 @@ __device__ __forceinline__ CRef map_cell(const KParams& P, int i, int j, int k) 
 
 // a neighbour whose coordinates DIR and t (a tangential direction) may lie
 // outside the grid
-template <int DIR>
+template <int DIR, bool CHR = true>
 __device__ __forceinline__ CRef map_cell_dt(const KParams& P, int t, int i, int j, int k) {
-  if (t == 0) return map_cell_m<(1u << DIR) | 1u>(P, i, j, k);
-  if (t == 1) return map_cell_m<(1u << DIR) | 2u>(P, i, j, k);
-  return map_cell_m<(1u << DIR) | 4u>(P, i, j, k);
+  if (t == 0) return map_cell_m<(1u << DIR) | 1u, CHR>(P, i, j, k);
+  if (t == 1) return map_cell_m<(1u << DIR) | 2u, CHR>(P, i, j, k);
+  return map_cell_m<(1u << DIR) | 4u, CHR>(P, i, j, k);
 }
 
 __device__ __forceinline__ double sgn_flip(unsigned flip, int d) { return (flip >> d) & 1u ? -1.0 : 1.0; }
