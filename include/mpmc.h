@@ -173,6 +173,11 @@ int mpmc_set_stream(mpmc_ctx* ctx, void* stream);
 /* Number of conserved components ns + dim + 1 and of cells. */
 int mpmc_nvars(const mpmc_ctx* ctx);
 size_t mpmc_ncells(const mpmc_ctx* ctx);
+/* Doubles of one primitive cache (the per-cell fields of Sec. 3.1.3's
+ * step 1 that the face pass reads, with the boundary slots): the unit of
+ * the W_stages buffers of mpmc_rk_step_record / mpmc_rk_step_adjoint.  0
+ * for a null context. */
+size_t mpmc_cache_doubles(const mpmc_ctx* ctx);
 
 /* Conserved state from primitive fields (Eq. NASG_EOS with Amagat mixing,
  * Sec. 2.2.1): rhoY_k = alpha_k / v_k(P,T), m = rho u,
@@ -230,19 +235,24 @@ int mpmc_rhs_adjoint(mpmc_ctx* ctx, const double* U, const mpmc_stage* stage, co
 
 /* One SSP-RK3 step like mpmc_rk_step that also keeps what its reverse needs:
  * U_stages (device, 2 x nv x ncells, caller-owned) receives the stage states
- * U^(1) and U^(2); tape (nullable, device, 3 x faces uint32) the flags. */
-int mpmc_rk_step_record(mpmc_ctx* ctx, double* U, double dt, uint32_t* tape, double* U_stages);
+ * U^(1) and U^(2); tape (nullable, device, 3 x faces uint32) the flags;
+ * W_stages (nullable, device, 3 x mpmc_cache_doubles, caller-owned; FP64
+ * contexts only, else MPMC_INVALID_ARG) the primitive caches of U^n, U^(1)
+ * and U^(2), which spare the reverse step their recomputation. */
+int mpmc_rk_step_record(mpmc_ctx* ctx, double* U, double dt, uint32_t* tape, double* U_stages, double* W_stages);
 
 /* Reverse of one SSP-RK3 step (Eq. SSPRK3) from U_n:
  *   lam_n = (dU^{n+1}/dU^n)^T lam_next.
  * dt: as passed to mpmc_rk_step (<= 0: the CFL step of U_n, recomputed
  * bit-identically).  U_stages (nullable): the step's stage states from
- * mpmc_rk_step_record; recomputed from U_n when null.  tape: that step's
+ * mpmc_rk_step_record; recomputed from U_n when null.  W_stages (nullable;
+ * only with U_stages): that call's primitive caches, used instead of
+ * recomputing them (the result is the same bit for bit).  tape: that step's
  * 3 x faces flags (nullable: recomputed).  lam_n may equal lam_next (in
  * place).  Device arrays, layout of U.  The result does not depend on the
  * order in which the GPU runs threads (no atomic accumulation). */
-int mpmc_rk_step_adjoint(mpmc_ctx* ctx, const double* U_n, const double* U_stages, double dt, const uint32_t* tape,
-                         const double* lam_next, double* lam_n);
+int mpmc_rk_step_adjoint(mpmc_ctx* ctx, const double* U_n, const double* U_stages, const double* W_stages, double dt,
+                         const uint32_t* tape, const double* lam_next, double* lam_n);
 
 /* Reverse of mpmc_init_state: lam_prim = (dU/dprim)^T lam_U, layouts as for
  * mpmc_init_state (prim: the forward's input). */

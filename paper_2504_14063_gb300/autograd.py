@@ -70,6 +70,17 @@ class _Primitives(torch.autograd.Function):
         return None, fctx.ctx.primitives_adjoint(U, gW.contiguous())
 
 
+def _stage_caches(ctx, m, device, share=0.5):
+    """Buffers for the primitive caches of a segment's m steps (3 stages
+    each), which spare the reverse steps their recomputation, when they fit
+    in `share` of the device's free memory; else None (recomputed)."""
+    nbytes = m * 3 * ctx.cache_doubles * 8
+    free, _ = torch.cuda.mem_get_info(device)
+    if nbytes > share * free:
+        return None
+    return torch.empty((m, 3 * ctx.cache_doubles), dtype=torch.float64, device=device)
+
+
 def _probe_term(ctx, U, probe):
     """sum_c probe_c P_c(U)"""
     return (ctx.primitives(U)[1] * probe).sum()
@@ -117,17 +128,20 @@ class _Rollout(torch.autograd.Function):
             states = torch.empty((m + 1,) + tuple(lam.shape), dtype=lam.dtype, device=lam.device)
             stages = torch.empty((m, 2) + tuple(lam.shape), dtype=lam.dtype, device=lam.device)
             tapes = torch.empty((m, 3 * nf), dtype=torch.int32, device=lam.device)
+            wst = _stage_caches(ctx, m, lam.device)
             states[0].copy_(fctx.ckpts[seg])
             for q in range(m):
                 states[q + 1].copy_(states[q])
-                ctx.rk_step_record(states[q + 1], dt_host[k0 + q], tapes[q], stages[q])
+                ctx.rk_step_record(states[q + 1], dt_host[k0 + q], tapes[q], stages[q],
+                                   wst[q] if wst is not None else None)
             for q in reversed(range(m)):
                 k = k0 + q
                 if lamW is not None:
                     # dJ/dU^{k+1} = gJ dt_k (dP/dU)^T probe
                     lamW[1] = (gJ * dt_host[k]) * probe
                     ctx.primitives_adjoint(states[q + 1], lamW, lam)
-                ctx.rk_step_adjoint(states[q], lam, dt=dt_host[k], tape=tapes[q], lam_n=lam, stages=stages[q])
+                ctx.rk_step_adjoint(states[q], lam, dt=dt_host[k], tape=tapes[q], lam_n=lam, stages=stages[q],
+                                    wstages=wst[q] if wst is not None else None)
         return None, lam, None, None, None, None
 
 

@@ -70,6 +70,7 @@ def _load():
         "mpmc_set_stream": (i, [vp, vp]),
         "mpmc_nvars": (i, [vp]),
         "mpmc_ncells": (ctypes.c_size_t, [vp]),
+        "mpmc_cache_doubles": (ctypes.c_size_t, [vp]),
         "mpmc_init_state": (i, [vp, vp, vp]),
         "mpmc_rhs": (i, [vp, vp, vp, ctypes.POINTER(StageC), vp]),
         "mpmc_rk_step": (i, [vp, vp, d, vp]),
@@ -77,8 +78,8 @@ def _load():
         "mpmc_step_n_host": (i, [vp, vp, i]),
         "mpmc_dt_gamma": (i, [vp, vp, vp]),
         "mpmc_rhs_adjoint": (i, [vp, vp, ctypes.POINTER(StageC), vp, vp, vp]),
-        "mpmc_rk_step_record": (i, [vp, vp, d, vp, vp]),
-        "mpmc_rk_step_adjoint": (i, [vp, vp, vp, d, vp, vp, vp]),
+        "mpmc_rk_step_record": (i, [vp, vp, d, vp, vp, vp]),
+        "mpmc_rk_step_adjoint": (i, [vp, vp, vp, vp, d, vp, vp, vp]),
         "mpmc_init_state_adjoint": (i, [vp, vp, vp, vp]),
         "mpmc_primitives": (i, [vp, vp, vp]),
         "mpmc_primitives_adjoint": (i, [vp, vp, vp, vp]),
@@ -171,6 +172,7 @@ class Context:
         self.h = h
         self.nv = lib.mpmc_nvars(h)
         self.ncells = lib.mpmc_ncells(h)
+        self.cache_doubles = lib.mpmc_cache_doubles(h)
         self.shape = (self.nv, problem.n[2], problem.n[1], problem.n[0])
         self.device = torch.device("cuda", torch.cuda.current_device())
 
@@ -261,21 +263,32 @@ class Context:
                                          _dev(lam_dUdt), _dev(lam_U)))
         return lam_U
 
-    def rk_step_record(self, U, dt=0.0, tape=None, stages=None):
+    def _wstages(self, w):
+        """Device pointer of a stage-cache buffer (3 x cache_doubles FP64), or None."""
+        if w is None:
+            return None
+        if not (w.dtype == torch.float64 and w.is_cuda and w.is_contiguous() and w.numel() >= 3 * self.cache_doubles):
+            raise ValueError("wstages: a contiguous CUDA float64 tensor of at least 3 x cache_doubles elements")
+        return w.data_ptr()
+
+    def rk_step_record(self, U, dt=0.0, tape=None, stages=None, wstages=None):
         """One SSP-RK3 step in place that also returns its stage states
-        (2 x state: U^(1), U^(2)) and fills `tape` (3 x faces uint32) if given."""
+        (2 x state: U^(1), U^(2)) and fills `tape` (3 x faces uint32) and
+        `wstages` (3 x cache_doubles FP64: the primitive caches of U^n, U^(1),
+        U^(2)) if given."""
         stages = torch.empty((2,) + tuple(U.shape), dtype=U.dtype, device=U.device) if stages is None else stages
-        self._check(lib.mpmc_rk_step_record(self.h, _dev(U), float(dt), _ptr(tape), _dev(stages)))
+        self._check(lib.mpmc_rk_step_record(self.h, _dev(U), float(dt), _ptr(tape), _dev(stages),
+                                            self._wstages(wstages)))
         return stages
 
-    def rk_step_adjoint(self, U_n, lam_next, dt=0.0, tape=None, lam_n=None, stages=None):
+    def rk_step_adjoint(self, U_n, lam_next, dt=0.0, tape=None, lam_n=None, stages=None, wstages=None):
         """lam_n = (dU^{n+1}/dU^n)^T lam_next for the SSP-RK3 step from U_n
-        (dt and Gamma frozen; dt <= 0: the CFL step of U_n).  stages/tape:
-        from rk_step_record (recomputed when None).  lam_n may be lam_next
-        (in place)."""
+        (dt and Gamma frozen; dt <= 0: the CFL step of U_n).  stages/tape/
+        wstages: from rk_step_record (recomputed when None).  lam_n may be
+        lam_next (in place)."""
         lam_n = torch.empty_like(lam_next) if lam_n is None else lam_n
-        self._check(lib.mpmc_rk_step_adjoint(self.h, _dev(U_n), _ptr(stages), float(dt), _ptr(tape),
-                                             _dev(lam_next), _dev(lam_n)))
+        self._check(lib.mpmc_rk_step_adjoint(self.h, _dev(U_n), _ptr(stages), self._wstages(wstages), float(dt),
+                                             _ptr(tape), _dev(lam_next), _dev(lam_n)))
         return lam_n
 
     def init_state_adjoint(self, prim, lam_U):
@@ -347,12 +360,12 @@ def rhs_adjoint(ctx, U, stage, tape, lam_dUdt, lam_U=None):
     return ctx.rhs_adjoint(U, stage, tape, lam_dUdt, lam_U)
 
 
-def rk_step_record(ctx, U, dt=0.0, tape=None, stages=None):
-    return ctx.rk_step_record(U, dt, tape, stages)
+def rk_step_record(ctx, U, dt=0.0, tape=None, stages=None, wstages=None):
+    return ctx.rk_step_record(U, dt, tape, stages, wstages)
 
 
-def rk_step_adjoint(ctx, U_n, lam_next, dt=0.0, tape=None, lam_n=None, stages=None):
-    return ctx.rk_step_adjoint(U_n, lam_next, dt, tape, lam_n, stages)
+def rk_step_adjoint(ctx, U_n, lam_next, dt=0.0, tape=None, lam_n=None, stages=None, wstages=None):
+    return ctx.rk_step_adjoint(U_n, lam_next, dt, tape, lam_n, stages, wstages)
 
 
 def init_state_adjoint(ctx, prim, lam_U):

@@ -299,6 +299,7 @@ extern "C" int mpmc_set_stream(mpmc_ctx* c, void* stream) {
 
 extern "C" int mpmc_nvars(const mpmc_ctx* c) { return c ? c->P.nv : 0; }
 extern "C" size_t mpmc_ncells(const mpmc_ctx* c) { return c ? (size_t)c->P.ncell : 0; }
+extern "C" size_t mpmc_cache_doubles(const mpmc_ctx* c) { return c ? (size_t)c->P.nW * c->P.wstride : 0; }
 extern "C" const char* mpmc_last_error(const mpmc_ctx* c) { return c ? c->err : "null context"; }
 
 extern "C" int mpmc_init_state(mpmc_ctx* c, const double* prim, double* U) {
@@ -484,16 +485,16 @@ static void faces_only(mpmc_ctx* c, cudaStream_t s, const double* Un, const doub
 // out = a x + b y + cz z + coef (dt) (dL/dU)^T lamL at U (whose primitive
 // cache is in Wc): per direction the faces' slots, their gather, then the
 // per-cell primitive-recovery reverse fused with the combination
-static void stage_vjp(mpmc_ctx* c, cudaStream_t s, const double* U, const uint32_t* tape, const double* lamL,
-                      double coef, int mul_dt, double* out, double a, const double* x, double b, const double* y,
-                      double cz, const double* z) {
+static void stage_vjp(mpmc_ctx* c, cudaStream_t s, const double* U, const double* Wc, const uint32_t* tape,
+                      const double* lamL, double coef, int mul_dt, double* out, double a, const double* x, double b,
+                      const double* y, double cz, const double* z) {
   const KParams& P = c->P;
   long long off = 0;
   for (int d = 0; d < P.dim; ++d) {
     {
       ProfScope ps(c, FAM_ADJ_FACE, s);
-      c->aops.face(P, s, d, c->Wc, U, c->Uin, c->scal, tape + off, lamL, coef, mul_dt, c->Cslots);
-      if (P.viscous) c->aops.face_visc(P, s, d, c->Wc, c->scal, tape + off, lamL, coef, mul_dt, c->Cslots);
+      c->aops.face(P, s, d, Wc, U, c->Uin, c->scal, tape + off, lamL, coef, mul_dt, c->Cslots);
+      if (P.viscous) c->aops.face_visc(P, s, d, Wc, c->scal, tape + off, lamL, coef, mul_dt, c->Cslots);
     }
     ProfScope ps(c, FAM_ADJ_PRIM, s);
     c->aops.gather(P, s, d, c->Cslots, d == 0, c->gW, c->gU);
@@ -519,30 +520,43 @@ extern "C" int mpmc_rhs_adjoint(mpmc_ctx* c, const double* U, const mpmc_stage* 
     faces_only(c, s, Un, U, rk0, rk1, rk2, c->tape_int);
     tape = c->tape_int;
   }
-  stage_vjp(c, s, U, tape, lam_dUdt, 1.0, 0, lam_U, 1.0, lam_U, 0.0, nullptr, 0.0, nullptr);
+  stage_vjp(c, s, U, (const double*)c->Wc, tape, lam_dUdt, 1.0, 0, lam_U, 1.0, lam_U, 0.0, nullptr, 0.0, nullptr);
   return check_launch(c, "rhs_adjoint");
 }
 
-extern "C" int mpmc_rk_step_record(mpmc_ctx* c, double* U, double dt, uint32_t* tape, double* U_stages) {
+extern "C" int mpmc_rk_step_record(mpmc_ctx* c, double* U, double dt, uint32_t* tape, double* U_stages,
+                                   double* W_stages) {
   if (!c || !U || !U_stages) return fail(c, MPMC_INVALID_ARG, "rk_step_record: null argument");
+  if (W_stages && c->precision != MPMC_FP64)
+    return fail(c, MPMC_INVALID_ARG, "rk_step_record: W_stages needs an FP64 context");
   const KParams& P = c->P;
   const long long n = (long long)P.nv * P.ncell, nf = c->nface_total;
+  const size_t nw = mpmc_cache_doubles(c);
   double* U1 = U_stages;
   double* U2 = U_stages + n;
   cudaStream_t s = c->stream;
+  // the primitive cache just computed, kept as stage k's
+  auto keep = [&](int k) {
+    return !W_stages || cudaMemcpyAsync(W_stages + k * nw, c->Wc, nw * sizeof(double), cudaMemcpyDeviceToDevice,
+                                        s) == cudaSuccess;
+  };
   dt_gamma(c, s, U, dt, -1.0, nullptr);
+  if (!keep(0)) return fail(c, MPMC_CUDA_ERROR, "rk_step_record: cache copy");
   stage(c, s, U, U, 1.0, 0.0, 1.0, U1, nullptr, tape);
   prim(c, s, U1, nullptr);
+  if (!keep(1)) return fail(c, MPMC_CUDA_ERROR, "rk_step_record: cache copy");
   stage(c, s, U, U1, 0.75, 0.25, 0.25, U2, nullptr, tape ? tape + nf : nullptr);
   prim(c, s, U2, nullptr);
+  if (!keep(2)) return fail(c, MPMC_CUDA_ERROR, "rk_step_record: cache copy");
   stage(c, s, U, U2, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, U, nullptr, tape ? tape + 2 * nf : nullptr);
   c->faces_done += 3ull * c->nface_total;
   return check_launch(c, "rk_step_record");
 }
 
-extern "C" int mpmc_rk_step_adjoint(mpmc_ctx* c, const double* U_n, const double* U_stages, double dt,
-                                    const uint32_t* tape, const double* lam_next, double* lam_n) {
+extern "C" int mpmc_rk_step_adjoint(mpmc_ctx* c, const double* U_n, const double* U_stages, const double* W_stages,
+                                    double dt, const uint32_t* tape, const double* lam_next, double* lam_n) {
   if (!c || !U_n || !lam_next || !lam_n) return fail(c, MPMC_INVALID_ARG, "rk_step_adjoint: null argument");
+  if (W_stages && !U_stages) return fail(c, MPMC_INVALID_ARG, "rk_step_adjoint: W_stages without U_stages");
   int rc = ensure_adjoint(c);
   if (rc) return rc;
   const KParams& P = c->P;
@@ -566,21 +580,27 @@ extern "C" int mpmc_rk_step_adjoint(mpmc_ctx* c, const double* U_n, const double
     faces_only(c, s, U_n, U1, 0.75, 0.25, 0.25, tp + nf);
     prim(c, s, U2, nullptr);
     faces_only(c, s, U_n, U2, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, tp + 2 * nf);
-  } else {
+  } else if (!W_stages) {
     prim(c, s, U2, nullptr);
   }
   const uint32_t* T = tape ? tape : c->tape_int;
+  // the primitive cache of each stage state: kept by mpmc_rk_step_record, or
+  // recomputed into the context's cache just before its use
+  const size_t nw = mpmc_cache_doubles(c);
+  const double* Wc = c->Wc;
   // Eq. SSPRK3 reversed:
   //   lam2 = 2/3 lam3 + 2/3 dt L(U2)^T lam3
   //   lam1 = 1/4 lam2 + 1/4 dt L(U1)^T lam2
   //   lamn = 1/3 lam3 + 3/4 lam2 + lam1 + dt L(Un)^T lam1
   double* l2 = c->lamB;
   double* l1 = c->lamA;
-  stage_vjp(c, s, U2, T + 2 * nf, lam_next, 2.0 / 3.0, 1, l2, 2.0 / 3.0, lam_next, 0.0, nullptr, 0.0, nullptr);
-  prim(c, s, U1, nullptr);
-  stage_vjp(c, s, U1, T + nf, l2, 0.25, 1, l1, 0.25, l2, 0.0, nullptr, 0.0, nullptr);
-  prim(c, s, U_n, nullptr);
-  stage_vjp(c, s, U_n, T, l1, 1.0, 1, lam_n, 1.0 / 3.0, lam_next, 0.75, l2, 1.0, l1);
+  stage_vjp(c, s, U2, W_stages ? W_stages + 2 * nw : Wc, T + 2 * nf, lam_next, 2.0 / 3.0, 1, l2, 2.0 / 3.0,
+            lam_next, 0.0, nullptr, 0.0, nullptr);
+  if (!W_stages) prim(c, s, U1, nullptr);
+  stage_vjp(c, s, U1, W_stages ? W_stages + nw : Wc, T + nf, l2, 0.25, 1, l1, 0.25, l2, 0.0, nullptr, 0.0,
+            nullptr);
+  if (!W_stages) prim(c, s, U_n, nullptr);
+  stage_vjp(c, s, U_n, W_stages ? W_stages : Wc, T, l1, 1.0, 1, lam_n, 1.0 / 3.0, lam_next, 0.75, l2, 1.0, l1);
   return check_launch(c, "rk_step_adjoint");
 }
 

@@ -107,6 +107,16 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert h.value is None
 
 
+def test_null_context_queries_without_a_gpu(lib):
+    """The size queries answer 0 for a null context; the recording and
+    reverse steps reject it before any CUDA call."""
+    from paper_2504_14063_gb300 import binding as b
+    assert b.lib.mpmc_cache_doubles(None) == 0
+    assert b.lib.mpmc_ncells(None) == 0
+    assert b.lib.mpmc_rk_step_record(None, None, 0.0, None, None, None) == b.INVALID_ARG
+    assert b.lib.mpmc_rk_step_adjoint(None, None, None, None, 0.0, None, None, None) == b.INVALID_ARG
+
+
 def test_characteristic_boundaries_are_validated_without_a_gpu(lib):
     """MPMC_BC_CHAR (the header's value) is accepted along x only; the
     allocation-free entry refuses it before any CUDA call."""

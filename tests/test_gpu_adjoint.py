@@ -92,6 +92,15 @@ def test_rk_step_adjoint_dot_product(mp, name, make):
     assert np.array_equal(lam_r, lam_n)
     lam_s = ctx.rk_step_adjoint(Ug, _cuda(lam), dt=dt, stages=stages).cpu().numpy()
     assert np.array_equal(lam_s, lam_n)
+    # the primitive caches kept by the recording step stand in for their
+    # recomputation, bit for bit
+    wst = torch.empty(3 * ctx.cache_doubles, dtype=torch.float64, device="cuda")
+    stages_w = ctx.rk_step_record(Ug.clone(), dt, tape, wstages=wst)
+    assert torch.equal(stages_w, stages)
+    lam_w = ctx.rk_step_adjoint(Ug, _cuda(lam), dt=dt, tape=tape, stages=stages_w, wstages=wst).cpu().numpy()
+    assert np.array_equal(lam_w, lam_n)
+    with pytest.raises(mp.MpmcError):
+        ctx.rk_step_adjoint(Ug, _cuda(lam), dt=dt, tape=tape, wstages=wst)
     # in place
     L = _cuda(lam)
     ctx.rk_step_adjoint(Ug, L, dt=dt, lam_n=L)
