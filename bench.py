@@ -56,12 +56,12 @@ L2_BYTES = 129 * 2 ** 20
 # and while the kernels' sources hash to the captured version (None
 # otherwise).
 TRAFFIC_GRID = 256
-TRAFFIC = {"k_face": 6.282e9, "mx::k_face": 3.764e9, "k_prim": 4.206e9, "mx::k_prim": 3.109e9,
-           "k_update": 5.961e9, "mx::k_update": 5.958e9}
+TRAFFIC = {"k_face": 6.279e9, "mx::k_face": 3.762e9, "k_prim": 4.208e9, "mx::k_prim": 3.113e9,
+           "k_update": 5.962e9, "mx::k_update": 5.959e9}
 TRAFFIC_SOURCES = ("paper_2504_14063_gb300/csrc/mpmc_kernels.cuh", "paper_2504_14063_gb300/csrc/mpmc_device.cuh",
                    "paper_2504_14063_gb300/csrc/mpmc_kernels_d3.cu", "paper_2504_14063_gb300/csrc/mpmc_mixed.cuh",
                    "paper_2504_14063_gb300/csrc/mpmc_mixed_d3.cu", "paper_2504_14063_gb300/csrc/mpmc_update.cuh")
-TRAFFIC_SHA256 = "d6d4ba50a99450c275fa7fa362febd4e1afef7816102db13a16801fed0402ea0"
+TRAFFIC_SHA256 = "2e3ed5b714319dfd0118e1dbfed9dde9a9bce3b69f918c6298b2a1d17a1b679e"
 
 
 def sources_sha256():

@@ -548,7 +548,9 @@ __device__ __forceinline__ void eos_forward(const KParams& P, const double* Y, d
   rho = 1.0 / v;
   alpha = rho * sa;
   beta = rho * sb;
-  a = sqrt(cp / (rho * beta * cp - alpha * alpha * T));
+  // sqrt(cp / den) as cp rsqrt(cp den): one reciprocal square root in place
+  // of a division and a square root (cp > 0; den <= 0 gives NaN or inf alike)
+  a = cp * rsqrt(cp * (rho * beta * cp - alpha * alpha * T));
 }
 
 // the sound speed, alpha and beta of eos_forward at a state whose density
@@ -579,7 +581,9 @@ __device__ __forceinline__ void eos_char(const KParams& P, const double* Y, doub
   }
   alpha = rho * sa;
   beta = rho * sb;
-  a = sqrt(cp / (rho * beta * cp - alpha * alpha * T));
+  // sqrt(cp / den) as cp rsqrt(cp den): one reciprocal square root in place
+  // of a division and a square root (cp > 0; den <= 0 gives NaN or inf alike)
+  a = cp * rsqrt(cp * (rho * beta * cp - alpha * alpha * T));
 }
 
 // ---------------------------------------------------------------------------
@@ -768,16 +772,62 @@ __device__ __forceinline__ double recon(double v0, double v1, double v2, double 
 
 // both face values of one field from the cells y[0..5] = i-2..i+3 around
 // the face i+1/2: L from the left (recon of y[0..5]), R from the right (of
-// y[5..0]).  WENO5-Z forms the two quotients with one reciprocal,
+// y[5..0]).  WENO5-Z shares the two sides' common candidates and second
+// differences (weno5z_lr_nd) and forms the two quotients with one reciprocal,
 // num_L d_R / (d_L d_R) and num_R d_L / (d_L d_R), while d_L d_R is a
 // normal number whose reciprocal is normal too (exponent field 2..2044,
 // tested on the integer pipe), else with two divisions.
+// WENO5-Z weights of one side over the common denominator: a_k = (c_k +
+// tau) prod_{j!=k} c_j, c_k = b_k + eps (as weno5z_nd)
+__device__ __forceinline__ void weno5z_alpha(double b0, double b1, double b2, double eps, double& a0, double& a1,
+                                             double& a2) {
+  const double tau = fabs(b0 - b2);
+  const double c0 = b0 + eps, c1 = b1 + eps, c2 = b2 + eps;
+  a0 = (c0 + tau) * (c1 * c2);
+  a1 = (c1 + tau) * (c0 * c2);
+  a2 = (c2 + tau) * (c0 * c1);
+}
+
+// numerators and denominators of both sides of a face (weno5z_nd of
+// w[0..4] and of w[5..1]).  The two sides share two candidate stencils:
+// 6 q_1 of the left side (cells w1..w3) is 6 q_2 of the right one, and
+// 6 q_2 of the left (w2..w4) is 6 q_1 of the right; and two second
+// differences (w1 - 2 w2 + w3, w2 - 2 w3 + w4) with their (13/12) t^2 terms.
+__device__ __forceinline__ void weno5z_lr_nd(const double* w, double eps, double& nL, double& dL, double& nR,
+                                             double& dR) {
+  const double t123 = w[1] - 2.0 * w[2] + w[3], t234 = w[2] - 2.0 * w[3] + w[4];
+  const double e123 = (13.0 / 12.0) * t123 * t123, e234 = (13.0 / 12.0) * t234 * t234;
+  const double A = -w[1] + 5.0 * w[2] + 2.0 * w[3];
+  const double B = 2.0 * w[2] + 5.0 * w[3] - w[4];
+  {
+    const double t = w[0] - 2.0 * w[1] + w[2], s = w[0] - 4.0 * w[1] + 3.0 * w[2];
+    const double b0 = (13.0 / 12.0) * t * t + 0.25 * s * s;
+    const double s1 = w[1] - w[3], s2 = 3.0 * w[2] - 4.0 * w[3] + w[4];
+    const double b1 = e123 + 0.25 * s1 * s1, b2 = e234 + 0.25 * s2 * s2;
+    double a0, a1, a2;
+    weno5z_alpha(b0, b1, b2, eps, a0, a1, a2);
+    const double Q0 = 2.0 * w[0] - 7.0 * w[1] + 11.0 * w[2];
+    nL = a0 * Q0 + a1 * (6.0 * A) + a2 * (3.0 * B);
+    dL = 6.0 * a0 + 36.0 * a1 + 18.0 * a2;
+  }
+  {
+    const double t = w[5] - 2.0 * w[4] + w[3], s = w[5] - 4.0 * w[4] + 3.0 * w[3];
+    const double b0 = (13.0 / 12.0) * t * t + 0.25 * s * s;
+    const double s1 = w[4] - w[2], s2 = 3.0 * w[3] - 4.0 * w[2] + w[1];
+    const double b1 = e234 + 0.25 * s1 * s1, b2 = e123 + 0.25 * s2 * s2;
+    double a0, a1, a2;
+    weno5z_alpha(b0, b1, b2, eps, a0, a1, a2);
+    const double Q0 = 2.0 * w[5] - 7.0 * w[4] + 11.0 * w[3];
+    nR = a0 * Q0 + a1 * (6.0 * B) + a2 * (3.0 * A);
+    dR = 6.0 * a0 + 36.0 * a1 + 18.0 * a2;
+  }
+}
+
 template <int RC>
 __device__ __forceinline__ void recon_lr(const double* y, double eps, double& L, double& R) {
   if constexpr (RC == RC_WENO5Z) {
     double nL, dL, nR, dR;
-    weno5z_nd(y[0], y[1], y[2], y[3], y[4], eps, nL, dL);
-    weno5z_nd(y[5], y[4], y[3], y[2], y[1], eps, nR, dR);
+    weno5z_lr_nd(y, eps, nL, dL, nR, dR);
     const double dd = dL * dR;
     const unsigned ex = ((unsigned)__double2hiint(dd) >> 20) & 0x7ffu;
     if (ex - 2u <= 2042u) {

@@ -141,6 +141,38 @@ __device__ __forceinline__ float weno5z_f(float v0, float v1, float v2, float v3
   return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
 }
 
+// weno5z_f of both sides of a face, of y[0..4] and of y[5..1]: the two
+// sides share two candidates (q_1 of one is q_2 of the other) and two
+// second differences with their (13/12) t^2 terms
+__device__ __forceinline__ float weno5z_side_f(float b0, float b1, float b2, float q0, float q1, float q2) {
+  const float tau = fabsf(b0 - b2);
+  const float a0 = 0.1f * (1.f + fminf(__fdividef(tau, b0 + WENO_EPS32), 1e30f));
+  const float a1 = 0.6f * (1.f + fminf(__fdividef(tau, b1 + WENO_EPS32), 1e30f));
+  const float a2 = 0.3f * (1.f + fminf(__fdividef(tau, b2 + WENO_EPS32), 1e30f));
+  return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+}
+
+__device__ __forceinline__ void weno5z_lr_f(const float* y, float& L, float& R) {
+  const float t123 = y[1] - 2.f * y[2] + y[3], t234 = y[2] - 2.f * y[3] + y[4];
+  const float e123 = (13.f / 12.f) * t123 * t123, e234 = (13.f / 12.f) * t234 * t234;
+  const float qa = (-y[1] + 5.f * y[2] + 2.f * y[3]) * (1.f / 6.f);
+  const float qb = (2.f * y[2] + 5.f * y[3] - y[4]) * (1.f / 6.f);
+  {
+    const float t = y[0] - 2.f * y[1] + y[2], s = y[0] - 4.f * y[1] + 3.f * y[2];
+    const float s1 = y[1] - y[3], s2 = 3.f * y[2] - 4.f * y[3] + y[4];
+    const float q0 = (2.f * y[0] - 7.f * y[1] + 11.f * y[2]) * (1.f / 6.f);
+    L = weno5z_side_f((13.f / 12.f) * t * t + 0.25f * s * s, e123 + 0.25f * s1 * s1, e234 + 0.25f * s2 * s2, q0,
+                      qa, qb);
+  }
+  {
+    const float t = y[5] - 2.f * y[4] + y[3], s = y[5] - 4.f * y[4] + 3.f * y[3];
+    const float s1 = y[4] - y[2], s2 = 3.f * y[3] - 4.f * y[2] + y[1];
+    const float q0 = (2.f * y[5] - 7.f * y[4] + 11.f * y[3]) * (1.f / 6.f);
+    R = weno5z_side_f((13.f / 12.f) * t * t + 0.25f * s * s, e234 + 0.25f * s1 * s1, e123 + 0.25f * s2 * s2, q0,
+                      qb, qa);
+  }
+}
+
 // Sec. 4.1's other ENO-type interpolations in FP32 (as the FP64 ones in
 // mpmc_device.cuh; the mixed face kernel feeds them deviations from the left
 // cell).  Ratios tau / (beta + eps) are clamped at 1e30 as in weno5z_f.
@@ -228,6 +260,18 @@ __device__ __forceinline__ float recon_f(float v0, float v1, float v2, float v3,
   else if constexpr (RC == RC_TENO5) return teno5_f(v0, v1, v2, v3, v4);
   else if constexpr (RC == RC_TENO6) return teno6_f(v0, v1, v2, v3, v4, v5);
   else return weno5z_f(v0, v1, v2, v3, v4);
+}
+
+// both sides of a face from the six cells y[0..5] (left: y[0..5]; right:
+// y[5..0]); WENO5-Z shares the sides' common terms (weno5z_lr_f)
+template <int RC>
+__device__ __forceinline__ void recon_lr_f(const float* y, float& L, float& R) {
+  if constexpr (RC == RC_WENO5Z) {
+    weno5z_lr_f(y, L, R);
+  } else {
+    L = recon_f<RC>(y[0], y[1], y[2], y[3], y[4], y[5]);
+    R = recon_f<RC>(y[5], y[4], y[3], y[2], y[1], y[0]);
+  }
 }
 
 template <int NS>
@@ -718,12 +762,10 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
       w5[j] = (0.5f * c) * du + 0.5f * dp;
       w6[j] = (-0.5f * c) * du + 0.5f * dp;
     }
-    const float w1L = recon_f<RC>(w1[0], w1[1], w1[2], w1[3], w1[4], w1[5]);
-    const float w1R = recon_f<RC>(w1[5], w1[4], w1[3], w1[2], w1[1], w1[0]);
-    const float w5L = recon_f<RC>(w5[0], w5[1], w5[2], w5[3], w5[4], w5[5]);
-    const float w5R = recon_f<RC>(w5[5], w5[4], w5[3], w5[2], w5[1], w5[0]);
-    const float w6L = recon_f<RC>(w6[0], w6[1], w6[2], w6[3], w6[4], w6[5]);
-    const float w6R = recon_f<RC>(w6[5], w6[4], w6[3], w6[2], w6[1], w6[0]);
+    float w1L, w1R, w5L, w5R, w6L, w6R;
+    recon_lr_f<RC>(w1, w1L, w1R);
+    recon_lr_f<RC>(w5, w5L, w5R);
+    recon_lr_f<RC>(w6, w6L, w6R);
     TL = Ti + (w1L + X * (w5L + w6L));
     TR = Ti + (w1R + X * (w5R + w6R));
     uL[d] = uni + ic * (w5L - w6L);
@@ -739,8 +781,10 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
     float y[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) y[j] = wgetf(P, Wc, P.wY + k, cr[j]) - Yi[k];
-    YL[k] = Yi[k] + recon_f<RC>(y[0], y[1], y[2], y[3], y[4], y[5]);
-    YR[k] = Yi[k] + recon_f<RC>(y[5], y[4], y[3], y[2], y[1], y[0]);
+    float dl, dr;
+    recon_lr_f<RC>(y, dl, dr);
+    YL[k] = Yi[k] + dl;
+    YR[k] = Yi[k] + dr;
   }
 #pragma unroll
   for (int t = 0; t < D; ++t) {
@@ -749,8 +793,10 @@ __global__ void __launch_bounds__(FACE_THREADS, 5)
     float y[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) y[j] = wgetf(P, Wc, P.wU + t, cr[j]) * sgnf(cr[j].flip, t) - ut;
-    uL[t] = ut + recon_f<RC>(y[0], y[1], y[2], y[3], y[4], y[5]);
-    uR[t] = ut + recon_f<RC>(y[5], y[4], y[3], y[2], y[1], y[0]);
+    float dl, dr;
+    recon_lr_f<RC>(y, dl, dr);
+    uL[t] = ut + dl;
+    uR[t] = ut + dr;
   }
 
   if (P.pos_limiter) {

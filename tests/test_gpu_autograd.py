@@ -88,6 +88,16 @@ def _J_of_amps(mp, ag, ctx, p, amps, nsteps, probe, dts=None):
 
 
 def test_fourier_amplitude_gradient_vs_central_differences(mp, ag):
+    """Central differences away from switching points.  The discrete map has
+    jumps where a limiter decision flips (of order 1e-10 of J here, e.g. the
+    mass-fraction limiter's rounding-level threshold); a flip inside the
+    interval [-h, h] of one component moves that component's difference
+    quotient by jump / 2h, at one step size and not at the others (measured:
+    6e-4 of the gradient at h = 1e-6, 1e-5 at h = 3e-6 and 1e-5).  So each
+    component is differenced at h = 1e-5, 3e-6 and 1e-6, and the adjoint is
+    compared with the median of the three (a flip spoils at most the one
+    whose interval holds it); every step size must still agree with the
+    adjoint on all but at most two components."""
     n, nsteps, G = 64, 60, 400.0
     p = _amplitude_problem(n, G)
     ctx = mp.Context(p)
@@ -98,21 +108,29 @@ def test_fourier_amplitude_gradient_vs_central_differences(mp, ag):
     grad, = torch.autograd.grad(J, amps)
     grad = grad.cpu().numpy()
     dts = dts.cpu().tolist()
-    h = 1e-6
-    fd = np.zeros_like(amps0)
-    for m in range(8):
-        for c in range(2):
-            e = np.zeros_like(amps0)
-            e[m, c] = h
-            Jp = _J_of_amps(mp, ag, ctx, p, torch.from_numpy(amps0 + e).cuda(), nsteps, probe, dts)[1]
-            Jm = _J_of_amps(mp, ag, ctx, p, torch.from_numpy(amps0 - e).cuda(), nsteps, probe, dts)[1]
-            fd[m, c] = (Jp - Jm) / (2 * h)
-    err = np.abs(grad - fd).max() / np.abs(fd).max()
-    print(f"dJ/d(amplitudes): max |adjoint - central difference| / max |gradient| = {err:.2e}")
+    hs = (1e-5, 3e-6, 1e-6)
+    fd = np.zeros((len(hs),) + amps0.shape)
+    for q, h in enumerate(hs):
+        for m in range(8):
+            for c in range(2):
+                e = np.zeros_like(amps0)
+                e[m, c] = h
+                Jp = _J_of_amps(mp, ag, ctx, p, torch.from_numpy(amps0 + e).cuda(), nsteps, probe, dts)[1]
+                Jm = _J_of_amps(mp, ag, ctx, p, torch.from_numpy(amps0 - e).cuda(), nsteps, probe, dts)[1]
+                fd[q, m, c] = (Jp - Jm) / (2 * h)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    med = np.median(fd, axis=0)
+    err = np.abs(grad - med).max() / scale
+    per_h = np.abs(grad[None] - fd) / scale
+    print(f"dJ/d(amplitudes): max |adjoint - median central difference| / max |gradient| = {err:.2e}")
+    for q, h in enumerate(hs):
+        print(f"  h = {h:.0e}: max {per_h[q].max():.2e}, components above 1e-4: {int((per_h[q] > 1e-4).sum())}")
     print("adjoint", np.array2string(grad.ravel(), precision=4))
-    print("fd     ", np.array2string(fd.ravel(), precision=4))
-    assert np.abs(fd).max() > 0
+    print("fd     ", np.array2string(med.ravel(), precision=4))
     assert err < 1e-4
+    for q in range(len(hs)):
+        assert (per_h[q] > 1e-4).sum() <= 2
 
 
 def test_fourier_amplitude_gradient_vs_oracle_tangent(mp, ag):
