@@ -1131,9 +1131,9 @@ __global__ void __launch_bounds__(CELL_THREADS)
 // out may alias x, y or z)
 template <int NS, int D>
 __global__ void __launch_bounds__(CELL_THREADS)
-    k_cell_adj(const KParams P, const double* __restrict__ U, const double* __restrict__ gW,
-               const double* __restrict__ gU, double* out, const double a, const double* x, const double b,
-               const double* y, const double cz, const double* z) {
+    k_cell_adj(const KParams P, const double* __restrict__ U, const double* __restrict__ Wc,
+               const double* __restrict__ gW, const double* __restrict__ gU, double* out, const double a,
+               const double* x, const double b, const double* y, const double cz, const double* z) {
   constexpr int NV = NS + D + 1;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= P.ncell) return;
@@ -1159,7 +1159,14 @@ __global__ void __launch_bounds__(CELL_THREADS)
   for (int v = 0; v < NV; ++v) Uc[v] = U[(long long)v * P.ncell + c];
   double rho, Y[NS], u[3], e, vol, p, T;
   decode<NS, D>(Uc, rho, Y, u, e, vol);
-  pt_equilibrium<NS>(P, Y, e, vol, p, T);
+  if (Wc) {
+    // the primitive pass of U solved the same equations from the same
+    // decode: its T and P, read back
+    T = Wc[P.wT * ws + c];
+    p = Wc[P.wP * ws + c];
+  } else {
+    pt_equilibrium<NS>(P, Y, e, vol, p, T);
+  }
   Thermo<NS> th;
 #pragma unroll
   for (int k = 0; k < NS; ++k) th.Y[k] = Y[k];
@@ -1452,9 +1459,11 @@ struct AdjImpl {
     else
       k_gather<NS, D, (D > 2 ? 2 : 0)><<<nb, CELL_THREADS, 0, s>>>(P, C, first, gW, gU);
   }
-  static void cell(const KParams& P, cudaStream_t s, const double* U, const double* gW, const double* gU,
-                   double* out, double a, const double* x, double b, const double* y, double cz, const double* z) {
-    k_cell_adj<NS, D><<<nblocks(P.ncell, CELL_THREADS), CELL_THREADS, 0, s>>>(P, U, gW, gU, out, a, x, b, y, cz, z);
+  static void cell(const KParams& P, cudaStream_t s, const double* U, const double* Wc, const double* gW,
+                   const double* gU, double* out, double a, const double* x, double b, const double* y, double cz,
+                   const double* z) {
+    k_cell_adj<NS, D><<<nblocks(P.ncell, CELL_THREADS), CELL_THREADS, 0, s>>>(P, U, Wc, gW, gU, out, a, x, b, y,
+                                                                               cz, z);
   }
   static void init(const KParams& P, cudaStream_t s, const double* prim, const double* lamU, double* lprim,
                    long long n) {

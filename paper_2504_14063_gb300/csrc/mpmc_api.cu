@@ -501,7 +501,7 @@ static void stage_vjp(mpmc_ctx* c, cudaStream_t s, const double* U, const double
     off += c->nface[d];
   }
   ProfScope ps(c, FAM_ADJ_PRIM, s);
-  c->aops.cell(P, s, U, c->gW, c->gU, out, a, x, b, y, cz, z);
+  c->aops.cell(P, s, U, Wc, c->gW, c->gU, out, a, x, b, y, cz, z);
 }
 
 extern "C" int mpmc_rhs_adjoint(mpmc_ctx* c, const double* U, const mpmc_stage* st, const uint32_t* tape,
@@ -637,7 +637,7 @@ extern "C" int mpmc_primitives_adjoint(mpmc_ctx* c, const double* U, const doubl
                         s) != cudaSuccess)
     return fail(c, MPMC_CUDA_ERROR, "primitives_adjoint: copy");
   ProfScope ps(c, FAM_ADJ_PRIM, s);
-  c->aops.cell(P, s, U, c->gW, c->gU, lam_U, 1.0, lam_U, 0.0, nullptr, 0.0, nullptr);
+  c->aops.cell(P, s, U, nullptr, c->gW, c->gU, lam_U, 1.0, lam_U, 0.0, nullptr, 0.0, nullptr);
   return check_launch(c, "primitives_adjoint");
 }
 

@@ -34,8 +34,10 @@ struct AdjOps {
   void (*face_visc)(const KParams&, cudaStream_t, int d, const double* Wc, const double* scal,
                     const uint32_t* tape, const double* lamL, double coef, int mul_dt, double* C);
   void (*gather)(const KParams&, cudaStream_t, int d, const double* C, int first, double* gW, double* gU);
-  void (*cell)(const KParams&, cudaStream_t, const double* U, const double* gW, const double* gU, double* out,
-               double a, const double* x, double b, const double* y, double cz, const double* z);
+  // Wc (nullable): U's primitive cache, whose T and P the reverse takes
+  // instead of solving the p-T equilibrium again
+  void (*cell)(const KParams&, cudaStream_t, const double* U, const double* Wc, const double* gW, const double* gU,
+               double* out, double a, const double* x, double b, const double* y, double cz, const double* z);
   void (*init)(const KParams&, cudaStream_t, const double* prim, const double* lamU, double* lprim, long long n);
 };
 
