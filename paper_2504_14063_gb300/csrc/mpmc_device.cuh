@@ -432,7 +432,31 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
     }
     double f, df, d2f, mag;
     bool conv = false;
-    for (int it = 0; it < 100; ++it) {
+    if (F32OUT) {
+      // FP32 output: one Newton step from the FP32 root suffices (its error,
+      // dxn^2 / (x - lo) <= 1e-12 (x - lo), is below FP32 rounding of P);
+      // the reciprocals 1/(x + Pinf_k) from an FP32 seed and one Newton
+      // refinement (relative error ~1e-14).  A larger step, or a seed that
+      // is not a normal number, falls through to the iteration below.
+      double fn = -Cv, dfn = 0.0;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        if (Y[k] != 0.0) {
+          const double y = x + P.pinf[k];
+          double r = (double)__frcp_rn((float)y);
+          r = r * (2.0 - y * r);
+          const double t = w[k] * r;
+          fn += t;
+          dfn -= t * r;
+        }
+      }
+      const double xn = x - fn / dfn;
+      if (xn > lo && fabs(xn - x) <= 1e-6 * (x - lo)) {
+        x = xn;
+        conv = true;
+      }
+    }
+    for (int it = 0; it < 100 && !conv; ++it) {
       pt_residual<NS>(P, Y, w, Cv, x, f, df, d2f, mag);
       if (f > 0.0) a = x;
       else bb = x;
