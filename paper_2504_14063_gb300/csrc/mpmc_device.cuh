@@ -233,9 +233,9 @@ __device__ __forceinline__ void pt_residual(const KParams& P, const double* Y, c
   bool have_rg = false;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    if (Y[k] != 0.0) {
+    if (nonzero(Y[k])) {
       double r;
-      if (P.pinf[k] == 0.0) {
+      if (!nonzero(P.pinf[k])) {
         if (!have_rg) {
           rg = 1.0 / x;
           have_rg = true;
@@ -309,7 +309,7 @@ __device__ __forceinline__ double pt_start_f32(const KParams& P, const double* Y
                                                double lo, double x0) {
   float wf[NS];
 #pragma unroll
-  for (int k = 0; k < NS; ++k) wf[k] = Y[k] != 0.0 ? narrow(w[k]) : 0.f;
+  for (int k = 0; k < NS; ++k) wf[k] = nonzero(Y[k]) ? narrow(w[k]) : 0.f;
   const float cvf = narrow(Cv), lof = narrow(lo);
   float x = narrow(x0), a = lof, b = INFINITY;
   for (int it = 0; it < 40; ++it) {
@@ -317,7 +317,7 @@ __device__ __forceinline__ double pt_start_f32(const KParams& P, const double* Y
     bool have_rg = false;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      if (Y[k] != 0.0) {
+      if (nonzero(Y[k])) {
         float r;
         if (P.f32.pinf[k] == 0.f) {
           if (!have_rg) {
@@ -382,9 +382,9 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
   bool multi = false, gas = false;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    if (Y[k] > 0.0) {
+    if (positive(Y[k])) {
       pmin = fmin(pmin, P.pinf[k]);
-      if (P.pinf[k] > 0.0) {
+      if (positive(P.pinf[k])) {
         if (pl < 0.0) pl = P.pinf[k];
         else if (P.pinf[k] != pl) multi = true;
         Rl = add_<EX>(Rl, mul_<EX>(Y[k], P.Rk[k]));
@@ -415,7 +415,7 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
     const double lo = -pmin;
     double w[NS];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) w[k] = Y[k] != 0.0 ? Y[k] * P.Rk[k] * (Ep - P.pinf[k]) : 0.0;
+    for (int k = 0; k < NS; ++k) w[k] = nonzero(Y[k]) ? Y[k] * P.Rk[k] * (Ep - P.pinf[k]) : 0.0;
     double a = lo, bb = INFINITY;
     double x;
     if (guess > lo && guess < 1e300) {
@@ -441,7 +441,7 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
       double fn = -Cv, dfn = 0.0;
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        if (Y[k] != 0.0) {
+        if (nonzero(Y[k])) {
           const double y = x + P.pinf[k];
           double r = (double)__frcp_rn((float)y);
           r = r * (2.0 - y * r);
@@ -458,14 +458,14 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
     }
     for (int it = 0; it < 100 && !conv; ++it) {
       pt_residual<NS>(P, Y, w, Cv, x, f, df, d2f, mag);
-      if (f > 0.0) a = x;
+      if (positive(f)) a = x;
       else bb = x;
       // the residual is a difference of terms of size mag: once it is at its
       // own rounding level, x is the root as far as the data determine it
       // (a stiff liquid with trace gas: the iterate would wander in that band)
       if (fabs(f) <= 16.0 * 2.220446049250313e-16 * mag) { conv = true; break; }
       const double hd = 2.0 * df * df - f * d2f;
-      double xn = hd > 0.0 ? x - 2.0 * f * df / hd : x - f / df;
+      double xn = positive(hd) ? x - 2.0 * f * df / hd : x - f / df;
       if (!(xn > a && xn < bb)) {
         if (bb == INFINITY) {
           xn = x + fmax(x - lo, 1.0);       // root above every point tried so far
@@ -495,7 +495,7 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
       float den = 0.f;
 #pragma unroll
       for (int k = 0; k < NS; ++k)
-        if (Y[k] != 0.0) {
+        if (nonzero(Y[k])) {
           const float r = P.f32.pinf[k] == 0.f
                               ? 1.f
                               : __fdividef(pf + P.f32.gam[k] * P.f32.pinf[k], pf + P.f32.pinf[k]);
@@ -514,8 +514,8 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
     double g = 0.0, l = 0.0;
 #pragma unroll
     for (int k = 0; k < NS; ++k)
-      if (Y[k] != 0.0) {
-        if (P.pinf[k] == 0.0)
+      if (nonzero(Y[k])) {
+        if (!nonzero(P.pinf[k]))
           g += Y[k] * P.cv[k];
         else if (P.pinf[k] == pl)
           l += Y[k] * P.cv[k] * (p + P.gam[k] * pl);
@@ -528,8 +528,8 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
   double den = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k)
-    if (Y[k] != 0.0) {
-      if (!EX && P.pinf[k] == 0.0)
+    if (nonzero(Y[k])) {
+      if (!EX && !nonzero(P.pinf[k]))
         den += Y[k] * P.cv[k];   // (P + gamma Pinf) / (P + Pinf) = 1
       else
         den = add_<EX>(den, mul_<EX>(mul_<EX>(Y[k], P.cv[k]), add_<EX>(p, mul_<EX>(P.gam[k], P.pinf[k]))) /
@@ -549,10 +549,10 @@ __device__ __forceinline__ void eos_forward(const KParams& P, const double* Y, d
   e = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    if (Y[k] != 0.0) {
+    if (nonzero(Y[k])) {
       // ideal-gas species share 1/(P + 0) = 1/P (the same value bit for bit)
       double r;
-      if (P.pinf[k] == 0.0) {
+      if (!nonzero(P.pinf[k])) {
         if (!have_rg) {
           rg = 1.0 / p;
           have_rg = true;
@@ -587,9 +587,9 @@ __device__ __forceinline__ void eos_char(const KParams& P, const double* Y, doub
   bool have_rg = false;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    if (Y[k] != 0.0) {
+    if (nonzero(Y[k])) {
       double r;
-      if (P.pinf[k] == 0.0) {
+      if (!nonzero(P.pinf[k])) {
         if (!have_rg) {
           rg = 1.0 / p;
           have_rg = true;
@@ -953,14 +953,14 @@ __device__ __forceinline__ bool admissible_bq(const double* b, const double* q, 
   }
   // (without covolumes or reference energies the b and q terms are zero:
   // they are skipped, not evaluated as 1 - 0 and x - 0)
-  bool ok = rho > 0.0 && (!has_b || (1.0 - sb) > 0.0);
+  bool ok = positive(rho) && (!has_b || positive(1.0 - sb));
 #pragma unroll
   for (int k = 0; k < NS; ++k) ok = ok && (U[k] >= -YTOL * rho);
   double mm = 0.0;
 #pragma unroll
   for (int d = 0; d < D; ++d) mm += U[NS + d] * U[NS + d];
   const double ei = rho * U[NS + D] - 0.5 * mm;
-  return ok && ((has_q ? ei - rho * sq : ei) > 0.0);
+  return ok && positive(has_q ? ei - rho * sq : ei);
 }
 
 template <int NS, int D>

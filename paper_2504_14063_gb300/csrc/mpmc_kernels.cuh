@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
   bool ok = Tg > 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k)
-    if (Yg[k] > 0.0 && !(Pg + P.pinf[k] > 0.0)) ok = false;
+    if (positive(Yg[k]) && !positive(Pg + P.pinf[k])) ok = false;
   double Ug[NV];
   if (ok) {
     State<NS> st;
@@ -409,8 +409,8 @@ __global__ void __launch_bounds__(FACE_THREADS)
     bool okL = true, okR = true;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      if (YL[k] > 0.0 && !(PL + P.pinf[k] > 0.0)) okL = false;
-      if (YR[k] > 0.0 && !(PR + P.pinf[k] > 0.0)) okR = false;
+      if (positive(YL[k]) && !positive(PL + P.pinf[k])) okL = false;
+      if (positive(YR[k]) && !positive(PR + P.pinf[k])) okR = false;
     }
     if (!okL) { PL = Pi; fl |= F_THETA_P_L; }
     if (!okR) { PR = Pj; fl |= F_THETA_P_R; }

@@ -11,7 +11,8 @@
 // subnormal results, infinities and NaN take the hardware conversion, which
 // computes the same rounding.
 //
-// Host-compilable so that a host test can compare it with the C cast.
+// Host-compilable so that a host test can compare it with the C cast (and
+// the zero / sign tests below with the C comparisons).
 #pragma once
 #include <cstdint>
 #include <cstring>
@@ -52,6 +53,26 @@ MPMC_HD2 float narrow(double x) {
   std::memcpy(&f, &r, sizeof f);
   return f;
 #endif
+}
+
+MPMC_HD2 uint64_t bits_of(double x) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(x);
+#else
+  uint64_t b;
+  std::memcpy(&b, &x, sizeof b);
+  return b;
+#endif
+}
+
+// y != 0 and y > 0 from the bits, on the integer pipes (an FP64 comparison
+// issues on the FP64 pipe, which binds the FP64 kernels); the same results
+// as the comparisons for every input: +-0 is zero, NaN is nonzero and not
+// positive, +inf is positive
+MPMC_HD2 bool nonzero(double y) { return (bits_of(y) << 1) != 0ull; }
+MPMC_HD2 bool positive(double y) {
+  const int64_t b = (int64_t)bits_of(y);
+  return b > 0 && b <= (int64_t)0x7ff0000000000000ull;
 }
 
 }  // namespace mpmc

@@ -3,7 +3,10 @@ primitive pass uses (csrc/mpmc_narrow.h): compiled with the host compiler
 and compared bit for bit with the C conversion (round to nearest, ties to
 even) on random doubles over the whole exponent range, exact ties of both
 parities, and the boundaries (the largest finite FP32 and the carry into
-infinity, the smallest normal, zeros, infinities, NaN)."""
+infinity, the smallest normal, zeros, infinities, NaN).  The same header's
+integer-pipe zero and sign tests (nonzero, positive) are compared with the C
+comparisons on random bit patterns of every class (normal, subnormal, zero,
+infinity, NaN) and the special values."""
 import os
 import shutil
 import subprocess
@@ -59,6 +62,21 @@ int main() {
                          1.0, 1.0 + std::ldexp(1.0, -24), 1.0 + std::ldexp(1.0, -24) + std::ldexp(1.0, -52),
                          1.0 + 3 * std::ldexp(1.0, -24), 0.1, 300.0, 101325.0, 6e8};
   for (double x : edge) check(x);
+  // the integer-pipe zero and sign tests against the comparisons: random
+  // bit patterns of every class, and the special values
+  for (int i = 0; i < 4000000; ++i) {
+    const uint64_t u = rnd();
+    const double xs[] = {from_bits(u), from_bits(u & 0x800fffffffffffffull), from_bits(u | 0x7ff0000000000000ull)};
+    for (double x : xs) {
+      ++n;
+      if (mpmc::nonzero(x) != (x != 0.0) || mpmc::positive(x) != (x > 0.0)) ++bad;
+    }
+  }
+  for (double x : edge) {
+    ++n;
+    if (mpmc::nonzero(x) != (x != 0.0) || mpmc::positive(x) != (x > 0.0)) ++bad;
+    if (mpmc::nonzero(-x) != (-x != 0.0) || mpmc::positive(-x) != (-x > 0.0)) ++bad;
+  }
   std::printf("%llu %llu\n", bad, n);
   return bad != 0;
 }
