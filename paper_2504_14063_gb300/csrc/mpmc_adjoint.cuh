@@ -204,7 +204,7 @@ __device__ __forceinline__ void thermo_fwd(const KParams& P, Thermo<NS>& t) {
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     t.r[k] = 1.0 / (t.p + P.pinf[k]);
-    if (t.Y[k] != 0.0) {
+    if (nonzero(t.Y[k])) {
       const double RT = P.Rk[k] * t.T;
       t.v += t.Y[k] * (RT * t.r[k] + P.b[k]);
       t.e += t.Y[k] * (P.cv[k] * t.T * (t.p + P.gam[k] * P.pinf[k]) * t.r[k] + P.q[k]);
@@ -226,7 +226,7 @@ __device__ __forceinline__ void thermo_rev(const KParams& P, const Thermo<NS>& t
                                            double lal, double lbe, double* lY, double& lp, double& lT) {
   // a = sqrt(cp / den)
   double lcp = 0.0, lden = 0.0;
-  if (la != 0.0) {
+  if (nonzero(la)) {
     const double g = la * 0.5 / t.a, iden = 1.0 / t.den;
     lcp += g * iden;
     lden -= g * t.cp * iden * iden;
@@ -244,7 +244,7 @@ __device__ __forceinline__ void thermo_rev(const KParams& P, const Thermo<NS>& t
   const double lv = -lrho * t.rho * t.rho;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    if (t.Y[k] == 0.0) continue;
+    if (!nonzero(t.Y[k])) continue;
     const double r = t.r[k], RT = P.Rk[k] * t.T, pg = t.p + P.gam[k] * P.pinf[k];
     const double vk = RT * r + P.b[k];
     const double ek = P.cv[k] * t.T * pg * r + P.q[k];
@@ -269,7 +269,7 @@ __device__ __forceinline__ void pt_rev(const KParams& P, const double* Y, double
   double A = 0.0, B = 0.0, AP = 0.0, BP = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    if (Y[k] == 0.0) continue;
+    if (!nonzero(Y[k])) continue;
     A += Y[k] * P.Rk[k] * r[k];
     AP -= Y[k] * P.Rk[k] * r[k] * r[k];
     const double g = (p + P.gam[k] * P.pinf[k]) * r[k];
@@ -288,7 +288,7 @@ __device__ __forceinline__ void pt_rev(const KParams& P, const double* Y, double
   le += mu2;   // dG2/de = -1
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    if (Y[k] == 0.0) continue;
+    if (!nonzero(Y[k])) continue;
     const double dG1 = T * P.Rk[k] * r[k] + P.b[k];
     const double dG2 = T * P.cv[k] * (p + P.gam[k] * P.pinf[k]) * r[k] + P.q[k];
     lY[k] -= mu1 * dG1 + mu2 * dG2;
@@ -352,7 +352,7 @@ __device__ __forceinline__ void hllc_rev(int d, const St<NS>& L, const St<NS>& R
   const double num = R.p - L.p + L.rho * L.u[d] * dL - R.rho * R.u[d] * dR;
   const double den = L.rho * dL - R.rho * dR;
   const double ss = num / den;
-  const double wl = ss > 0.0 ? 1.0 : (ss < 0.0 ? 0.0 : 0.5);
+  const double wl = positive(ss) ? 1.0 : (ss < 0.0 ? 0.0 : 0.5);
   const double wr = 1.0 - wl;
   const double eL = sL - ss, eR = sR - ss;
   const double fL = dL / eL, fR = dR / eR;
@@ -458,7 +458,7 @@ __device__ __forceinline__ void hllc_rev(int d, const St<NS>& L, const St<NS>& R
   lsR += ldR;
   gR.u[d] -= ldR;
   if (sL < 0.0) lsL += lsm;
-  if (sR > 0.0) lsR += lsp;
+  if (positive(sR)) lsR += lsp;
   double lub = 0.0, lab = 0.0;
   if (bl) { lub += lsL; lab -= lsL; } else { gL.u[d] += lsL; gL.a -= lsL; }
   if (br) { lub += lsR; lab += lsR; } else { gR.u[d] += lsR; gR.a += lsR; }

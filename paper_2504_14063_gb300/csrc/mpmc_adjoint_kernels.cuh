@@ -96,7 +96,7 @@ __device__ __forceinline__ void ylim_fwd(YLim<NS>& s, double* Y) {
       Sig += s.m[k];
     }
     s.Sig = Sig;
-    if (Sig != 0.0) {
+    if (nonzero(Sig)) {
       s.f = (1.0 - sum) / Sig;
       s.corrected = true;
     }
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(VJP_THREADS)
     const double a = real_j ? lamL[(long long)v * P.ncell + rj.idx] : 0.0;
     const double b = real_i ? lamL[(long long)v * P.ncell + ri.idx] : 0.0;
     nu[v] = (a - b) * sc;
-    any = any || nu[v] != 0.0;
+    any = any || nonzero(nu[v]);
   }
   if (!any) {
     for (int q = 0; q < L.total; ++q) put(q, 0.0);
@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(VJP_THREADS)
     const double a = real_j ? lamL[(long long)v * P.ncell + rj.idx] : 0.0;
     const double b = real_i ? lamL[(long long)v * P.ncell + ri.idx] : 0.0;
     nu[v] = (a - b) * sc;
-    any = any || nu[v] != 0.0;
+    any = any || nonzero(nu[v]);
   }
   // (k_face_adj has zeroed every slot of a face whose flux adjoint is zero)
   if (!any) return;
@@ -1141,7 +1141,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
   {
     // a cell whose cache adjoint is zero needs no primitive-recovery reverse
     bool any = false;
-    for (int f = 0; f < P.nW; ++f) any = any || gW[(long long)f * ws + c] != 0.0;
+    for (int f = 0; f < P.nW; ++f) any = any || nonzero(gW[(long long)f * ws + c]);
     if (!any) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -1189,7 +1189,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
     for (int k = 0; k < NS; ++k) {
       const int ph = P.phase[k];
       Yp[ph] += Y[k];
-      if (Uc[k] != 0.0) {
+      if (nonzero(Uc[k])) {
         phi[ph] += Uc[k] * (P.Rk[k] * T * th.r[k] + P.b[k]);
         hr[ph] += Uc[k] * h_k(P, k, p, T);
       }
@@ -1229,7 +1229,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
 #pragma unroll
         for (int j = 0; j < NS; ++j)
           if (P.phase[j] == 1) den[i] += Y[j] * P.wilke[i][j];
-        if (den[i] > 0.0) num += Y[i] * P.mu[i] / den[i];
+        if (positive(den[i])) num += Y[i] * P.mu[i] / den[i];
       }
       mup[1] = Yp[1] >= ABSENT ? num : 0.0;
       if (P.viscous) {
@@ -1294,10 +1294,10 @@ __global__ void __launch_bounds__(CELL_THREADS)
           if (P.phase[j] == ph) lY[j] += lYp;
       }
       // mu_g = sum_i Y_i mu_i / den_i, den_i = sum_j Y_j wilke_ij
-      if (Yp[1] >= ABSENT && lmu[1] != 0.0) {
+      if (Yp[1] >= ABSENT && nonzero(lmu[1])) {
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
-          if (P.phase[i] != 1 || !(den[i] > 0.0)) continue;
+          if (P.phase[i] != 1 || !(positive(den[i]))) continue;
           lY[i] += lmu[1] * P.mu[i] / den[i];
           const double lden = -lmu[1] * Y[i] * P.mu[i] / (den[i] * den[i]);
 #pragma unroll
@@ -1309,7 +1309,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
     // phi_p = sum U_k v_k(P,T), hr_p = sum U_k h_k(P,T)
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      if (Uc[k] == 0.0) continue;
+      if (!nonzero(Uc[k])) continue;
       const int ph = P.phase[k];
       const double r = th.r[k];
       const double vk = P.Rk[k] * T * r + P.b[k];
@@ -1348,7 +1348,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     al[k] = prim[(long long)k * n + c];
-    ry[k] = al[k] != 0.0 ? al[k] / v_k(P, k, p, T) : 0.0;
+    ry[k] = nonzero(al[k]) ? al[k] / v_k(P, k, p, T) : 0.0;
     rho += ry[k];
   }
   double u[3] = {0.0, 0.0, 0.0}, u2 = 0.0;
@@ -1370,7 +1370,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     double la = 0.0;
-    if (al[k] != 0.0) {
+    if (nonzero(al[k])) {
       const double r = 1.0 / (p + P.pinf[k]);
       const double vk = P.Rk[k] * T * r + P.b[k];
       const double ek = P.cv[k] * T * (p + P.gam[k] * P.pinf[k]) * r + P.q[k];
