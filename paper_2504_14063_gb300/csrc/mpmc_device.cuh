@@ -374,10 +374,10 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
   }
   const double em = sub_<EX>(e, q), vm = sub_<EX>(v, b);
   int st = ST_OK;
-  if (!(em > 0.0) || !(vm > 0.0)) st = ST_INADMISSIBLE;
+  if (!positive(em) || !positive(vm)) st = ST_INADMISSIBLE;
   // (the contracted form takes E' = (e - q) rho, one division fewer, when no
   // species has a covolume and the caller passes rho = 1/v)
-  const double Ep = (!EX && !P.has_b && rho > 0.0) ? em * rho : em / vm;
+  const double Ep = (!EX && !P.has_b && positive(rho)) ? em * rho : em / vm;
   double pl = -1.0, pmin = 1e300, Rg = 0.0, Rl = 0.0, wpl = 0.0;
   bool multi = false, gas = false;
 #pragma unroll
@@ -505,7 +505,7 @@ __device__ int pt_equilibrium(const KParams& P, const double* Y, double e, doubl
       return st;
     }
   }
-  if (!EX && !multi && pl > 0.0) {
+  if (!EX && !multi && positive(pl)) {
     // every stiffened species present shares P + pl: T = em (P + pl) /
     // (sum_gas Y cv (P + pl) + sum_liquid Y cv (P + gamma pl)), one division
     // (a species with another Pinf can only be a trace below zero, which
@@ -905,9 +905,9 @@ __device__ __forceinline__ void hllc(int d, const State<NS>& L, const State<NS>&
   const double ss = (R.p - L.p + L.rho * L.u[d] * dL - R.rho * R.u[d] * dR) / (L.rho * dL - R.rho * dR);
   // only the side of the contact the face lies on is evaluated; sign(0) = 0
   // takes both with weight 1/2
-  if (ss > 0.0) {
+  if (positive(ss)) {
     hllc_side<NS, D>(d, L, sm, sL, dL, ss, F);
-  } else if (ss < 0.0) {
+  } else if (negative(ss)) {
     hllc_side<NS, D>(d, R, sp, sR, dR, ss, F);
   } else {
     constexpr int NV = NS + D + 1;
@@ -974,7 +974,7 @@ __device__ __forceinline__ bool y_limiter(double* Y, const double* Yc) {
   bool active = false;
 #pragma unroll
   for (int k = 0; k < NS; ++k)
-    if (Y[k] < 0.0) {
+    if (negative(Y[k])) {
       Y[k] = 0.0;
       active = true;
     }
@@ -991,7 +991,7 @@ __device__ __forceinline__ bool y_limiter(double* Y, const double* Yc) {
       dd[k] = (over ? fmin(Y[k], Yc[k]) : fmax(Y[k], Yc[k])) - Y[k];
       Sig += dd[k];
     }
-    if (Sig != 0.0) {
+    if (nonzero(Sig)) {
       const double f = (1.0 - sum) / Sig;
 #pragma unroll
       for (int k = 0; k < NS; ++k) Y[k] += f * dd[k];

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
     const long long ws = P.wstride;
     double rho, Y[NS], u[3], e, irho;
     decode<NS, D>(Uc, rho, Y, u, e, irho);
-    int st = rho > 0.0 ? ST_OK : ST_INADMISSIBLE;
+    int st = positive(rho) ? ST_OK : ST_INADMISSIBLE;
 #pragma unroll
     for (int k = 0; k < NS; ++k)
       if (Uc[k] < -YTOL * rho) st = ST_INADMISSIBLE;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
         for (int k = 0; k < NS; ++k)
           if (P.phase[k] == ph) {
             yp += Y[k];
-            if (Uc[k] != 0.0) {
+            if (nonzero(Uc[k])) {
               // the oracle's operation order without contraction
               const double vk = add_(mul_(P.Rk[k], T) / add_(p, P.pinf[k]), P.b[k]);
               const double hk = add_(add_(mul_(P.cp[k], T), mul_(P.b[k], p)), P.q[k]);
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
 #pragma unroll
           for (int j = 0; j < NS; ++j)
             if (P.phase[j] == 1) den += Y[j] * P.wilke[i][j];
-          if (den > 0.0) num += Y[i] * P.mu[i] / den;
+          if (positive(den)) num += Y[i] * P.mu[i] / den;
         }
         mup[1] = Yp[1] >= ABSENT ? num : 0.0;
         mu = phi[0] * mup[0] + phi[1] * mup[1];
@@ -404,8 +404,8 @@ __global__ void __launch_bounds__(FACE_THREADS)
   if (P.pos_limiter) {
     if (y_limiter<NS>(YL, Yi)) fl |= F_YLIM_L;
     if (y_limiter<NS>(YR, Yj)) fl |= F_YLIM_R;
-    if (!(TL > 0.0)) { TL = Ti; fl |= F_THETA_T_L; }
-    if (!(TR > 0.0)) { TR = Tj; fl |= F_THETA_T_R; }
+    if (!positive(TL)) { TL = Ti; fl |= F_THETA_T_L; }
+    if (!positive(TR)) { TR = Tj; fl |= F_THETA_T_R; }
     bool okL = true, okR = true;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {

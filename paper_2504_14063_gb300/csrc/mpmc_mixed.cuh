@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
     const long long ws = P.wstride;
     double rho, Y[NS], u[3], e, vol;
     decode<NS, D, false>(Uc, rho, Y, u, e, vol);
-    int st = rho > 0.0 ? ST_OK : ST_INADMISSIBLE;
+    int st = positive(rho) ? ST_OK : ST_INADMISSIBLE;
 #pragma unroll
     for (int k = 0; k < NS; ++k)
       if (Uc[k] < -YTOL * rho) st = ST_INADMISSIBLE;
@@ -647,7 +647,7 @@ __device__ __forceinline__ bool admissible_stream(const KParams& P, const double
     if (P.has_b) sb += t * P.b[k];
     if (P.has_q) sq += t * P.q[k];
   }
-  if (!(rho > 0.0) || (P.has_b && !((1.0 - sb) > 0.0))) return false;
+  if (!positive(rho) || (P.has_b && !positive(1.0 - sb))) return false;
 #pragma unroll
   for (int k = 0; k < NS; ++k)
     if (!(T(k) >= -YTOL * rho)) return false;
@@ -658,7 +658,7 @@ __device__ __forceinline__ bool admissible_stream(const KParams& P, const double
     mm += t * t;
   }
   const double ei = rho * T(NS + D) - 0.5 * mm;
-  return (P.has_q ? ei - rho * sq : ei) > 0.0;
+  return positive(P.has_q ? ei - rho * sq : ei);
 }
 
 // per face: FP32 pipeline; the limiter's decisions from FP32 copies of the

@@ -65,7 +65,7 @@ MPMC_HD2 uint64_t bits_of(double x) {
 #endif
 }
 
-// y != 0 and y > 0 from the bits, on the integer pipes (an FP64 comparison
+// y != 0, y > 0 and y < 0 from the bits, on the integer pipes (an FP64 comparison
 // issues on the FP64 pipe, which binds the FP64 kernels); the same results
 // as the comparisons for every input: +-0 is zero, NaN is nonzero and not
 // positive, +inf is positive
@@ -73,6 +73,11 @@ MPMC_HD2 bool nonzero(double y) { return (bits_of(y) << 1) != 0ull; }
 MPMC_HD2 bool positive(double y) {
   const int64_t b = (int64_t)bits_of(y);
   return b > 0 && b <= (int64_t)0x7ff0000000000000ull;
+}
+// y < 0: the sign bit set on a nonzero magnitude that is not NaN
+MPMC_HD2 bool negative(double y) {
+  const uint64_t b = bits_of(y), m = b & 0x7fffffffffffffffull;
+  return (b >> 63) != 0 && m != 0 && m <= 0x7ff0000000000000ull;
 }
 
 }  // namespace mpmc

@@ -4,7 +4,7 @@ and compared bit for bit with the C conversion (round to nearest, ties to
 even) on random doubles over the whole exponent range, exact ties of both
 parities, and the boundaries (the largest finite FP32 and the carry into
 infinity, the smallest normal, zeros, infinities, NaN).  The same header's
-integer-pipe zero and sign tests (nonzero, positive) are compared with the C
+integer-pipe zero and sign tests (nonzero, positive, negative) are compared with the C
 comparisons on random bit patterns of every class (normal, subnormal, zero,
 infinity, NaN) and the special values."""
 import os
@@ -69,13 +69,14 @@ int main() {
     const double xs[] = {from_bits(u), from_bits(u & 0x800fffffffffffffull), from_bits(u | 0x7ff0000000000000ull)};
     for (double x : xs) {
       ++n;
-      if (mpmc::nonzero(x) != (x != 0.0) || mpmc::positive(x) != (x > 0.0)) ++bad;
+      if (mpmc::nonzero(x) != (x != 0.0) || mpmc::positive(x) != (x > 0.0) || mpmc::negative(x) != (x < 0.0)) ++bad;
     }
   }
   for (double x : edge) {
     ++n;
-    if (mpmc::nonzero(x) != (x != 0.0) || mpmc::positive(x) != (x > 0.0)) ++bad;
-    if (mpmc::nonzero(-x) != (-x != 0.0) || mpmc::positive(-x) != (-x > 0.0)) ++bad;
+    if (mpmc::nonzero(x) != (x != 0.0) || mpmc::positive(x) != (x > 0.0) || mpmc::negative(x) != (x < 0.0)) ++bad;
+    if (mpmc::nonzero(-x) != (-x != 0.0) || mpmc::positive(-x) != (-x > 0.0) || mpmc::negative(-x) != (-x < 0.0))
+      ++bad;
   }
   std::printf("%llu %llu\n", bad, n);
   return bad != 0;
