@@ -106,6 +106,14 @@ struct ProfScope {
 };
 
 namespace mpmc {
+// the run clock and end time of a step_n call (scal[2], scal[3]), set in
+// stream order from kernel arguments: a host copy from pageable memory
+// would block the caller until the work queued before it had finished
+__global__ void k_set_run_time(double* scal, double t_end) {
+  scal[2] = 0.0;
+  scal[3] = t_end;
+}
+
 __global__ void k_dt(const KParams P, unsigned long long* red, double* scal, double dt_fixed, double gamma_fixed,
                      double* dt_hist, int* counter) {
   const double smax = __longlong_as_double((long long)red[0]);
@@ -381,12 +389,8 @@ extern "C" int mpmc_step_n(mpmc_ctx* c, double* U, int n, double t_end, double* 
   if (!c || !U || n < 0) return fail(c, MPMC_INVALID_ARG, "step_n: bad argument");
   if (n == 0) return MPMC_OK;
   cudaStream_t s = c->stream;
-  {
-    // run clock and end time (scal[2], scal[3]) for the steps of this call
-    const double tt[2] = {0.0, t_end > 0.0 ? t_end : 0.0};
-    if (cudaMemcpyAsync(c->scal + 2, tt, sizeof(tt), cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return fail(c, MPMC_CUDA_ERROR, "step_n: set end time");
-  }
+  // run clock and end time (scal[2], scal[3]) for the steps of this call
+  k_set_run_time<<<1, 1, 0, s>>>(c->scal, t_end > 0.0 ? t_end : 0.0);
   if (!c->gexec || c->g_U != U || c->g_hist != dt_out) {
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);
@@ -417,12 +421,8 @@ extern "C" int mpmc_step_n(mpmc_ctx* c, double* U, int n, double t_end, double* 
     if (e != cudaSuccess) return fail(c, MPMC_CUDA_ERROR, "step_n: graph launch: %s", cudaGetErrorString(e));
   }
   c->faces_done += 3ull * c->nface_total * (unsigned long long)n;
-  {
-    // later single steps are not clipped
-    const double tt[2] = {0.0, 0.0};
-    if (cudaMemcpyAsync(c->scal + 2, tt, sizeof(tt), cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return fail(c, MPMC_CUDA_ERROR, "step_n: reset end time");
-  }
+  // later single steps are not clipped
+  k_set_run_time<<<1, 1, 0, s>>>(c->scal, 0.0);
   return check_launch(c, "step_n");
 }
 
