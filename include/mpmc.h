@@ -203,7 +203,10 @@ int mpmc_rk_step(mpmc_ctx* ctx, double* U, double dt, uint32_t* tape);
  * stops at physical time t_end — the step that would pass it is clipped to
  * it and any later step has zero length (U unchanged), all decided on the
  * device; t_end <= 0: no end time.  dt_dev_out (nullable, device): receives
- * the n step sizes (their sum is the time advanced). */
+ * the n step sizes (their sum is the time advanced).  Asynchronous, like
+ * mpmc_rk_step: the call returns once the steps are enqueued on the
+ * context's stream (the host does not wait for them); mpmc_get_status
+ * synchronizes. */
 int mpmc_step_n(mpmc_ctx* ctx, double* U, int n, double t_end, double* dt_dev_out);
 
 /* Host-buffer entry: copies U_host (nv x ncells FP64, pinned or pageable)
