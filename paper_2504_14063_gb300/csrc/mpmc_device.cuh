@@ -677,12 +677,44 @@ __device__ __forceinline__ Eno3 eno3(double v0, double v1, double v2, double v3,
   return e;
 }
 
-__device__ __forceinline__ double weno5js(double v0, double v1, double v2, double v3, double v4) {
-  const Eno3 e = eno3(v0, v1, v2, v3, v4);
+// eno3 of both sides of a face: L of w[0..4], R of w[5..1].  The sides share
+// two candidates (the central one of each is the right one of the other)
+// and the second differences w1 - 2 w2 + w3, w2 - 2 w3 + w4.
+__device__ __forceinline__ void eno3_lr(const double* w, Eno3& L, Eno3& R) {
+  const double qa = (-w[1] + 5.0 * w[2] + 2.0 * w[3]) * (1.0 / 6.0);
+  const double qb = (2.0 * w[2] + 5.0 * w[3] - w[4]) * (1.0 / 6.0);
+  const double t123 = w[1] - 2.0 * w[2] + w[3], t234 = w[2] - 2.0 * w[3] + w[4];
+  const double e123 = (13.0 / 12.0) * t123 * t123, e234 = (13.0 / 12.0) * t234 * t234;
+  L.ql = (2.0 * w[0] - 7.0 * w[1] + 11.0 * w[2]) * (1.0 / 6.0);
+  L.qc = qa;
+  L.qr = qb;
+  double t = w[0] - 2.0 * w[1] + w[2], s = w[0] - 4.0 * w[1] + 3.0 * w[2];
+  L.bl = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  s = w[1] - w[3];
+  L.bc = e123 + 0.25 * s * s;
+  s = 3.0 * w[2] - 4.0 * w[3] + w[4];
+  L.br = e234 + 0.25 * s * s;
+  R.ql = (2.0 * w[5] - 7.0 * w[4] + 11.0 * w[3]) * (1.0 / 6.0);
+  R.qc = qb;
+  R.qr = qa;
+  t = w[5] - 2.0 * w[4] + w[3];
+  s = w[5] - 4.0 * w[4] + 3.0 * w[3];
+  R.bl = (13.0 / 12.0) * t * t + 0.25 * s * s;
+  s = w[4] - w[2];
+  R.bc = e234 + 0.25 * s * s;
+  s = 3.0 * w[3] - 4.0 * w[2] + w[1];
+  R.br = e123 + 0.25 * s * s;
+}
+
+__device__ __forceinline__ double weno5js_e(const Eno3& e) {
   constexpr double eps = 1e-6;
   const double il = 1.0 / (eps + e.bl), ic = 1.0 / (eps + e.bc), ir = 1.0 / (eps + e.br);
   const double al = 0.1 * il * il, ac = 0.6 * ic * ic, ar = 0.3 * ir * ir;
   return (al * e.ql + ac * e.qc + ar * e.qr) / (al + ac + ar);
+}
+
+__device__ __forceinline__ double weno5js(double v0, double v1, double v2, double v3, double v4) {
+  return weno5js_e(eno3(v0, v1, v2, v3, v4));
 }
 
 // TENO selection: r_k = C + tau / (beta_k + eps); chi_k = r_k^q / sum r^q,
@@ -749,10 +781,13 @@ __device__ __forceinline__ unsigned teno5_kept(const Eno3& e) {
   return teno_kept<3>(b, fabs(e.bl - e.br), 1e-5);
 }
 
-__device__ __forceinline__ double teno5(double v0, double v1, double v2, double v3, double v4) {
-  const Eno3 e = eno3(v0, v1, v2, v3, v4);
+__device__ __forceinline__ double teno5_e(const Eno3& e) {
   const double q[3] = {e.qc, e.ql, e.qr};
   return teno_combine<3>(q, TENO5_D, teno5_kept(e));
+}
+
+__device__ __forceinline__ double teno5(double v0, double v1, double v2, double v3, double v4) {
+  return teno5_e(eno3(v0, v1, v2, v3, v4));
 }
 
 // TENO6: adds the four-cell candidate i..i+3; optimal weights
@@ -777,10 +812,14 @@ __device__ __forceinline__ unsigned teno6_kept(const Eno3& e, double v0, double 
   return teno_kept<4>(b, fabs(b6 - (e.bl + e.br + 4.0 * e.bc) * (1.0 / 6.0)), 1e-7);
 }
 
-__device__ __forceinline__ double teno6(double v0, double v1, double v2, double v3, double v4, double v5) {
-  const Eno3 e = eno3(v0, v1, v2, v3, v4);
+__device__ __forceinline__ double teno6_e(const Eno3& e, double v0, double v1, double v2, double v3, double v4,
+                                         double v5) {
   const double q[4] = {e.qc, e.ql, e.qr, (3.0 * v2 + 13.0 * v3 - 5.0 * v4 + v5) * (1.0 / 12.0)};
   return teno_combine<4>(q, TENO6_D, teno6_kept(e, v0, v1, v2, v3, v4, v5));
+}
+
+__device__ __forceinline__ double teno6(double v0, double v1, double v2, double v3, double v4, double v5) {
+  return teno6_e(eno3(v0, v1, v2, v3, v4), v0, v1, v2, v3, v4, v5);
 }
 
 // the interpolation of kind RC on the stencil v0..v5 (left side: cells
@@ -863,8 +902,19 @@ __device__ __forceinline__ void recon_lr(const double* y, double eps, double& L,
       R = nR / dR;
     }
   } else {
-    L = recon<RC>(y[0], y[1], y[2], y[3], y[4], y[5], eps);
-    R = recon<RC>(y[5], y[4], y[3], y[2], y[1], y[0], eps);
+    // the other interpolations share the sides' three-cell terms too
+    Eno3 eL, eR;
+    eno3_lr(y, eL, eR);
+    if constexpr (RC == RC_WENO5JS) {
+      L = weno5js_e(eL);
+      R = weno5js_e(eR);
+    } else if constexpr (RC == RC_TENO5) {
+      L = teno5_e(eL);
+      R = teno5_e(eR);
+    } else {
+      L = teno6_e(eL, y[0], y[1], y[2], y[3], y[4], y[5]);
+      R = teno6_e(eR, y[5], y[4], y[3], y[2], y[1], y[0]);
+    }
   }
 }
 
