@@ -61,7 +61,7 @@ TRAFFIC = {"k_face": 6.279e9, "mx::k_face": 3.762e9, "k_prim": 4.207e9, "mx::k_p
 TRAFFIC_SOURCES = ("paper_2504_14063_gb300/csrc/mpmc_kernels.cuh", "paper_2504_14063_gb300/csrc/mpmc_device.cuh",
                    "paper_2504_14063_gb300/csrc/mpmc_kernels_d3.cu", "paper_2504_14063_gb300/csrc/mpmc_mixed.cuh",
                    "paper_2504_14063_gb300/csrc/mpmc_mixed_d3.cu", "paper_2504_14063_gb300/csrc/mpmc_update.cuh")
-TRAFFIC_SHA256 = "9fa27617ce42ebc64daaeed5ea8f6efc0f113e131dce86d529dad3f9562a5b04"
+TRAFFIC_SHA256 = "2fe30e2cc812f9f9efc25d643d0188eb8434e4643e20d8be13770ab9422f1c4d"
 
 
 def sources_sha256():
